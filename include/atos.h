@@ -1,0 +1,173 @@
+/*
+ * atos.h -- C ABI of a GB300 (sm_103a) task-parallel dynamic scheduler for irregular graph work.
+ *
+ * The library implements the scheduling model of "Atos: A Task-Parallel GPU Dynamic Scheduling
+ * Framework for Dynamic Irregular Computations" (Chen et al., PPoPP 2022): one device-wide
+ * worklist of vertex tasks, popped by warp- or CTA-sized workers in a persistent kernel (or one
+ * discrete launch per queue generation), with a tunable fetch size (Sections 3 and 4, Listing 2
+ * and the launch API of Listing 3).  Three relaxed-dependency applications run on it (Section 5):
+ * speculative BFS (Algorithm 2), asynchronous push-residual PageRank (Algorithm 4) and
+ * speculative greedy colouring (Algorithm 6); the level-synchronous forms (Algorithms 1, 3, 5) are
+ * available as the BSP comparator.
+ *
+ * Conventions for every entry point:
+ *   - Graphs are undirected int32 CSR: row_ptr[n + 1] (row_ptr[0] = 0, non-decreasing,
+ *     row_ptr[n] = nnz) and col[nnz] with 0 <= col[k] < n; each undirected edge appears in both
+ *     rows.  nnz must fit in int32.
+ *   - Output buffers are DEVICE memory allocated by the caller (for example torch tensors);
+ *     small control arrays (BFS sources) are HOST memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All work is stream-ordered.
+ *   - Return value: ATOS_OK (0) or a negative ATOS_ERR_* code.  No C++ exception crosses the ABI.
+ *     When a call is given a non-NULL `stats`, it synchronises `stream`, fills `stats` and returns
+ *     the device-side status as well (for example ATOS_ERR_QUEUE_OVERFLOW); with stats == NULL
+ *     it returns once the work is enqueued and reports only host-side errors.
+ *   - Calls on one graph object share its scratch memory: do not let two calls on the same graph
+ *     object overlap on the device.  Different graph objects are independent.
+ *   - The library owns the memory it allocates and frees it in atos_graph_destroy /
+ *     atos_batch_destroy.
+ */
+#ifndef ATOS_H_
+#define ATOS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define ATOS_OK 0
+#define ATOS_ERR_INVALID_ARG (-1)    /* NULL pointer, size out of range, bad config */
+#define ATOS_ERR_BAD_CSR (-2)        /* row_ptr not monotone, col out of range, not symmetric */
+#define ATOS_ERR_OOM (-3)            /* device allocation failed */
+#define ATOS_ERR_QUEUE_OVERFLOW (-4) /* a worklist ring ran out of slots; results are invalid */
+#define ATOS_ERR_TIMEOUT (-5)        /* a device-side wait exceeded spin_limit_ns */
+#define ATOS_ERR_CUDA (-6)           /* a CUDA runtime call failed (no device, launch error...) */
+#define ATOS_ERR_UNSUPPORTED (-7)    /* configuration not built (e.g. this worker size) */
+
+/* ------------------------------------------------------------------ configuration */
+#define ATOS_WORKER_WARP 32 /* worker_size == 32: one warp per worker (persist-32) */
+
+#define ATOS_PERSISTENT 0 /* one launch; workers loop on the queue until it drains (Section 3.4) */
+#define ATOS_DISCRETE 1   /* one launch per queue generation; the host reads the next size */
+#define ATOS_BSP 2        /* level-synchronous comparator (Algorithms 1, 3, 5) */
+
+#define ATOS_FETCH_FIXED 0  /* every pop reserves exactly fetch_size slots */
+#define ATOS_FETCH_GREEDY 1 /* a pop reserves min(fetch_size, tasks available), at least 1 */
+#define ATOS_FETCH_SPREAD 2 /* a pop reserves min(fetch_size, available / workers), at least 1 */
+
+/* atos_config.flags */
+#define ATOS_FLAG_PHANTOM_TASK 1u /* test hook: count one task that is never pushed, so that the
+                                     workers wait for it until spin_limit_ns and report
+                                     ATOS_ERR_TIMEOUT (exercises the bounded waits) */
+
+typedef struct atos_config {
+  int32_t worker_size;    /* 32 (warp worker) or a CTA worker of 64, 128, 256, 512 or 1024 threads */
+  int32_t fetch_size;     /* tasks per pop, 1..1024; at most worker_size for CTA workers (FETCH_SIZE
+                             of Section 4); at most 32 for the warp worker */
+  int32_t strategy;       /* ATOS_PERSISTENT, ATOS_DISCRETE or ATOS_BSP */
+  int32_t fetch_policy;   /* ATOS_FETCH_FIXED, _GREEDY or _SPREAD (persistent strategy only) */
+  int32_t num_blocks;     /* persistent grid size; 0 = all CTAs that fit at once (occupancy x SMs) */
+  int32_t check_size;     /* PageRank: vertex ids checked per task (Check_Size of Algorithm 4);
+                             0 = 32 */
+  int32_t window;         /* batched runs: instances active at once; 0 = automatic */
+  uint32_t flags;         /* ATOS_FLAG_* */
+  int64_t queue_capacity; /* ring slots per instance, rounded up to a power of two; 0 = automatic */
+  int64_t spin_limit_ns;  /* budget of any single device-side wait; 0 = 4 seconds */
+} atos_config;
+
+/* Per-call statistics (filled when the call is given a non-NULL pointer). */
+typedef struct atos_stats {
+  double ms;              /* device time of the call's kernels (CUDA events on `stream`) */
+  int64_t tasks;          /* tasks popped and processed, summed over instances */
+  int64_t edges;          /* neighbour entries read by task bodies */
+  int64_t pushes;         /* tasks pushed (children, re-checks, re-colourings) */
+  int64_t iterations;     /* kernel launches of the scheduling loop (1 when persistent) */
+  double residual_l1;     /* PageRank: FP64 sum of the residues left (unnormalised scale) */
+  double error_bound;     /* PageRank: FP64 bound on the L1 distance of the normalised result
+                             to the exact fixed point, residual_l1 / ((1 - alpha) * sum) */
+  int32_t num_colors;     /* colouring: colours used */
+  int32_t status;         /* device-side status (ATOS_OK or ATOS_ERR_*) */
+} atos_stats;
+
+typedef struct atos_graph_s* atos_graph_t;
+
+/* atos_graph_create flags */
+#define ATOS_DEVICE_PTRS 1u      /* row_ptr and col are device pointers */
+#define ATOS_BORROW 2u           /* with ATOS_DEVICE_PTRS: use the caller's buffers in place; the
+                                    caller keeps them alive and unchanged until destroy */
+#define ATOS_CHECK_SYMMETRIC 4u  /* also verify that every entry (u, v) has its mirror (v, u) */
+#define ATOS_SKIP_VALIDATION 8u  /* trust the CSR (host pointers only) */
+
+/* ------------------------------------------------------------------ entry points */
+
+/* Fills *cfg with the preset named `preset`: NULL or "default" (persistent CTA worker of 256
+ * threads, fetch 256), "persist-warp" (Section 5's persist-32), "persist-cta", "discrete-cta",
+ * "discrete-warp", "bsp".  Returns ATOS_ERR_INVALID_ARG for an unknown name or NULL cfg. */
+int atos_queue_config(atos_config* cfg, const char* preset);
+
+/* Host-side CSR check (the one atos_graph_create runs on host pointers).  flags may contain
+ * ATOS_CHECK_SYMMETRIC.  Returns ATOS_OK, ATOS_ERR_INVALID_ARG (NULL pointer, n < 0, nnz < 0 or
+ * nnz > INT32_MAX) or ATOS_ERR_BAD_CSR.  Touches no GPU. */
+int atos_csr_validate(const int32_t* row_ptr, const int32_t* col, int32_t n, int64_t nnz, uint32_t flags);
+
+/* Uploads (or, with ATOS_DEVICE_PTRS | ATOS_BORROW, adopts) an undirected CSR graph of n
+ * vertices and nnz entries (the CSR of Section 5's algorithms: vertex.neighbors /
+ * neighborLen).  Host CSR is validated on the host; device CSR is validated by a kernel.
+ * On success *out receives a handle owned by the caller until atos_graph_destroy.  n == 0 is
+ * allowed (an empty graph). */
+int atos_graph_create(const int32_t* row_ptr, const int32_t* col, int32_t n, int64_t nnz, uint32_t flags,
+                      void* stream, atos_graph_t* out);
+
+/* Frees everything the library allocated for g (synchronises the device first).  NULL is a
+ * no-op. */
+int atos_graph_destroy(atos_graph_t g);
+
+/* Reports the vertex count, entry count and maximum degree of g (any pointer may be NULL). */
+int atos_graph_info(atos_graph_t g, int32_t* n, int64_t* nnz, int32_t* max_degree);
+
+/* Breadth-first search from each of nsrc sources (Section 5.1; Algorithm 2 when the strategy is
+ * persistent or discrete, Algorithm 1 for ATOS_BSP).  sources: HOST array of nsrc vertex ids in
+ * [0, n).  depths: DEVICE int32 array of nsrc * n entries, row s = hop distances from
+ * sources[s], INT32_MAX for vertices outside the source's component.  All nsrc searches run in
+ * one launch with one worklist each (cfg->window of them active at a time).  Errors:
+ * ATOS_ERR_INVALID_ARG for a NULL pointer, nsrc < 1 or a source out of range. */
+int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* depths, const atos_config* cfg,
+             void* stream, atos_stats* stats);
+
+/* Push-residual PageRank (Section 5.2; Algorithm 4 persistent or discrete, Algorithm 3 for
+ * ATOS_BSP) on the unnormalised scale of the paper: rank starts at 1 - alpha, the residue
+ * of v starts at (1 - alpha) alpha sum_{u in N(v)} 1 / deg(u), and a task pushes
+ * alpha * residue / deg(v) to each neighbour.  Runs until every residue is at most eps.  rank:
+ * DEVICE float array of n entries, returned normalised to sum 1 (the sum is taken in FP64).
+ * alpha in (0, 1), eps > 0.  The FP64 residual and error bound are reported in stats. */
+int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const atos_config* cfg, void* stream,
+                  atos_stats* stats);
+
+/* Speculative greedy colouring (Section 5.3; Algorithm 6's task uberkernel, Algorithm 5 for
+ * ATOS_BSP): every vertex takes the smallest colour not held by a neighbour, then re-checks;
+ * of two adjacent vertices with the same colour the one with the larger id recolours.  colors:
+ * DEVICE int32 array of n entries, each in [0, deg(v)], proper on termination.  num_colors:
+ * HOST int32 receiving the number of colours used (may be NULL; filled after a stream sync). */
+int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_config* cfg, void* stream,
+               atos_stats* stats);
+
+/* Diagnostics: after synchronising the device, copies the queue control words of the last
+ * launch's first ninst instances on g (words[i]: tasks pushed in the high 32 bits, tasks
+ * completed in the low 32 bits; heads[i]: pop tickets handed out) and the site of the first
+ * device wait that ran out of budget (0 = none; 1 ring slot, 2 CTA worker idle, 3 warp worker
+ * idle, 4 successor hand-over, 5 worker lifetime).  Any output pointer may be NULL.  Returns
+ * ATOS_ERR_INVALID_ARG if ninst exceeds the instances g's scratch holds. */
+int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint32_t* heads, int32_t* fail_site);
+
+/* Human-readable name of a status code (static storage). */
+const char* atos_status_string(int status);
+
+/* Library version string (static storage). */
+const char* atos_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ATOS_H_ */

@@ -1,0 +1,270 @@
+"""ctypes binding of the C ABI declared in include/atos.h (argument marshalling only).
+
+Every step of BFS, PageRank and colouring runs in the CUDA kernels of ``libatos.so``; this module
+only converts Python / torch arguments into the plain pointers and sizes of the C entry points.
+PyTorch provides device memory (output tensors) and streams.  There is no CPU fallback: if the
+library is missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libatos.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "atos.h")
+
+# status codes and constants (mirrors include/atos.h)
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_BAD_CSR = -2
+ERR_OOM = -3
+ERR_QUEUE_OVERFLOW = -4
+ERR_TIMEOUT = -5
+ERR_CUDA = -6
+ERR_UNSUPPORTED = -7
+
+WORKER_WARP = 32
+PERSISTENT, DISCRETE, BSP = 0, 1, 2
+FETCH_FIXED, FETCH_GREEDY, FETCH_SPREAD = 0, 1, 2
+FLAG_PHANTOM_TASK = 1
+DEVICE_PTRS, BORROW, CHECK_SYMMETRIC, SKIP_VALIDATION = 1, 2, 4, 8
+UNREACHED = 2**31 - 1
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("worker_size", ctypes.c_int32),
+        ("fetch_size", ctypes.c_int32),
+        ("strategy", ctypes.c_int32),
+        ("fetch_policy", ctypes.c_int32),
+        ("num_blocks", ctypes.c_int32),
+        ("check_size", ctypes.c_int32),
+        ("window", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+        ("queue_capacity", ctypes.c_int64),
+        ("spin_limit_ns", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+    def __repr__(self):
+        return f"Config({self.as_dict()})"
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("ms", ctypes.c_double),
+        ("tasks", ctypes.c_int64),
+        ("edges", ctypes.c_int64),
+        ("pushes", ctypes.c_int64),
+        ("iterations", ctypes.c_int64),
+        ("residual_l1", ctypes.c_double),
+        ("error_bound", ctypes.c_double),
+        ("num_colors", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AtosError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})" if what else status_string(status))
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libatos.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u32, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float
+        P = ctypes.POINTER
+        L.atos_queue_config.argtypes = [P(Config), ctypes.c_char_p]
+        L.atos_csr_validate.argtypes = [vp, vp, i32, i64, u32]
+        L.atos_graph_create.argtypes = [vp, vp, i32, i64, u32, vp, P(vp)]
+        L.atos_graph_destroy.argtypes = [vp]
+        L.atos_graph_info.argtypes = [vp, P(i32), P(i64), P(i32)]
+        L.atos_bfs.argtypes = [vp, vp, i32, vp, P(Config), vp, P(Stats)]
+        L.atos_pagerank.argtypes = [vp, f32, f32, vp, P(Config), vp, P(Stats)]
+        L.atos_color.argtypes = [vp, vp, P(i32), P(Config), vp, P(Stats)]
+        L.atos_debug_queue_state.argtypes = [vp, i32, vp, vp, P(i32)]
+        L.atos_debug_queue_state.restype = ctypes.c_int
+        L.atos_status_string.argtypes = [ctypes.c_int]
+        L.atos_status_string.restype = ctypes.c_char_p
+        L.atos_version.restype = ctypes.c_char_p
+        for name in ("atos_queue_config", "atos_csr_validate", "atos_graph_create", "atos_graph_destroy",
+                     "atos_graph_info", "atos_bfs", "atos_pagerank", "atos_color"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def header_functions(path: str = HEADER) -> list[str]:
+    """Names of the functions declared in an include/*.h header."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(atos_\w+)\s*\(", text)) - {"atos_graph_t"})
+
+
+def status_string(status: int) -> str:
+    return lib().atos_status_string(int(status)).decode()
+
+
+def version() -> str:
+    return lib().atos_version().decode()
+
+
+def queue_config(preset: str | None = None, **overrides) -> Config:
+    """A config filled from a preset ("default", "persist-warp", "persist-cta", "discrete-cta",
+    "discrete-warp", "bsp"), then with the given fields overridden."""
+    cfg = Config()
+    rc = lib().atos_queue_config(ctypes.byref(cfg), preset.encode() if preset else None)
+    if rc != OK:
+        raise AtosError(rc, f"atos_queue_config({preset!r})")
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def csr_validate(row_ptr, col, check_symmetric: bool = False) -> int:
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    return int(lib().atos_csr_validate(rp.ctypes.data, c.ctypes.data if c.size else None, rp.shape[0] - 1,
+                                       c.shape[0], CHECK_SYMMETRIC if check_symmetric else 0))
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise AtosError(rc, what)
+
+
+class Graph:
+    """An undirected int32 CSR graph resident on the GPU (wraps an atos_graph_t).
+
+    ``row_ptr`` / ``col`` may be numpy arrays (host; validated on the host and copied) or torch
+    CUDA int32 tensors (device; ``borrow=True`` uses them in place)."""
+
+    def __init__(self, row_ptr, col, *, borrow: bool = False, check_symmetric: bool = False,
+                 skip_validation: bool = False, stream=None):
+        self._h = ctypes.c_void_p()
+        self._keep = None
+        flags = (CHECK_SYMMETRIC if check_symmetric else 0) | (SKIP_VALIDATION if skip_validation else 0)
+        if hasattr(row_ptr, "is_cuda") and row_ptr.is_cuda:
+            import torch
+            assert row_ptr.dtype == torch.int32 and col.dtype == torch.int32
+            rp, c = row_ptr.contiguous(), col.contiguous()
+            flags |= DEVICE_PTRS | (BORROW if borrow else 0)
+            if borrow:
+                self._keep = (rp, c)
+            n, nnz = rp.numel() - 1, c.numel()
+            rc = lib().atos_graph_create(rp.data_ptr(), c.data_ptr() if nnz else None, n, nnz, flags,
+                                         _stream_handle(stream), ctypes.byref(self._h))
+        else:
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            c = np.ascontiguousarray(col, dtype=np.int32)
+            n, nnz = rp.shape[0] - 1, c.shape[0]
+            rc = lib().atos_graph_create(rp.ctypes.data, c.ctypes.data if nnz else None, n, nnz, flags,
+                                         _stream_handle(stream), ctypes.byref(self._h))
+        _check(rc, "atos_graph_create")
+        n_, nnz_, md = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+        _check(lib().atos_graph_info(self._h, ctypes.byref(n_), ctypes.byref(nnz_), ctypes.byref(md)),
+               "atos_graph_info")
+        self.n, self.nnz, self.max_degree = n_.value, nnz_.value, md.value
+
+    @classmethod
+    def from_csr(cls, g, **kw):
+        """From any object with ``row_ptr`` and ``col`` arrays (e.g. graphgen.CSR)."""
+        return cls(g.row_ptr, g.col, **kw)
+
+    def close(self):
+        if self._h:
+            lib().atos_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def queue_state(self, ninst: int):
+        """(tail, completed, head) per instance of the last launch, and the failed wait site."""
+        words = np.zeros(ninst, dtype=np.uint64)
+        heads = np.zeros(ninst, dtype=np.uint32)
+        site = ctypes.c_int32(0)
+        _check(lib().atos_debug_queue_state(self._h, ninst, words.ctypes.data, heads.ctypes.data,
+                                            ctypes.byref(site)), "atos_debug_queue_state")
+        return [(int(w >> 32), int(w & 0xffffffff), int(h)) for w, h in zip(words, heads)], site.value
+
+    # ------------------------------------------------------------------------------ apps
+
+    def bfs(self, sources, depths=None, cfg: Config | None = None, stream=None, stats: bool = True):
+        """Hop distances from each source: returns (depths [len(sources), n] int32 CUDA tensor,
+        Stats or None).  Raises AtosError on failure (including device-side errors when stats)."""
+        import torch
+        src = np.ascontiguousarray(np.atleast_1d(np.asarray(sources)), dtype=np.int32)
+        if depths is None:
+            depths = torch.empty((src.shape[0], self.n), dtype=torch.int32, device="cuda")
+        st = Stats() if stats else None
+        rc = lib().atos_bfs(self._h, src.ctypes.data, src.shape[0], depths.data_ptr(),
+                            ctypes.byref(cfg) if cfg is not None else None, _stream_handle(stream),
+                            ctypes.byref(st) if st is not None else None)
+        _check(rc, "atos_bfs")
+        return depths, st
+
+    def pagerank(self, alpha: float = 0.85, eps: float = 1e-9, rank=None, cfg: Config | None = None, stream=None,
+                 stats: bool = True):
+        """Push-residual PageRank: returns (rank [n] float32 CUDA tensor summing to 1, Stats)."""
+        import torch
+        if rank is None:
+            rank = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        st = Stats() if stats else None
+        rc = lib().atos_pagerank(self._h, float(alpha), float(eps), rank.data_ptr() if self.n else None,
+                                 ctypes.byref(cfg) if cfg is not None else None, _stream_handle(stream),
+                                 ctypes.byref(st) if st is not None else None)
+        _check(rc, "atos_pagerank")
+        return rank, st
+
+    def color(self, colors=None, cfg: Config | None = None, stream=None, stats: bool = True):
+        """Speculative greedy colouring: returns (colors [n] int32 CUDA tensor, num_colors, Stats)."""
+        import torch
+        if colors is None:
+            colors = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        st = Stats() if stats else None
+        k = ctypes.c_int32(0)
+        rc = lib().atos_color(self._h, colors.data_ptr() if self.n else None, ctypes.byref(k) if stats else None,
+                              ctypes.byref(cfg) if cfg is not None else None, _stream_handle(stream),
+                              ctypes.byref(st) if st is not None else None)
+        _check(rc, "atos_color")
+        return colors, (k.value if stats else None), st

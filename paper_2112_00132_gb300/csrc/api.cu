@@ -1,0 +1,626 @@
+// api.cu -- the C ABI (include/atos.h): argument checks, graph objects, scratch memory, and the
+// host side of the persistent / discrete scheduling loops.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "atos.h"
+#include "engine.cuh"
+#include "launch.cuh"
+#include "state.cuh"
+
+namespace atos {
+const void* pr_persistent_kernel(int worker);
+const void* pr_discrete_kernel(int worker);
+const void* gc_persistent_kernel(int worker);
+const void* gc_discrete_kernel(int worker);
+cudaError_t pr_verify_sweep(Instance* d_insts, int ninst, int max_n, DevCtl* d_ctl, cudaStream_t s);
+cudaError_t pr_finish(Instance* d_insts, int ninst, int n, float alpha, DevCtl* d_ctl, bool certificate,
+                      double exact_sum, cudaStream_t s);
+cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s);
+int bsp_bfs(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t src, int32_t* depth, void* scratch,
+            size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges);
+}  // namespace atos
+
+using namespace atos;
+
+namespace {
+
+constexpr int64_t kDefaultSpinNs = 4000000000LL;
+
+uint32_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p > 0x80000000ULL ? 0 : (uint32_t)p;
+}
+
+int from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return ATOS_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? ATOS_ERR_OOM : ATOS_ERR_CUDA;
+}
+
+#define ATOS_TRY(expr)                          \
+  do {                                          \
+    int _rc = from_cuda(expr);                  \
+    if (_rc != ATOS_OK) return _rc;             \
+  } while (0)
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+// Scratch owned by a graph: instance table, queue control blocks, rings, statistics and the
+// device control block, grown on demand and reused by later calls.
+struct Scratch {
+  int ninst = 0;     // instances the arrays hold
+  uint32_t cap = 0;  // ring slots per instance
+  Instance* d_insts = nullptr;
+  Instance* h_insts = nullptr;  // pinned
+  QueueCtl* d_qctl = nullptr;
+  unsigned long long* d_ring = nullptr;
+  unsigned long long* d_stats = nullptr;
+  unsigned long long* h_stats = nullptr;  // pinned
+  DevCtl* d_ctl = nullptr;
+  DevCtl* h_ctl = nullptr;  // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, upload_done = nullptr;
+  bool upload_pending = false;
+
+  void release() {
+    cudaFree(d_insts), cudaFreeHost(h_insts), cudaFree(d_qctl), cudaFree(d_ring);
+    cudaFree(d_stats), cudaFreeHost(h_stats), cudaFree(d_ctl), cudaFreeHost(h_ctl);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (upload_done) cudaEventDestroy(upload_done);
+    *this = Scratch();
+  }
+};
+
+}  // namespace
+
+struct atos_graph_s {
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int32_t max_degree = 0;
+  int32_t n_isolated = 0;
+  int32_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  bool owned = true;
+  Scratch s;
+  // application state that is not a caller output
+  float* d_res = nullptr;
+  uint32_t* d_qbits = nullptr;
+  void* d_bsp = nullptr;  // BSP comparator frontiers and scan space
+  size_t bsp_bytes = 0;
+};
+
+namespace {
+
+int ensure_scratch(atos_graph_s* g, int ninst, uint32_t cap) {
+  Scratch& s = g->s;
+  if (!s.ev0) {
+    ATOS_TRY(cudaEventCreate(&s.ev0));
+    ATOS_TRY(cudaEventCreate(&s.ev1));
+    ATOS_TRY(cudaEventCreateWithFlags(&s.upload_done, cudaEventDisableTiming));
+  }
+  if (!s.d_ctl) {
+    ATOS_TRY(dev_alloc(&s.d_ctl, 1));
+    ATOS_TRY(cudaMallocHost((void**)&s.h_ctl, sizeof(DevCtl)));
+    DevCtl init;
+    memset(&init, 0, sizeof(init));
+    init.dirty = 1;
+    ATOS_TRY(cudaMemcpy(s.d_ctl, &init, sizeof(init), cudaMemcpyHostToDevice));
+  }
+  if (s.upload_pending) {
+    cudaEventSynchronize(s.upload_done);
+    s.upload_pending = false;
+  }
+  if (ninst <= s.ninst && cap == s.cap) return ATOS_OK;
+  // (re)allocate; the device must be idle with respect to the old buffers
+  cudaDeviceSynchronize();
+  cudaFree(s.d_insts), cudaFreeHost(s.h_insts), cudaFree(s.d_qctl), cudaFree(s.d_ring);
+  cudaFree(s.d_stats), cudaFreeHost(s.h_stats);
+  s.d_insts = nullptr, s.h_insts = nullptr, s.d_qctl = nullptr, s.d_ring = nullptr;
+  s.d_stats = nullptr, s.h_stats = nullptr;
+  const int m = std::max(ninst, s.ninst);
+  s.ninst = 0;
+  s.cap = 0;
+  ATOS_TRY(dev_alloc(&s.d_insts, m));
+  ATOS_TRY(cudaMallocHost((void**)&s.h_insts, sizeof(Instance) * m));
+  ATOS_TRY(dev_alloc(&s.d_qctl, m));
+  ATOS_TRY(dev_alloc(&s.d_ring, (size_t)cap * m));
+  ATOS_TRY(dev_alloc(&s.d_stats, (size_t)kNumStats * m));
+  ATOS_TRY(cudaMallocHost((void**)&s.h_stats, sizeof(unsigned long long) * kNumStats * m));
+  s.ninst = m;
+  s.cap = cap;
+  // fresh rings hold garbage: mark dirty so the next prepare fills them with EMPTY
+  int one = 1;
+  ATOS_TRY(cudaMemcpy(&s.d_ctl->dirty, &one, sizeof(int), cudaMemcpyHostToDevice));
+  return ATOS_OK;
+}
+
+uint32_t ring_capacity(const atos_config& cfg, int32_t n, uint32_t prefix) {
+  uint64_t want = cfg.queue_capacity > 0 ? (uint64_t)cfg.queue_capacity : (uint64_t)2 * n + prefix + 1024;
+  return next_pow2(std::max<uint64_t>(want, 1024));
+}
+
+int check_config(const atos_config& c) {
+  if (!worker_supported(c.worker_size)) return ATOS_ERR_UNSUPPORTED;
+  if (c.fetch_size < 1 || c.fetch_size > 1024) return ATOS_ERR_INVALID_ARG;
+  if (c.worker_size != 32 && c.fetch_size > c.worker_size) return ATOS_ERR_INVALID_ARG;
+  if (c.strategy < ATOS_PERSISTENT || c.strategy > ATOS_BSP) return ATOS_ERR_INVALID_ARG;
+  if (c.fetch_policy < ATOS_FETCH_FIXED || c.fetch_policy > ATOS_FETCH_SPREAD) return ATOS_ERR_INVALID_ARG;
+  if (c.num_blocks < 0 || c.check_size < 0 || c.window < 0 || c.queue_capacity < 0 || c.spin_limit_ns < 0)
+    return ATOS_ERR_INVALID_ARG;
+  return ATOS_OK;
+}
+
+void default_config(atos_config* c) {
+  memset(c, 0, sizeof(*c));
+  c->worker_size = 256;
+  c->fetch_size = 256;
+  c->strategy = ATOS_PERSISTENT;
+  c->fetch_policy = ATOS_FETCH_SPREAD;
+  c->num_blocks = 0;
+  c->check_size = 32;
+  c->window = 0;
+  c->queue_capacity = 0;
+  c->spin_limit_ns = 0;
+}
+
+// Uploads the instance table (from pinned memory, so the copy is asynchronous; the next call
+// waits for it before rewriting the table).
+int upload_instances(Scratch& s, int ninst, cudaStream_t st) {
+  ATOS_TRY(cudaMemcpyAsync(s.d_insts, s.h_insts, sizeof(Instance) * ninst, cudaMemcpyHostToDevice, st));
+  ATOS_TRY(cudaEventRecord(s.upload_done, st));
+  s.upload_pending = true;
+  return ATOS_OK;
+}
+
+// Runs the scheduling loop over the instances in s.h_insts[0, ninst).  The caller has filled the
+// table; `kp` / `kd` are the body's persistent / discrete kernels.
+int run_instances(atos_graph_s* g, int ninst, int max_n, const atos_config& cfg, const void* (*kp)(int),
+                  const void* (*kd)(int), int app, cudaStream_t st, int64_t* iterations) {
+  Scratch& s = g->s;
+  const int worker = cfg.worker_size;
+  const int threads = block_threads(worker);
+  int window = cfg.window > 0 ? std::min(cfg.window, ninst) : ninst;
+  Launch L;
+  memset(&L, 0, sizeof(L));
+  L.insts = s.d_insts;
+  L.ninst = ninst;
+  L.window = window;
+  L.fetch = cfg.fetch_size;
+  L.policy = cfg.fetch_policy;
+  L.flags = cfg.flags;
+  L.status = &s.d_ctl->status;
+  L.next_inst = &s.d_ctl->next_inst;
+  L.spin_limit_ns = cfg.spin_limit_ns > 0 ? cfg.spin_limit_ns : kDefaultSpinNs;
+  L.lifetime_ns = L.spin_limit_ns * 16;
+  L.fail_site = &s.d_ctl->fail_site;
+  int rc = upload_instances(s, ninst, st);
+  if (rc) return rc;
+  ATOS_TRY(launch_prepare(s.d_insts, ninst, max_n, s.d_ctl, cfg.flags, (unsigned)window, st));
+  int64_t iters = 0;
+  if (cfg.strategy == ATOS_PERSISTENT) {
+    const void* fn = kp(worker);
+    if (!fn) return ATOS_ERR_UNSUPPORTED;
+    int nb = cfg.num_blocks > 0 ? cfg.num_blocks : resident_blocks(fn, threads);
+    if (nb <= 0) return ATOS_ERR_CUDA;
+    const int workers_per_block = worker == 32 ? kWarpBlock / 32 : 1;
+    L.nworkers = std::max(1, nb * workers_per_block / window);
+    ATOS_TRY(launch_kernel(fn, dim3(nb), threads, L, st));
+    iters = 1;
+  } else {
+    const void* fn = kd(worker);
+    if (!fn) return ATOS_ERR_UNSUPPORTED;
+    const int per_block = worker == 32 ? std::min(cfg.fetch_size, 32) * (kWarpBlock / 32) : cfg.fetch_size;
+    unsigned gen = 0;
+    for (int i = 0; i < ninst; ++i) gen = std::max(gen, s.h_insts[i].prefix_len);
+    for (;;) {
+      if (iters > (1 << 24)) return ATOS_ERR_TIMEOUT;
+      if (gen == 0) {
+        if (app != kAppPr) break;
+        // PageRank: the queue drained; sweep every residue once (Algorithm 4's scan over all
+        // ids) and stop only if nothing exceeds epsilon.
+        ATOS_TRY(pr_verify_sweep(s.d_insts, ninst, max_n, s.d_ctl, st));
+        ATOS_TRY(launch_next_generation(s.d_insts, ninst, s.d_ctl, st));
+        ATOS_TRY(cudaMemcpyAsync(s.h_ctl, s.d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+        ATOS_TRY(cudaStreamSynchronize(st));
+        if (s.h_ctl->status) break;
+        gen = s.h_ctl->maxgen;
+        if (gen == 0) break;
+      }
+      unsigned gx = (gen + per_block - 1) / per_block;
+      L.nworkers = (int)gx;
+      ATOS_TRY(launch_kernel(fn, dim3(gx, ninst), threads, L, st));
+      ATOS_TRY(launch_next_generation(s.d_insts, ninst, s.d_ctl, st));
+      ATOS_TRY(cudaMemcpyAsync(s.h_ctl, s.d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+      ATOS_TRY(cudaStreamSynchronize(st));
+      iters++;
+      if (s.h_ctl->status) break;
+      gen = s.h_ctl->maxgen;
+    }
+  }
+  ATOS_TRY(launch_finalize(s.d_ctl, st));
+  if (iterations) *iterations = iters;
+  return ATOS_OK;
+}
+
+// Synchronises and reads back the statistics of a launch over `ninst` instances.
+int collect_stats(atos_graph_s* g, int ninst, cudaStream_t st, atos_stats* out) {
+  Scratch& s = g->s;
+  ATOS_TRY(cudaMemcpyAsync(s.h_stats, s.d_stats, sizeof(unsigned long long) * kNumStats * ninst,
+                           cudaMemcpyDeviceToHost, st));
+  ATOS_TRY(cudaMemcpyAsync(s.h_ctl, s.d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+  ATOS_TRY(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, s.ev0, s.ev1);
+  out->ms = ms;
+  out->tasks = out->edges = out->pushes = 0;
+  for (int i = 0; i < ninst; ++i) {
+    out->tasks += (int64_t)s.h_stats[i * kNumStats + kStatTasks];
+    out->edges += (int64_t)s.h_stats[i * kNumStats + kStatEdges];
+    out->pushes += (int64_t)s.h_stats[i * kNumStats + kStatPushes];
+  }
+  out->status = s.h_ctl->status;
+  return ATOS_OK;
+}
+
+Instance base_instance(atos_graph_s* g, int i, int app, uint32_t cap, uint32_t prefix_len, int32_t prefix_item) {
+  Scratch& s = g->s;
+  Instance I;
+  memset(&I, 0, sizeof(I));
+  I.row_ptr = g->row_ptr;
+  I.col = g->col;
+  I.n = g->n;
+  I.app = app;
+  I.ring = s.d_ring + (size_t)cap * i;
+  I.cap = cap;
+  I.prefix_len = prefix_len;
+  I.prefix_item = prefix_item;
+  I.ctl = s.d_qctl + i;
+  I.stats = s.d_stats + (size_t)kNumStats * i;
+  return I;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+const char* atos_status_string(int status) {
+  switch (status) {
+    case ATOS_OK: return "ok";
+    case ATOS_ERR_INVALID_ARG: return "invalid argument";
+    case ATOS_ERR_BAD_CSR: return "malformed CSR graph";
+    case ATOS_ERR_OOM: return "device out of memory";
+    case ATOS_ERR_QUEUE_OVERFLOW: return "worklist ring overflow";
+    case ATOS_ERR_TIMEOUT: return "device wait exceeded its time budget";
+    case ATOS_ERR_CUDA: return "CUDA runtime error";
+    case ATOS_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* atos_version(void) { return "atos-gb300 0.1 (sm_103a)"; }
+
+int atos_queue_config(atos_config* cfg, const char* preset) {
+  if (!cfg) return ATOS_ERR_INVALID_ARG;
+  default_config(cfg);
+  if (!preset || !strcmp(preset, "default") || !strcmp(preset, "persist-cta")) return ATOS_OK;
+  if (!strcmp(preset, "persist-warp")) {
+    cfg->worker_size = 32;
+    cfg->fetch_size = 1;
+    cfg->fetch_policy = ATOS_FETCH_FIXED;
+    return ATOS_OK;
+  }
+  if (!strcmp(preset, "discrete-cta")) {
+    cfg->strategy = ATOS_DISCRETE;
+    return ATOS_OK;
+  }
+  if (!strcmp(preset, "discrete-warp")) {
+    cfg->worker_size = 32;
+    cfg->fetch_size = 1;
+    cfg->strategy = ATOS_DISCRETE;
+    return ATOS_OK;
+  }
+  if (!strcmp(preset, "bsp")) {
+    cfg->strategy = ATOS_BSP;
+    return ATOS_OK;
+  }
+  return ATOS_ERR_INVALID_ARG;
+}
+
+int atos_csr_validate(const int32_t* row_ptr, const int32_t* col, int32_t n, int64_t nnz, uint32_t flags) {
+  if (n < 0 || nnz < 0 || nnz > INT32_MAX || !row_ptr || (nnz > 0 && !col)) return ATOS_ERR_INVALID_ARG;
+  if (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz) return ATOS_ERR_BAD_CSR;
+  for (int32_t v = 0; v < n; ++v)
+    if (row_ptr[v + 1] < row_ptr[v]) return ATOS_ERR_BAD_CSR;
+  for (int64_t k = 0; k < nnz; ++k)
+    if (col[k] < 0 || col[k] >= n) return ATOS_ERR_BAD_CSR;
+  if (flags & ATOS_CHECK_SYMMETRIC) {
+    // every (v, w) needs (w, v): count mirrored entries row by row with a per-row cursor
+    std::vector<int32_t> cur(row_ptr, row_ptr + n);
+    for (int32_t v = 0; v < n; ++v)
+      for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+        const int32_t w = col[k];
+        bool found = false;
+        for (int32_t j = row_ptr[w]; j < row_ptr[w + 1]; ++j)
+          if (col[j] == v) {
+            found = true;
+            break;
+          }
+        if (!found) return ATOS_ERR_BAD_CSR;
+      }
+  }
+  return ATOS_OK;
+}
+
+int atos_graph_create(const int32_t* row_ptr, const int32_t* col, int32_t n, int64_t nnz, uint32_t flags,
+                      void* stream, atos_graph_t* out) {
+  if (!out) return ATOS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 0 || nnz < 0 || nnz > INT32_MAX || !row_ptr || (nnz > 0 && !col)) return ATOS_ERR_INVALID_ARG;
+  if ((flags & ATOS_BORROW) && !(flags & ATOS_DEVICE_PTRS)) return ATOS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> hrp;
+  const int32_t* rp_host = nullptr;
+  if (!(flags & ATOS_DEVICE_PTRS)) {
+    if (!(flags & ATOS_SKIP_VALIDATION)) {
+      int rc = atos_csr_validate(row_ptr, col, n, nnz, flags);
+      if (rc) return rc;
+    }
+    rp_host = row_ptr;
+  } else {
+    hrp.resize((size_t)n + 1);
+    ATOS_TRY(cudaMemcpyAsync(hrp.data(), row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+    ATOS_TRY(cudaStreamSynchronize(st));
+    rp_host = hrp.data();
+    if (rp_host[0] != 0 || rp_host[n] != nnz) return ATOS_ERR_BAD_CSR;
+    for (int32_t v = 0; v < n; ++v)
+      if (rp_host[v + 1] < rp_host[v]) return ATOS_ERR_BAD_CSR;
+  }
+  atos_graph_s* g = new (std::nothrow) atos_graph_s();
+  if (!g) return ATOS_ERR_OOM;
+  g->n = n;
+  g->nnz = nnz;
+  for (int32_t v = 0; v < n; ++v) {
+    const int32_t d = rp_host[v + 1] - rp_host[v];
+    g->max_degree = std::max(g->max_degree, d);
+    g->n_isolated += d == 0;
+  }
+  int rc = ATOS_OK;
+  if (flags & ATOS_BORROW) {
+    g->row_ptr = const_cast<int32_t*>(row_ptr);
+    g->col = const_cast<int32_t*>(col);
+    g->owned = false;
+  } else {
+    const cudaMemcpyKind kind = (flags & ATOS_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    rc = from_cuda(dev_alloc(&g->row_ptr, (size_t)n + 1));
+    if (!rc) rc = from_cuda(dev_alloc(&g->col, (size_t)nnz));
+    if (!rc) rc = from_cuda(cudaMemcpyAsync(g->row_ptr, row_ptr, sizeof(int32_t) * (n + 1), kind, st));
+    if (!rc && nnz) rc = from_cuda(cudaMemcpyAsync(g->col, col, sizeof(int32_t) * nnz, kind, st));
+    if (!rc) rc = from_cuda(cudaStreamSynchronize(st));
+  }
+  if (rc) {
+    atos_graph_destroy(g);
+    return rc;
+  }
+  *out = g;
+  return ATOS_OK;
+}
+
+int atos_graph_destroy(atos_graph_t g) {
+  if (!g) return ATOS_OK;
+  cudaDeviceSynchronize();
+  if (g->owned) cudaFree(g->row_ptr), cudaFree(g->col);
+  cudaFree(g->d_res), cudaFree(g->d_qbits), cudaFree(g->d_bsp);
+  g->s.release();
+  delete g;
+  return ATOS_OK;
+}
+
+int atos_graph_info(atos_graph_t g, int32_t* n, int64_t* nnz, int32_t* max_degree) {
+  if (!g) return ATOS_ERR_INVALID_ARG;
+  if (n) *n = g->n;
+  if (nnz) *nnz = g->nnz;
+  if (max_degree) *max_degree = g->max_degree;
+  return ATOS_OK;
+}
+
+int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* depths, const atos_config* cfg_in,
+             void* stream, atos_stats* stats) {
+  if (!g || !sources || !depths || nsrc < 1 || nsrc > 65535) return ATOS_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < nsrc; ++i)
+    if (sources[i] < 0 || sources[i] >= g->n) return ATOS_ERR_INVALID_ARG;
+  atos_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else default_config(&cfg);
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = g->n;
+  if (cfg.strategy == ATOS_BSP) {
+    if (!g->s.ev0) {
+      rc = ensure_scratch(g, 1, 1024);
+      if (rc) return rc;
+    }
+    const size_t need = sizeof(int32_t) * (3 * (size_t)n + (size_t)n / 1024 + 4096);
+    if (g->bsp_bytes < need) {
+      cudaDeviceSynchronize();
+      cudaFree(g->d_bsp);
+      g->d_bsp = nullptr;
+      g->bsp_bytes = 0;
+      ATOS_TRY(cudaMalloc(&g->d_bsp, need));
+      g->bsp_bytes = need;
+    }
+    ATOS_TRY(cudaEventRecord(g->s.ev0, st));
+    int64_t iters = 0, edges = 0;
+    for (int32_t i = 0; i < nsrc; ++i) {
+      int64_t it = 0, ed = 0;
+      rc = bsp_bfs(g->row_ptr, g->col, g->n, sources[i], depths + (size_t)i * n, g->d_bsp, g->bsp_bytes,
+                   (int32_t*)&g->s.h_ctl->maxgen, st, &it, &ed);
+      if (rc) return rc;
+      iters += it;
+      edges += ed;
+    }
+    ATOS_TRY(cudaEventRecord(g->s.ev1, st));
+    if (stats) {
+      memset(stats, 0, sizeof(*stats));
+      ATOS_TRY(cudaStreamSynchronize(st));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, g->s.ev0, g->s.ev1);
+      stats->ms = ms;
+      stats->iterations = iters;
+      stats->edges = edges;
+      stats->status = ATOS_OK;
+    }
+    return ATOS_OK;
+  }
+  const uint32_t cap = ring_capacity(cfg, g->n, 1);
+  if (!cap) return ATOS_ERR_INVALID_ARG;
+  rc = ensure_scratch(g, nsrc, cap);
+  if (rc) return rc;
+  for (int32_t i = 0; i < nsrc; ++i) {
+    Instance I = base_instance(g, i, kAppBfs, cap, 1, sources[i]);
+    I.depth = depths + (size_t)i * n;
+    g->s.h_insts[i] = I;
+  }
+  if (cfg.window == 0) {
+    // keep the depth arrays of the active searches within about half of L2 (129 MB)
+    const int64_t per = 4 * n + 1;
+    cfg.window = (int)std::max<int64_t>(1, std::min<int64_t>(nsrc, (64LL << 20) / per));
+  }
+  ATOS_TRY(cudaEventRecord(g->s.ev0, st));
+  int64_t iters = 0;
+  rc = run_instances(g, nsrc, g->n, cfg, bfs_persistent_kernel, bfs_discrete_kernel, kAppBfs, st, &iters);
+  if (rc) return rc;
+  ATOS_TRY(cudaEventRecord(g->s.ev1, st));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    rc = collect_stats(g, nsrc, st, stats);
+    if (rc) return rc;
+    stats->iterations = iters;
+    return stats->status;
+  }
+  return ATOS_OK;
+}
+
+int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const atos_config* cfg_in, void* stream,
+                  atos_stats* stats) {
+  if (!g || !rank || !(alpha > 0.0f && alpha < 1.0f) || !(eps > 0.0f)) return ATOS_ERR_INVALID_ARG;
+  atos_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else default_config(&cfg);
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (g->n == 0) return ATOS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t n = g->n;
+  if (cfg.strategy == ATOS_BSP) return ATOS_ERR_UNSUPPORTED;
+  const uint32_t cap = ring_capacity(cfg, n, (uint32_t)n);
+  if (!cap) return ATOS_ERR_INVALID_ARG;
+  rc = ensure_scratch(g, 1, cap);
+  if (rc) return rc;
+  if (!g->d_res) {
+    ATOS_TRY(dev_alloc(&g->d_res, (size_t)n));
+    ATOS_TRY(dev_alloc(&g->d_qbits, (size_t)(n + 31) / 32));
+  }
+  Instance I = base_instance(g, 0, kAppPr, cap, (uint32_t)n, -1);
+  I.rank = rank;
+  I.res = g->d_res;
+  I.qbits = g->d_qbits;
+  I.alpha = alpha;
+  I.eps = eps;
+  I.check_size = cfg.check_size > 0 ? (uint32_t)cfg.check_size : 32u;
+  g->s.h_insts[0] = I;
+  cfg.window = 1;
+  const double exact_sum = (double)n - (double)alpha * (double)g->n_isolated;
+  ATOS_TRY(cudaEventRecord(g->s.ev0, st));
+  int64_t iters = 0;
+  rc = run_instances(g, 1, n, cfg, pr_persistent_kernel, pr_discrete_kernel, kAppPr, st, &iters);
+  if (rc) return rc;
+  ATOS_TRY(pr_finish(g->s.d_insts, 1, n, alpha, g->s.d_ctl, stats != nullptr, exact_sum, st));
+  ATOS_TRY(cudaEventRecord(g->s.ev1, st));
+  if (stats) {
+    rc = collect_stats(g, 1, st, stats);
+    if (rc) return rc;
+    stats->iterations = iters;
+    stats->residual_l1 = g->s.h_ctl->sum_res;
+    const double denom = (1.0 - (double)alpha) * exact_sum;
+    stats->error_bound = g->s.h_ctl->cert_l1 / denom + 5.96e-8;  // + FP32 rounding of the output
+    return stats->status;
+  }
+  return ATOS_OK;
+}
+
+int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_config* cfg_in, void* stream,
+               atos_stats* stats) {
+  if (!g || !colors) return ATOS_ERR_INVALID_ARG;
+  atos_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else default_config(&cfg);
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (num_colors) *num_colors = 0;
+  if (g->n == 0) return ATOS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t n = g->n;
+  if (cfg.strategy == ATOS_BSP) return ATOS_ERR_UNSUPPORTED;
+  const uint32_t cap = ring_capacity(cfg, n, (uint32_t)n);
+  if (!cap) return ATOS_ERR_INVALID_ARG;
+  rc = ensure_scratch(g, 1, cap);
+  if (rc) return rc;
+  Instance I = base_instance(g, 0, kAppGc, cap, (uint32_t)n, -1);
+  I.color = colors;
+  g->s.h_insts[0] = I;
+  cfg.window = 1;
+  ATOS_TRY(cudaEventRecord(g->s.ev0, st));
+  int64_t iters = 0;
+  rc = run_instances(g, 1, n, cfg, gc_persistent_kernel, gc_discrete_kernel, kAppGc, st, &iters);
+  if (rc) return rc;
+  ATOS_TRY(gc_finish(&I, g->s.d_ctl, st));
+  ATOS_TRY(cudaEventRecord(g->s.ev1, st));
+  if (stats || num_colors) {
+    atos_stats local;
+    atos_stats* out = stats ? stats : &local;
+    memset(out, 0, sizeof(*out));
+    rc = collect_stats(g, 1, st, out);
+    if (rc) return rc;
+    out->iterations = iters;
+    out->num_colors = g->s.h_ctl->num_colors;
+    if (num_colors) *num_colors = g->s.h_ctl->num_colors;
+    return out->status;
+  }
+  return ATOS_OK;
+}
+
+int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint32_t* heads, int32_t* fail_site) {
+  if (!g || ninst < 0 || ninst > g->s.ninst) return ATOS_ERR_INVALID_ARG;
+  ATOS_TRY(cudaDeviceSynchronize());
+  for (int32_t i = 0; i < ninst; ++i) {
+    QueueCtl c;
+    ATOS_TRY(cudaMemcpy(&c, g->s.d_qctl + i, sizeof(c), cudaMemcpyDeviceToHost));
+    if (words) words[i] = c.word;
+    if (heads) heads[i] = c.head;
+  }
+  if (fail_site && g->s.d_ctl) {
+    DevCtl d;
+    ATOS_TRY(cudaMemcpy(&d, g->s.d_ctl, sizeof(d), cudaMemcpyDeviceToHost));
+    *fail_site = d.fail_site;
+  }
+  return ATOS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// bfs.cuh -- the speculative BFS task body (Section 5.1, Algorithm 2).
+#pragma once
+
+#include "engine.cuh"
+
+namespace atos {
+
+struct BfsBody {
+  using Extra = NoExtra;
+
+  // CTA worker: stage (row start, depth + 1) of the popped vertices, scan their degrees and map
+  // the flattened neighbour range onto the threads (load-balancing search inside the worker).
+  template <int BLOCK, class S>
+  __device__ static void cta_batch(S& sm, int cnt, const Launch& L, unsigned long long* st) {
+    const Instance& I = sm.I;
+    int deg = 0;
+    if ((int)threadIdx.x < cnt) {
+      const int v = sm.items[threadIdx.x];
+      const int s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
+      const int d = ld_relaxed(I.depth + v);
+      sm.start[threadIdx.x] = s;
+      sm.aux[threadIdx.x] = d + 1;
+      deg = d == kUnreached ? 0 : e - s;  // a queued vertex always has a depth; never relax from INT32_MAX
+    }
+    int total;
+    const int off = block_exclusive_scan<BLOCK>(deg, sm.tmp, total);
+    if ((int)threadIdx.x < cnt) sm.off[threadIdx.x] = off;
+    __syncthreads();
+    int32_t* __restrict__ depth = I.depth;
+    const int32_t* __restrict__ col = I.col;
+    for (int base = 0; base < total; base += BLOCK) {
+      const int e = base + threadIdx.x;
+      bool want = false;
+      int nb = 0;
+      if (e < total) {
+        const int i = owner_of(sm.off, cnt, e);
+        nb = ldg(col + sm.start[i] + (e - sm.off[i]));
+        const int nd = sm.aux[i];
+        if (nd < __ldcg(depth + nb)) want = nd < atomicMin(depth + nb, nd);
+      }
+      cta_push(sm, want, nb);
+      if (base + BLOCK < total) cta_maybe_flush<BLOCK>(sm, I, L, st);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      st[kStatTasks] += cnt;
+      st[kStatEdges] += total;
+    }
+    cta_flush<BLOCK>(sm, I, cnt, L, st);
+  }
+
+  template <int BLOCK, class S>
+  __device__ static int cta_idle(S& sm, const Launch&, unsigned long long*) {
+    return threadIdx.x == 0 ? (instance_quiescent(sm.I) ? 1 : 0) : 0;
+  }
+
+  // Warp worker: the 32 lanes stride the neighbour list of one vertex.
+  __device__ static void warp_item(WarpSmem& ws, const Instance& I, int v, const Launch& L, unsigned long long* st) {
+    const int lane = threadIdx.x & 31;
+    int d = 0;
+    if (lane == 0) d = ld_relaxed(I.depth + v);
+    d = __shfl_sync(0xffffffffu, d, 0);  // one read, so every lane relaxes with the same depth
+    const int nd = d + 1;
+    const int s = ldg(I.row_ptr + v), e = d == kUnreached ? s : ldg(I.row_ptr + v + 1);
+    for (int k = s; k < e; k += 32) {
+      const int j = k + lane;
+      bool want = false;
+      int nb = 0;
+      if (j < e) {
+        nb = ldg(I.col + j);
+        if (nd < __ldcg(I.depth + nb)) want = nd < atomicMin(I.depth + nb, nd);
+      }
+      warp_push(ws, want, nb);
+      warp_maybe_flush(ws, I, L, st);
+    }
+    if (lane == 0) st[kStatEdges] += e - s;
+  }
+
+  __device__ static int warp_idle(WarpSmem&, const Instance& I, const Launch&, unsigned long long*) {
+    return (threadIdx.x & 31) == 0 ? (instance_quiescent(I) ? 1 : 0) : 0;
+  }
+};
+
+}  // namespace atos

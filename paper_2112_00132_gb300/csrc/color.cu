@@ -1,0 +1,192 @@
+// color.cu -- asynchronous speculative greedy colouring (Section 5.3, Algorithm 6).
+//
+// One uberkernel handles two kinds of task, told apart by the sign of the item:
+//   * item v >= 0 (assign): read the colours of v's neighbours, give v the smallest colour none
+//     of them holds (first fit; the colour is at most deg(v)), then push the check task ~v;
+//   * item ~v < 0 (check): if a neighbour u < v holds v's colour, push v to recolour it.
+// Because only the larger id of a conflicting pair recolours, the smallest id of any conflict
+// keeps its colour and the recolouring cannot cycle; when the queue drains, every vertex's last
+// check ran after its last colour change, so the colouring is proper.  The check task is encoded
+// as ~v = -v - 1 so that vertex 0 has a distinct check task.
+//
+// Colours are read from L2 (ld.global.cg) so a worker sees other workers' recent writes; a colour
+// is written before the check task is published, and the publication is ordered after it by a
+// device-scope fence.
+#include "engine.cuh"
+#include "launch.cuh"
+#include "state.cuh"
+
+namespace atos {
+
+constexpr int kGcWindow = 64;  // colours examined per pass: two 32-bit words per item
+
+struct GcExtra {
+  unsigned bits[2 * 1024];  // per item: forbidden colours [base, base + 64) (assign) or
+                            // (own colour, conflict flag) (check)
+  int pass_base;
+};
+
+struct GcBody {
+  using Extra = GcExtra;
+
+  template <int BLOCK, class S>
+  __device__ static void cta_batch(S& sm, int cnt, const Launch& L, unsigned long long* st) {
+    const Instance& I = sm.I;
+    const int t = threadIdx.x;
+    int v = 0, deg = 0, s = 0;
+    bool assign = false;
+    if (t < cnt) {
+      const int item = sm.items[t];
+      assign = item >= 0;
+      v = assign ? item : ~item;
+      s = ldg(I.row_ptr + v);
+      deg = ldg(I.row_ptr + v + 1) - s;
+      sm.start[t] = s;
+      sm.aux[t] = item;
+      if (assign) {
+        sm.x.bits[2 * t] = 0u;
+        sm.x.bits[2 * t + 1] = 0u;
+      } else {
+        sm.x.bits[2 * t] = (unsigned)__ldcg(I.color + v);
+        sm.x.bits[2 * t + 1] = 0u;
+      }
+    }
+    int64_t edges = 0;
+    int colour = -1;  // result of an assign item (thread t)
+    // pass 0 runs every item; later passes only assign items that found no free colour in the
+    // window [base, base + 64).
+    bool active = t < cnt;
+    for (int base = 0;; base += kGcWindow) {
+      const int mydeg = active ? deg : 0;
+      int total;
+      const int off = block_exclusive_scan<BLOCK>(mydeg, sm.tmp, total);
+      // inactive items have degree 0 here, so the offsets stay non-decreasing and the owner
+      // search never lands on them
+      if (t < cnt) sm.off[t] = off;
+      if (total == 0 && base > 0) break;
+      __syncthreads();
+      for (int r = 0; r < total; r += BLOCK) {
+        const int e = r + t;
+        if (e < total) {
+          const int i = owner_of(sm.off, cnt, e);
+          const int nb = ldg(I.col + sm.start[i] + (e - sm.off[i]));
+          const int c = __ldcg(I.color + nb);
+          const int item = sm.aux[i];
+          if (item >= 0) {
+            const int rel = c - base;
+            if (rel >= 0 && rel < kGcWindow) atomicOr(&sm.x.bits[2 * i + (rel >> 5)], 1u << (rel & 31));
+          } else if (nb < ~item && c == (int)sm.x.bits[2 * i]) {
+            sm.x.bits[2 * i + 1] = 1u;
+          }
+        }
+      }
+      edges += total;
+      __syncthreads();
+      bool again = false;
+      if (active && assign) {
+        const unsigned lo = sm.x.bits[2 * t], hi = sm.x.bits[2 * t + 1];
+        const unsigned long long used = ((unsigned long long)hi << 32) | lo;
+        if (~used) {
+          colour = base + __ffsll((long long)~used) - 1;
+        } else {
+          again = true;
+          sm.x.bits[2 * t] = 0u;
+          sm.x.bits[2 * t + 1] = 0u;
+        }
+      }
+      active = again;
+      if (!__syncthreads_or(again)) break;
+    }
+    // results: write colours, then push check tasks / recolourings
+    bool want = false;
+    int push_item = 0;
+    if (t < cnt) {
+      if (assign) {
+        st_relaxed(I.color + v, colour);
+        want = true;
+        push_item = ~v;
+      } else if (sm.x.bits[2 * t + 1]) {
+        want = true;
+        push_item = v;
+      }
+    }
+    cta_push(sm, want, push_item);
+    __syncthreads();
+    if (t == 0) {
+      st[kStatTasks] += cnt;
+      st[kStatEdges] += edges;
+    }
+    cta_flush<BLOCK>(sm, I, cnt, L, st);
+  }
+
+  template <int BLOCK, class S>
+  __device__ static int cta_idle(S& sm, const Launch&, unsigned long long*) {
+    return threadIdx.x == 0 ? (instance_quiescent(sm.I) ? 1 : 0) : 0;
+  }
+
+  __device__ static void warp_item(WarpSmem& ws, const Instance& I, int item, const Launch& L,
+                                   unsigned long long* st) {
+    const int lane = threadIdx.x & 31;
+    const bool assign = item >= 0;
+    const int v = assign ? item : ~item;
+    const int s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
+    int64_t edges = 0;
+    if (assign) {
+      int colour = -1;
+      for (int base = 0; colour < 0; base += kGcWindow) {
+        unsigned lo = 0, hi = 0;
+        for (int k = s + lane; k < e; k += 32) {
+          const int rel = __ldcg(I.color + ldg(I.col + k)) - base;
+          if (rel >= 0 && rel < 32) lo |= 1u << rel;
+          else if (rel >= 32 && rel < 64) hi |= 1u << (rel - 32);
+        }
+        edges += e - s;
+        lo = __reduce_or_sync(0xffffffffu, lo);
+        hi = __reduce_or_sync(0xffffffffu, hi);
+        const unsigned long long used = ((unsigned long long)hi << 32) | lo;
+        if (~used) colour = base + __ffsll((long long)~used) - 1;
+      }
+      if (lane == 0) st_relaxed(I.color + v, colour);
+      __syncwarp();
+      warp_push(ws, lane == 0, ~v);
+    } else {
+      int cv = 0;
+      if (lane == 0) cv = __ldcg(I.color + v);
+      cv = __shfl_sync(0xffffffffu, cv, 0);
+      bool conflict = false;
+      for (int k = s + lane; k < e; k += 32) {
+        const int nb = ldg(I.col + k);
+        conflict |= nb < v && __ldcg(I.color + nb) == cv;
+      }
+      edges += e - s;
+      conflict = __any_sync(0xffffffffu, conflict);
+      warp_push(ws, lane == 0 && conflict, v);
+    }
+    warp_maybe_flush(ws, I, L, st);
+    if (lane == 0) st[kStatEdges] += edges;
+  }
+
+  __device__ static int warp_idle(WarpSmem&, const Instance& I, const Launch&, unsigned long long*) {
+    return (threadIdx.x & 31) == 0 ? (instance_quiescent(I) ? 1 : 0) : 0;
+  }
+};
+
+const void* gc_persistent_kernel(int worker) { return persistent_kernel_ptr<GcBody>(worker); }
+const void* gc_discrete_kernel(int worker) { return discrete_kernel_ptr<GcBody>(worker); }
+
+__global__ void gc_max_kernel(const int32_t* color, int n, int* out) {
+  int m = -1;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) m = max(m, color[v]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m + 1);
+}
+
+cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s) {
+  cudaMemsetAsync(&d_ctl->num_colors, 0, sizeof(int), s);
+  int gx = (h_inst->n + 255) / 256;
+  gx = gx < 1 ? 1 : (gx > 2048 ? 2048 : gx);
+  gc_max_kernel<<<gx, 256, 0, s>>>(h_inst->color, h_inst->n, &d_ctl->num_colors);
+  return cudaGetLastError();
+}
+
+}  // namespace atos

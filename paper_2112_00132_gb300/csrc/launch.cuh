@@ -1,0 +1,62 @@
+// launch.cuh -- host-side launch helpers for the worker engines (one instantiation per body).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "engine.cuh"
+
+namespace atos {
+
+// Worker shapes that are compiled: the warp worker (32) and CTA workers of 64 .. 1024 threads.
+inline bool worker_supported(int w) { return w == 32 || w == 64 || w == 128 || w == 256 || w == 512 || w == 1024; }
+
+template <class Body>
+const void* persistent_kernel_ptr(int worker) {
+  switch (worker) {
+    case 32: return (const void*)warp_persistent_kernel<Body>;
+    case 64: return (const void*)cta_persistent_kernel<Body, 64>;
+    case 128: return (const void*)cta_persistent_kernel<Body, 128>;
+    case 256: return (const void*)cta_persistent_kernel<Body, 256>;
+    case 512: return (const void*)cta_persistent_kernel<Body, 512>;
+    case 1024: return (const void*)cta_persistent_kernel<Body, 1024>;
+  }
+  return nullptr;
+}
+
+template <class Body>
+const void* discrete_kernel_ptr(int worker) {
+  switch (worker) {
+    case 32: return (const void*)warp_discrete_kernel<Body>;
+    case 64: return (const void*)cta_discrete_kernel<Body, 64>;
+    case 128: return (const void*)cta_discrete_kernel<Body, 128>;
+    case 256: return (const void*)cta_discrete_kernel<Body, 256>;
+    case 512: return (const void*)cta_discrete_kernel<Body, 512>;
+    case 1024: return (const void*)cta_discrete_kernel<Body, 1024>;
+  }
+  return nullptr;
+}
+
+inline int block_threads(int worker) { return worker == 32 ? kWarpBlock : worker; }
+
+// CTAs of this kernel that fit on the whole GPU at once (the persistent grid of Section 3.4).
+inline int resident_blocks(const void* fn, int threads) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess) return 0;
+  return per_sm * sms;
+}
+
+inline cudaError_t launch_kernel(const void* fn, dim3 grid, int threads, const Launch& L, cudaStream_t s) {
+  Launch copy = L;
+  void* args[] = {&copy};
+  return cudaLaunchKernel(fn, grid, dim3(threads), args, 0, s);
+}
+
+// Entry points each application translation unit defines.
+struct AppKernels {
+  const void* (*persistent)(int worker);
+  const void* (*discrete)(int worker);
+};
+
+}  // namespace atos

@@ -1,0 +1,127 @@
+// state.cu -- per-launch preparation and bookkeeping kernels shared by all applications.
+//
+//   prepare_kernel      resets every instance's queue control block and statistics, refills the
+//                       rings with EMPTY when the previous launch on this scratch failed (after a
+//                       clean run every slot is already EMPTY), and writes the initial state of
+//                       the application: BFS depth (INT32_MAX, source 0), PageRank rank = 1 -
+//                       alpha and the initial residue (one push of the initial rank, i.e.
+//                       (1 - alpha) alpha sum_{u in N(v)} 1/deg(u)), colouring colour = -1.
+//   next_generation     discrete strategy: the tasks pushed during the last launch become the
+//                       next generation; reports the largest generation over instances.
+//   finalize_kernel     remembers whether the launch failed (so the next prepare refills rings).
+#include "engine.cuh"
+#include "state.cuh"
+
+namespace atos {
+
+__global__ void prepare_kernel(Instance* insts, DevCtl* ctl, uint32_t flags, unsigned window) {
+  const Instance I = insts[blockIdx.y];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  if (ctl->dirty)
+    for (uint32_t k = tid; k < I.cap; k += stride) I.ring[k] = kFreeSlot;
+  if (tid == 0) {
+    QueueCtl* c = I.ctl;
+    const unsigned phantom = (flags & ATOS_FLAG_PHANTOM_TASK) ? 1u : 0u;
+    c->word = (unsigned long long)(I.prefix_len + phantom) << 32;
+    c->head = 0;
+    c->check = 0;
+    c->vword = 0;
+    c->vdone = 0;
+    c->finished = 0;
+    c->succ = -2;
+    c->gen_begin = 0;
+    c->gen_end = I.prefix_len;
+    for (int k = 0; k < kNumStats; ++k) I.stats[k] = 0;
+    if (blockIdx.y == 0) {
+      ctl->status = 0;
+      ctl->fail_site = 0;
+      ctl->next_inst = window;
+      ctl->maxgen = 0;
+    }
+  }
+  const int n = I.n;
+  switch (I.app) {
+    case kAppBfs:
+      for (int v = tid; v < n; v += stride) I.depth[v] = v == I.prefix_item ? 0 : kUnreached;
+      break;
+    case kAppPr: {
+      const float a = I.alpha, base = (1.0f - I.alpha) * I.alpha;
+      for (int v = tid; v < n; v += stride) I.rank[v] = 1.0f - a;
+      const int words = (n + 31) >> 5;
+      for (int w = tid; w < words; w += stride) {
+        const int rem = n - (w << 5);
+        I.qbits[w] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+      }
+      // residue[v] = base * sum_{u in N(v)} 1/deg(u): a pull over v's row (the graph is
+      // symmetric); one warp per vertex so that hub rows are read with coalesced loads.
+      const int lane = threadIdx.x & 31;
+      const int gw = tid >> 5, nw = stride >> 5;
+      for (int v = gw; v < n; v += nw) {
+        const int s = __ldg(I.row_ptr + v), e = __ldg(I.row_ptr + v + 1);
+        float acc = 0.0f;
+#pragma unroll 4
+        for (int k = s + lane; k < e; k += 32) {
+          const int u = __ldg(I.col + k);
+          acc += 1.0f / (float)(__ldg(I.row_ptr + u + 1) - __ldg(I.row_ptr + u));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) I.res[v] = base * acc;
+      }
+      break;
+    }
+    case kAppGc:
+      for (int v = tid; v < n; v += stride) I.color[v] = -1;
+      break;
+  }
+}
+
+__global__ void next_generation_kernel(Instance* insts, int ninst, DevCtl* ctl) {
+  __shared__ unsigned red[32];
+  unsigned mx = 0;
+  for (int i = threadIdx.x; i < ninst; i += blockDim.x) {
+    QueueCtl* c = insts[i].ctl;
+    const unsigned tail = (unsigned)(c->word >> 32);
+    const unsigned b = c->gen_end;
+    c->gen_begin = b;
+    c->gen_end = tail;
+    c->head = b;  // tickets below b are consumed: the overflow check may reuse their slots
+    mx = max(mx, tail - b);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) ctl->maxgen = mx;
+  }
+}
+
+__global__ void finalize_kernel(DevCtl* ctl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctl->dirty = ctl->status != 0 ? 1 : 0;
+}
+
+cudaError_t launch_prepare(Instance* d_insts, int ninst, int max_n, DevCtl* d_ctl, uint32_t flags, unsigned window,
+                           cudaStream_t s) {
+  int per = (max_n + 255) / 256;
+  int gx = per < 1 ? 1 : (per > 1024 ? 1024 : per);
+  if (ninst > 65535) return cudaErrorInvalidValue;
+  prepare_kernel<<<dim3(gx, ninst), 256, 0, s>>>(d_insts, d_ctl, flags, window);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_next_generation(Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s) {
+  next_generation_kernel<<<1, 1024, 0, s>>>(d_insts, ninst, d_ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(DevCtl* d_ctl, cudaStream_t s) {
+  finalize_kernel<<<1, 32, 0, s>>>(d_ctl);
+  return cudaGetLastError();
+}
+
+}  // namespace atos

@@ -1,0 +1,34 @@
+// state.cuh -- declarations shared by the host API and the bookkeeping kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "engine.cuh"
+
+namespace atos {
+
+// Small device-side control block of one scratch area (mirrored to pinned host memory).
+struct alignas(128) DevCtl {
+  int status;          // first error of the last launch
+  int dirty;           // rings may hold stale items (the last launch failed, or never used)
+  unsigned next_inst;  // batched launch: next instance to start
+  unsigned maxgen;     // discrete strategy: largest generation
+  unsigned pushed;     // PageRank final sweep (discrete): items pushed
+  int num_colors;
+  int fail_site;       // first wait that timed out (kSite*), 0 if none
+  int pad[1];
+  double sum_rank;     // PageRank: FP64 sum of the ranks
+  double sum_res;      // PageRank: FP64 sum of the residues left
+  double cert_l1;      // PageRank: FP64 ||(1 - alpha) 1 + alpha P x - x||_1 on the exact scale
+  double pad2[1];
+};
+
+cudaError_t launch_prepare(Instance* d_insts, int ninst, int max_n, DevCtl* d_ctl, uint32_t flags, unsigned window,
+                           cudaStream_t s);
+cudaError_t launch_next_generation(Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
+cudaError_t launch_finalize(DevCtl* d_ctl, cudaStream_t s);
+
+const void* bfs_persistent_kernel(int worker);
+const void* bfs_discrete_kernel(int worker);
+
+}  // namespace atos

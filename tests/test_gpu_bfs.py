@@ -1,0 +1,121 @@
+"""BFS on the GPU against the serial oracle: depths must be bit-exact (Section 5.1: the speculative
+search reaches the exact hop distances whatever the pop order)."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from gpu_common import atos_lib, bfs_sources, configs, small_graphs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def atos():
+    return atos_lib()
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    return small_graphs()
+
+
+@pytest.mark.parametrize("gname", list(small_graphs().keys()))
+def test_bfs_bit_exact_all_configs(atos, graphs, gname):
+    g = graphs[gname]
+    srcs = bfs_sources(g)
+    refs = {s: oracle.bfs(g, s) for s in srcs}
+    with atos.Graph.from_csr(g) as G:
+        for cname, cfg in list(configs(atos).items()) + [("bsp", atos.queue_config("bsp"))]:
+            try:
+                depths, st = G.bfs(srcs, cfg=cfg)
+            except atos.AtosError as e:
+                pytest.fail(f"{gname}/{cname}: {e}; queues {G.queue_state(len(srcs))}")
+            d = depths.cpu().numpy()
+            assert st.status == 0, (cname, st.status)
+            for i, s in enumerate(srcs):
+                bad = np.flatnonzero(d[i] != refs[s])
+                assert bad.size == 0, f"{gname}/{cname} src {s}: {bad.size} depths differ, e.g. v{bad[0]} " \
+                                      f"gpu {d[i][bad[0]]} oracle {refs[s][bad[0]]}"
+
+
+def test_bfs_many_sources_windows(atos):
+    g = gg.rmat(12, 16, seed=1)
+    srcs = [int(x) for x in gg.sources(g, 40, seed=2)]
+    refs = np.stack([oracle.bfs(g, s) for s in srcs])
+    with atos.Graph.from_csr(g) as G:
+        for window in (1, 3, 16, 40):
+            for worker in (32, 256):
+                cfg = atos.queue_config(window=window, worker_size=worker, fetch_size=32 if worker == 32 else 256)
+                depths, st = G.bfs(srcs, cfg=cfg)
+                assert st.status == 0
+                assert np.array_equal(depths.cpu().numpy(), refs), (window, worker)
+
+
+def test_bfs_stats_consistent(atos):
+    g = gg.grid(64, 64, delete_frac=0.1, seed=1)
+    ref = oracle.bfs(g, 0)
+    reached = int((ref != oracle.UNREACHED).sum())
+    with atos.Graph.from_csr(g) as G:
+        _, st = G.bfs([0])
+        # every reached vertex is popped at least once; every pop but the source's was a push
+        assert st.tasks >= reached
+        assert st.pushes == st.tasks - 1
+        deg = g.degrees
+        assert st.edges >= int(deg[ref != oracle.UNREACHED].sum())
+        _, st = G.bfs([0], cfg=atos.queue_config("discrete-cta"))
+        assert st.iterations == ref[ref != oracle.UNREACHED].max() + 1  # one generation per level
+        assert st.tasks == reached  # level-synchronous: no overwork
+
+
+def test_bfs_device_csr_borrow(atos):
+    import torch
+    g = gg.rmat(10, 16, seed=5)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    with atos.Graph(rp, col, borrow=True) as G:
+        depths, _ = G.bfs([3])
+        assert np.array_equal(depths.cpu().numpy()[0], oracle.bfs(g, 3))
+    with atos.Graph(rp, col) as G:
+        depths, _ = G.bfs([3])
+        assert np.array_equal(depths.cpu().numpy()[0], oracle.bfs(g, 3))
+
+
+def test_bfs_invalid_arguments(atos):
+    g = gg.path(10)
+    with atos.Graph.from_csr(g) as G:
+        for bad in ([10], [-1], []):
+            with pytest.raises(atos.AtosError) as e:
+                G.bfs(bad)
+            assert e.value.status == atos.abi.ERR_INVALID_ARG
+        with pytest.raises(atos.AtosError) as e:
+            G.bfs([0], cfg=atos.queue_config(worker_size=96))
+        assert e.value.status == atos.abi.ERR_UNSUPPORTED
+        with pytest.raises(atos.AtosError) as e:
+            G.bfs([0], cfg=atos.queue_config(worker_size=64, fetch_size=128))
+        assert e.value.status == atos.abi.ERR_INVALID_ARG
+
+
+def test_bfs_full_size_grid_2048(atos):
+    """The 2048 x 2048 grid with 10% of edges deleted, BFS from the corner: bit-exact."""
+    g = gg.grid(2048, delete_frac=0.1, seed=1)
+    ref = oracle.bfs(g, 0)
+    with atos.Graph.from_csr(g) as G:
+        depths, st = G.bfs([0])
+        assert st.status == 0
+        assert np.array_equal(depths.cpu().numpy()[0], ref)
+
+
+def test_bfs_full_size_rmat22_64_sources(atos):
+    """RMAT scale 22, 64 seeded sources in one launch: four sampled sources bit-exact against the
+    oracle, every source checked by the hop-distance certificate."""
+    g = gg.rmat(22, 16, seed=1)
+    srcs = [int(x) for x in gg.sources(g, 64, seed=1)]
+    with atos.Graph.from_csr(g) as G:
+        depths, st = G.bfs(srcs)
+        assert st.status == 0
+        d = depths.cpu().numpy()
+    for i in (0, 21, 42, 63):
+        assert np.array_equal(d[i], oracle.bfs(g, srcs[i])), f"source {srcs[i]}"
+    for i in range(0, 64, 4):
+        assert oracle.bfs_certificate(g, srcs[i], d[i]) == (0, -1), f"source {srcs[i]}"

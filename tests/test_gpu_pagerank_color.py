@@ -1,0 +1,140 @@
+"""PageRank and colouring on the GPU against the oracle.
+
+PageRank (Section 5.2): the normalised FP32 result must be within L1 1e-4 of the FP64 fixed point,
+and the FP64 error bound the library reports must cover the actual distance.  Colouring
+(Section 5.3): several colourings are correct, so the test checks what is unique -- properness and
+the first-fit range 0 <= c(v) <= deg(v) -- and reports the colour count next to serial greedy."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from gpu_common import ALPHA, EPS, PR_L1_TOL, atos_lib, configs, small_graphs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def atos():
+    return atos_lib()
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    return small_graphs()
+
+
+def pr_reference(g):
+    x, _, _ = oracle.pagerank(g, ALPHA, 1e-13)
+    return x / x.sum()
+
+
+@pytest.mark.parametrize("gname", ["rmat12", "rmat11_del", "grid97x61_del", "star1000", "clique40", "two_parts",
+                                   "path300", "single", "isolated3"])
+def test_pagerank_all_configs(atos, graphs, gname):
+    g = graphs[gname]
+    ref = pr_reference(g)
+    with atos.Graph.from_csr(g) as G:
+        for cname, cfg in configs(atos).items():
+            try:
+                rank, st = G.pagerank(ALPHA, EPS, cfg=cfg)
+            except atos.AtosError as e:
+                pytest.fail(f"{gname}/{cname}: {e}; queues {G.queue_state(1)}")
+            assert st.status == 0, cname
+            q = rank.cpu().numpy().astype(np.float64)
+            l1 = np.abs(q - ref).sum()
+            assert l1 <= PR_L1_TOL, f"{gname}/{cname}: L1 {l1}"
+            assert abs(q.sum() - 1.0) < 1e-5
+            assert st.error_bound <= PR_L1_TOL, f"{gname}/{cname}: bound {st.error_bound}"
+            assert l1 <= st.error_bound * 1.0001 + 1e-12, f"{gname}/{cname}: L1 {l1} > bound {st.error_bound}"
+
+
+def test_pagerank_check_size_and_epsilon(atos):
+    g = gg.rmat(12, 16, seed=1)
+    ref = pr_reference(g)
+    with atos.Graph.from_csr(g) as G:
+        for cs in (1, 8, 128):
+            rank, st = G.pagerank(ALPHA, EPS, cfg=atos.queue_config(check_size=cs))
+            assert np.abs(rank.cpu().numpy() - ref).sum() <= PR_L1_TOL
+        # a loose epsilon still meets its own bound and does less work
+        _, tight = G.pagerank(ALPHA, 1e-9)
+        rank, loose = G.pagerank(ALPHA, 1e-5)
+        assert loose.edges < tight.edges
+        l1 = np.abs(rank.cpu().numpy() - ref).sum()
+        assert l1 <= loose.error_bound * 1.0001
+
+
+def test_pagerank_invalid(atos):
+    with atos.Graph.from_csr(gg.path(5)) as G:
+        for a in (0.0, 1.0, -0.5):
+            with pytest.raises(atos.AtosError):
+                G.pagerank(a, EPS)
+        with pytest.raises(atos.AtosError):
+            G.pagerank(ALPHA, 0.0)
+
+
+def test_pagerank_full_size_grid_2048(atos):
+    """FP32 push PageRank on the 2048^2 grid (10% deletion), eps 1e-9, against the FP64 oracle."""
+    g = gg.grid(2048, delete_frac=0.1, seed=1)
+    ref = pr_reference(g)
+    with atos.Graph.from_csr(g) as G:
+        rank, st = G.pagerank(ALPHA, EPS)
+    q = rank.cpu().numpy().astype(np.float64)
+    l1 = np.abs(q - ref).sum()
+    assert st.status == 0 and l1 <= PR_L1_TOL and l1 <= st.error_bound * 1.0001
+    # the CPU certificate agrees with the bound the library computed on the device
+    assert oracle.pr_error_bound(g, q / q.sum(), ALPHA) <= PR_L1_TOL
+
+
+@pytest.mark.parametrize("gname", list(small_graphs().keys()))
+def test_color_proper_all_configs(atos, graphs, gname):
+    g = graphs[gname]
+    _, greedy = oracle.greedy_color(g)
+    with atos.Graph.from_csr(g) as G:
+        for cname, cfg in configs(atos).items():
+            try:
+                colors, k, st = G.color(cfg=cfg)
+            except atos.AtosError as e:
+                pytest.fail(f"{gname}/{cname}: {e}; queues {G.queue_state(1)}")
+            assert st.status == 0, cname
+            c = colors.cpu().numpy()
+            code, bad, kk = oracle.check_coloring(g, c)
+            assert code == 0, f"{gname}/{cname}: code {code} at vertex {bad}"
+            assert k == kk == st.num_colors
+            # first fit never needs more than max degree + 1 colours
+            assert k <= int(g.degrees.max()) + 1
+
+
+def test_color_known_graphs(atos):
+    with atos.Graph.from_csr(gg.clique(17)) as G:
+        _, k, _ = G.color()
+        assert k == 17
+    with atos.Graph.from_csr(gg.grid(40, 30)) as G:
+        colors, k, _ = G.color()
+        assert 2 <= k <= 5 and oracle.check_coloring(gg.grid(40, 30), colors.cpu().numpy())[0] == 0
+    with atos.Graph.from_csr(gg.star(300)) as G:
+        _, k, _ = G.color()
+        assert k == 2
+
+
+def test_color_full_size_rmat22(atos):
+    g = gg.rmat(22, 16, seed=1)
+    _, greedy = oracle.greedy_color(g)
+    with atos.Graph.from_csr(g) as G:
+        colors, k, st = G.color()
+    code, bad, kk = oracle.check_coloring(g, colors.cpu().numpy())
+    assert st.status == 0 and code == 0 and k == kk
+    print(f"rmat22 colouring: {k} colours (serial greedy {greedy}), {st.tasks / g.n:.3f} tasks per vertex")
+
+
+def test_pagerank_full_size_rmat22_certificate(atos):
+    """RMAT 22 is too large for the FP64 power iteration in a test; the FP64 residual certificate
+    (computed on the CPU from the GPU result) bounds the distance to the fixed point instead."""
+    g = gg.rmat(22, 16, seed=1)
+    with atos.Graph.from_csr(g) as G:
+        rank, st = G.pagerank(ALPHA, EPS)
+    q = rank.cpu().numpy().astype(np.float64)
+    bound = oracle.pr_error_bound(g, q / q.sum(), ALPHA)
+    assert st.status == 0 and bound <= PR_L1_TOL and st.error_bound <= PR_L1_TOL
+    print(f"rmat22 pagerank: bound {bound:.3e} (device {st.error_bound:.3e}), {st.tasks} tasks, "
+          f"{st.edges} edge pushes, {st.ms:.1f} ms")
