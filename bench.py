@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the task-parallel scheduler on one or more GB300s.
+
+One step = the whole hot path on one resident scale-free graph (RMAT scale 22, edge factor 16,
+a, b, c = 0.57, 0.19, 0.19, seed 1): breadth-first search from 64 seeded sources in one batched
+persistent launch, FP32 push-residual PageRank (alpha 0.85, eps 1e-9) and speculative greedy
+colouring.  The metric is GTEPS over the step:
+
+  * BFS: undirected edges of the source's connected component, per source (Graph500 rule);
+  * PageRank: edge pushes performed (one per neighbour entry scattered to);
+  * colouring: neighbour entries scanned by the assign and check tasks.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl atos|reference]
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU (the single-graph
+path does not shard); rank 0 prints one JSON line.  ``--impl reference`` times the serial CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "GTEPS (batched BFS x64 + PageRank + colouring step)"
+UNIT = "GTEPS"
+ALPHA, EPS = 0.85, 1e-9
+NSRC = 64
+L2_BYTES = 129 * 2**20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="atos", choices=["atos", "reference"])
+    ap.add_argument("--scale", type=int, default=22, help="RMAT scale of the workload graph")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--worker", type=int, default=256)
+    ap.add_argument("--fetch", type=int, default=256)
+    return ap.parse_args()
+
+
+def workload(scale: int):
+    g = gg.rmat(scale, 16, 0.57, 0.19, 0.19, seed=1)
+    srcs = gg.sources(g, NSRC, seed=1)
+    return g, srcs
+
+
+def workload_config(g, args, extra=None):
+    cfg = {"workload": f"rmat{args.scale}_bfs{NSRC}_pagerank_color", "graph": f"RMAT scale {args.scale}, edge "
+           f"factor 16, a=0.57 b=0.19 c=0.19, seed 1, symmetrised, deduplicated", "n": g.n, "nnz": g.nnz,
+           "bfs_sources": NSRC, "alpha": ALPHA, "eps": EPS,
+           "l2": (f"inputs larger than L2: col is {g.nnz * 4 / 2**20:.0f} MiB vs 129 MiB L2 (no flush needed)"
+                  if 4 * g.nnz > L2_BYTES else "inputs smaller than L2 (not flushed between steps)")}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[4:8]):
+                if flag.lower() in ("active", "1", "0x1"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- atos arm
+
+def component_edges(depths, deg_t):
+    """Graph500 edge count per BFS: undirected edges with both ends reached (sum of reached
+    degrees / 2), from the depths on the device."""
+    import torch
+    reached = depths != 2**31 - 1
+    return (reached.to(torch.int64) * deg_t.unsqueeze(0)).sum(dim=1) // 2
+
+
+def run_atos(args, rank: int, world: int):
+    import torch
+
+    import paper_2112_00132_gb300 as atos
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    atos.build() if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    atos.lib()
+    g, srcs = workload(args.scale)
+    stream = torch.cuda.current_stream()
+    cfg = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch)
+    G = atos.Graph.from_csr(g, skip_validation=False)
+    depths = torch.empty((NSRC, g.n), dtype=torch.int32, device="cuda")
+    rank_t = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    colors = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    deg_t = torch.from_numpy(np.diff(g.row_ptr).astype(np.int64)).cuda()
+
+    # warm-up steps with statistics (synchronising), to count the work of a step
+    bfs_edges = pr_edges = gc_edges = 0
+    pr_tasks = 0
+    bfs_stats = pr_stats = gc_stats = None
+    for w in range(max(args.warmup, 3)):
+        _, bfs_stats = G.bfs(srcs, depths, cfg=cfg, stream=stream)
+        _, pr_stats = G.pagerank(ALPHA, EPS, rank_t, cfg=cfg, stream=stream)
+        _, ncol, gc_stats = G.color(colors, cfg=cfg, stream=stream)
+        pr_edges += pr_stats.edges
+        pr_tasks += pr_stats.tasks
+        gc_edges += gc_stats.edges
+    nw = max(args.warmup, 3)
+    pr_edges /= nw
+    pr_tasks /= nw
+    gc_edges /= nw
+    comp = component_edges(depths, deg_t)
+    bfs_edges = int(comp.sum().item())
+    reached_v = int((depths != 2**31 - 1).sum().item())
+    comp_nnz = 2 * bfs_edges
+
+    # timed steps: no statistics, no host synchronisation inside a step
+    ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)] for k in ("bfs", "pr", "gc")}
+    l0 = atos.kernel_launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clocks:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        step_ev = []
+        for s in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e3 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.bfs(srcs, depths, cfg=cfg, stream=stream, stats=False)
+            e1.record(stream)
+            G.pagerank(ALPHA, EPS, rank_t, cfg=cfg, stream=stream, stats=False)
+            e2.record(stream)
+            G.color(colors, cfg=cfg, stream=stream, stats=False)
+            e3.record(stream)
+            step_ev.append((e0, e1, e2, e3))
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    launches = atos.kernel_launches() - l0
+    total_ms = t_start.elapsed_time(t_end)
+    bfs_ms = [a.elapsed_time(b) for a, b, _, _ in step_ev]
+    pr_ms = [b.elapsed_time(c) for _, b, c, _ in step_ev]
+    gc_ms = [c.elapsed_time(d) for _, _, c, d in step_ev]
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_step = total_ms / args.steps
+    work = bfs_edges + pr_edges + gc_edges
+    value = world * work / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the call whose kernels take the most time)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    mean = lambda xs: sum(xs) / len(xs)  # noqa: E731
+    parts = {
+        # bytes per launch: PageRank 20 B per push + 8 B per edge push (a col read and a residue
+        # update); BFS 4 B per component entry + 12 B per vertex, per source; colouring 16 B per
+        # entry + 24 B per vertex (assign + check passes)
+        "pagerank_persistent": (mean(pr_ms), 20.0 * pr_tasks + 8.0 * pr_edges),
+        "bfs_persistent_batched": (mean(bfs_ms), NSRC * 12.0 * g.n + 4.0 * comp_nnz),
+        "color_persistent": (mean(gc_ms), 16.0 * g.nnz + 24.0 * g.n),
+    }
+    dom = max(parts, key=lambda k: parts[k][0])
+    dom_ms, dom_bytes = parts[dom]
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src, "traffic": None,
+                "algorithmic_bytes": dom_bytes, "launch_ms": round(dom_ms, 3)}
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32 (BFS, colouring) + f32 (PageRank)", "data": "synthetic",
+        "config": workload_config(g, args, {"worker_size": args.worker, "fetch_size": args.fetch,
+                                            "strategy": "persistent", "parallelism": f"replicas x{world}"}),
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "breakdown": {
+            "bfs_ms": round(mean(bfs_ms), 3), "pagerank_ms": round(mean(pr_ms), 3), "color_ms": round(mean(gc_ms), 3),
+            "bfs_gteps": round(bfs_edges / (mean(bfs_ms) * 1e-3) / 1e9, 3),
+            "pagerank_gteps": round(pr_edges / (mean(pr_ms) * 1e-3) / 1e9, 3),
+            "color_gteps": round(gc_edges / (mean(gc_ms) * 1e-3) / 1e9, 3),
+            "bfs_graph500_edges": bfs_edges, "bfs_reached_vertices": reached_v, "bfs_tasks": bfs_stats.tasks,
+            "pagerank_edge_pushes": pr_edges, "pagerank_tasks": pr_tasks,
+            "pagerank_error_bound": pr_stats.error_bound, "color_edges": gc_edges, "colors": int(ncol),
+        },
+        "clocks": clocks.summary(),
+    }
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(args, g, srcs, cfg, bfs_edges + pr_edges + gc_edges, world)
+    G.close()
+    return result
+
+
+def run_e2e(args, g, srcs, cfg, work, world):
+    """The same step through the public API from pinned host buffers: upload the CSR, run the
+    three calls, read the results back, destroy the graph."""
+    import torch
+
+    import paper_2112_00132_gb300 as atos
+    stream = torch.cuda.current_stream()
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    depths_h = torch.empty((NSRC, g.n), dtype=torch.int32).pin_memory()
+    rank_h = torch.empty(g.n, dtype=torch.float32).pin_memory()
+    colors_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    depths = torch.empty((NSRC, g.n), dtype=torch.int32, device="cuda")
+    rank_t = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    colors = torch.empty(g.n, dtype=torch.int32, device="cuda")
+
+    def step():
+        G = atos.Graph(rp_h.numpy(), col_h.numpy(), skip_validation=True, stream=stream)
+        G.bfs(srcs, depths, cfg=cfg, stream=stream, stats=False)
+        G.pagerank(ALPHA, EPS, rank_t, cfg=cfg, stream=stream, stats=False)
+        G.color(colors, cfg=cfg, stream=stream, stats=False)
+        depths_h.copy_(depths, non_blocking=True)
+        rank_h.copy_(rank_t, non_blocking=True)
+        colors_h.copy_(colors, non_blocking=True)
+        torch.cuda.synchronize()
+        G.close()
+
+    step()
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = (time.perf_counter() - t0) / steps
+    h2d = 4 * (g.n + 1) + 4 * g.nnz + 4 * NSRC
+    d2h = 4 * NSRC * g.n + 4 * g.n + 4 * g.n
+    return {"value": round(world * work / dt / 1e9, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 3),
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "note": "graph created from pinned host CSR (validation skipped: checked once before), "
+                    "results copied back to pinned host memory, inside the timed region"}
+
+
+# --------------------------------------------------------------------------- CPU oracle arm
+
+def oracle_sample(g, srcs, nbfs=1, sweeps=3, color=True):
+    """Serial oracle on a bounded sample of the step; returns (work in the metric's units, seconds)."""
+    import oracle
+    oracle.build()
+    deg = np.diff(g.row_ptr)
+    work = 0.0
+    t0 = time.perf_counter()
+    for s in srcs[:nbfs]:
+        d = oracle.bfs(g, int(s))
+        work += deg[d != oracle.UNREACHED].sum() / 2
+    if sweeps:
+        oracle.pagerank_sweeps(g, ALPHA, sweeps)
+        work += sweeps * g.nnz
+    if color:
+        oracle.greedy_color(g)
+        work += g.nnz
+    return work, time.perf_counter() - t0
+
+
+def cpu_baseline(g, srcs):
+    work, dt = oracle_sample(g, srcs, nbfs=2, sweeps=3, color=True)
+    return {"value": round(work / dt / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "serial C oracle, one thread: BFS from 2 of the 64 sources, 3 FP64 power-iteration "
+                      "sweeps (nnz edge operations each), one greedy colouring (nnz entries)",
+            "seconds": round(dt, 2), "host_cores": os.cpu_count()}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    g, srcs = workload(args.scale)
+    for _ in range(args.warmup):
+        oracle_sample(g, srcs, nbfs=1, sweeps=1, color=False)
+    works, times = [], []
+    for _ in range(args.steps):
+        w, dt = oracle_sample(g, srcs, nbfs=1, sweeps=2, color=True)
+        works.append(w)
+        times.append(dt)
+    value = sum(works) / sum(times) / 1e9
+    ms = 1e3 * sum(times) / len(times)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32 + f64", "data": "synthetic",
+            "config": workload_config(g, args, {"strategy": "serial CPU oracle"}),
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": "per step: BFS from one of the 64 sources, 2 FP64 power-iteration sweeps, "
+                                       "one greedy colouring"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_atos(args, rank, world)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            g, srcs = workload(args.scale)
+            res["cpu_baseline"] = cpu_baseline(g, srcs)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

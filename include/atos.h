@@ -160,6 +160,10 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
  * ATOS_ERR_INVALID_ARG if ninst exceeds the instances g's scratch holds. */
 int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint32_t* heads, int32_t* fail_site);
 
+/* Number of CUDA kernels this library has launched in this process (monotone counter, all
+ * threads, all devices); lets a caller count the launches of a region of its own program. */
+uint64_t atos_kernel_launches(void);
+
 /* Human-readable name of a status code (static storage). */
 const char* atos_status_string(int status);
 

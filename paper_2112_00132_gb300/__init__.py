@@ -8,12 +8,13 @@ Python binding.
 """
 from ._binding import (  # noqa: F401
     BSP, DISCRETE, FETCH_FIXED, FETCH_GREEDY, FETCH_SPREAD, FLAG_PHANTOM_TASK, PERSISTENT, UNREACHED, WORKER_WARP,
-    AtosError, Config, Graph, Stats, csr_validate, header_functions, lib, queue_config, status_string, version,
+    AtosError, Config, Graph, Stats, csr_validate, header_functions, kernel_launches, lib, queue_config, status_string,
+    version,
 )
 from . import _binding as abi  # noqa: F401
 
 
 def build(force: bool = False) -> str:
     """Compiles libatos.so for sm_103a (nvcc) and returns its path."""
-    from .build import build as _build
+    from .compile_lib import build as _build
     return _build(force=force)

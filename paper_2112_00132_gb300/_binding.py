@@ -102,6 +102,8 @@ def lib() -> ctypes.CDLL:
         L.atos_color.argtypes = [vp, vp, P(i32), P(Config), vp, P(Stats)]
         L.atos_debug_queue_state.argtypes = [vp, i32, vp, vp, P(i32)]
         L.atos_debug_queue_state.restype = ctypes.c_int
+        L.atos_kernel_launches.argtypes = []
+        L.atos_kernel_launches.restype = ctypes.c_uint64
         L.atos_status_string.argtypes = [ctypes.c_int]
         L.atos_status_string.restype = ctypes.c_char_p
         L.atos_version.restype = ctypes.c_char_p
@@ -117,6 +119,11 @@ def header_functions(path: str = HEADER) -> list[str]:
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(atos_\w+)\s*\(", text)) - {"atos_graph_t"})
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched so far in this process."""
+    return int(lib().atos_kernel_launches())
 
 
 def status_string(status: int) -> str:

@@ -22,6 +22,7 @@ cudaError_t pr_verify_sweep(Instance* d_insts, int ninst, int max_n, DevCtl* d_c
 cudaError_t pr_finish(Instance* d_insts, int ninst, int n, float alpha, DevCtl* d_ctl, bool certificate,
                       double exact_sum, cudaStream_t s);
 cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s);
+unsigned long long launches_so_far();
 int bsp_bfs(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t src, int32_t* depth, void* scratch,
             size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges);
 }  // namespace atos
@@ -622,5 +623,7 @@ int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint3
   }
   return ATOS_OK;
 }
+
+uint64_t atos_kernel_launches(void) { return (uint64_t)launches_so_far(); }
 
 }  // extern "C"

@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "bsp.cuh"
+#include "launch.cuh"
 
 namespace atos {
 namespace bsp {
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(kBlock) add_chunk_offsets(int32_t* offs, int32
 cudaError_t scan_degrees(const int32_t* frontier, int32_t F, const int32_t* row_ptr, int32_t* offs, int32_t* bsums,
                          cudaStream_t s) {
   const int nb = (F + kChunk - 1) / kChunk;
+  count_launches(3);
   degree_chunk_sums<<<nb, kBlock, 0, s>>>(frontier, F, row_ptr, offs, bsums);
   scan_chunk_sums<<<1, 1024, 0, s>>>(bsums, nb, offs, F);
   add_chunk_offsets<<<nb, kBlock, 0, s>>>(offs, F, bsums);
@@ -163,6 +165,7 @@ int bsp_bfs(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t src, 
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  count_launches(1);
   bfs_init<<<std::max(1, std::min(1024, (n + 255) / 256)), 256, 0, s>>>(depth, n, src, fa, count);
   int32_t F = 1, level = 0;
   int64_t iters = 0, ed = 0;
@@ -173,6 +176,7 @@ int bsp_bfs(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t src, 
       break;
     }
     cudaMemsetAsync(count, 0, sizeof(int32_t), s);
+    count_launches(1);
     bfs_advance<<<sms * 8, kBlock, 0, s>>>(fa, F, offs, row_ptr, col, depth, level + 1, fb, count);
     int32_t tot = 0;
     cudaMemcpyAsync(hcount, count, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

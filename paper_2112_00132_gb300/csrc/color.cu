@@ -185,6 +185,7 @@ cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s) {
   cudaMemsetAsync(&d_ctl->num_colors, 0, sizeof(int), s);
   int gx = (h_inst->n + 255) / 256;
   gx = gx < 1 ? 1 : (gx > 2048 ? 2048 : gx);
+  count_launches(1);
   gc_max_kernel<<<gx, 256, 0, s>>>(h_inst->color, h_inst->n, &d_ctl->num_colors);
   return cudaGetLastError();
 }

@@ -47,9 +47,13 @@ inline int resident_blocks(const void* fn, int threads) {
   return per_sm * sms;
 }
 
+// Kernels this library has launched (all launch sites add to it; read by atos_kernel_launches).
+void count_launches(unsigned n);
+
 inline cudaError_t launch_kernel(const void* fn, dim3 grid, int threads, const Launch& L, cudaStream_t s) {
   Launch copy = L;
   void* args[] = {&copy};
+  count_launches(1);
   return cudaLaunchKernel(fn, grid, dim3(threads), args, 0, s);
 }
 

@@ -287,6 +287,7 @@ __global__ void pr_sweep_kernel(Instance* insts, int* status) {
 cudaError_t pr_verify_sweep(Instance* d_insts, int ninst, int max_n, DevCtl* d_ctl, cudaStream_t s) {
   int gx = (max_n + 255) / 256;
   gx = gx < 1 ? 1 : (gx > 2048 ? 2048 : gx);
+  count_launches(1);
   pr_sweep_kernel<<<dim3(gx, ninst), 256, 0, s>>>(d_insts, &d_ctl->status);
   return cudaGetLastError();
 }
@@ -347,6 +348,7 @@ cudaError_t pr_finish(Instance* d_insts, int ninst, int n, float alpha, DevCtl* 
   cudaMemsetAsync(&d_ctl->sum_rank, 0, 3 * sizeof(double), s);
   int gx = (n + 255) / 256;
   gx = gx < 1 ? 1 : (gx > 2048 ? 2048 : gx);
+  count_launches(certificate ? 3 : 2);
   pr_sums_kernel<<<gx, 256, 0, s>>>(d_insts, d_ctl);
   if (certificate) pr_certificate_kernel<<<gx, 256, 0, s>>>(d_insts, d_ctl, exact_sum);
   pr_normalise_kernel<<<gx, 256, 0, s>>>(d_insts, d_ctl);

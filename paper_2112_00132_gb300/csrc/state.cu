@@ -9,10 +9,17 @@
 //   next_generation     discrete strategy: the tasks pushed during the last launch become the
 //                       next generation; reports the largest generation over instances.
 //   finalize_kernel     remembers whether the launch failed (so the next prepare refills rings).
+#include <atomic>
+
 #include "engine.cuh"
+#include "launch.cuh"
 #include "state.cuh"
 
 namespace atos {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 __global__ void prepare_kernel(Instance* insts, DevCtl* ctl, uint32_t flags, unsigned window) {
   const Instance I = insts[blockIdx.y];
@@ -110,16 +117,19 @@ cudaError_t launch_prepare(Instance* d_insts, int ninst, int max_n, DevCtl* d_ct
   int per = (max_n + 255) / 256;
   int gx = per < 1 ? 1 : (per > 1024 ? 1024 : per);
   if (ninst > 65535) return cudaErrorInvalidValue;
+  count_launches(1);
   prepare_kernel<<<dim3(gx, ninst), 256, 0, s>>>(d_insts, d_ctl, flags, window);
   return cudaGetLastError();
 }
 
 cudaError_t launch_next_generation(Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s) {
+  count_launches(1);
   next_generation_kernel<<<1, 1024, 0, s>>>(d_insts, ninst, d_ctl);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(DevCtl* d_ctl, cudaStream_t s) {
+  count_launches(1);
   finalize_kernel<<<1, 32, 0, s>>>(d_ctl);
   return cudaGetLastError();
 }
