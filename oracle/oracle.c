@@ -136,9 +136,11 @@ static double* inverse_degrees(const int32_t* row_ptr, int32_t n) {
 }
 
 /* FP64 Jacobi power iteration x <- (1 - alpha) 1 + alpha P x from x = 1, until
- * ||x_new - x||_1 <= tol_per_vertex * n or max_iter sweeps.  x_out is on the unnormalised scale
- * (sum ~ n); divide by its sum for the probability vector.  Returns 0, or 1 if max_iter was hit,
- * or -1 on bad arguments.  *iters and *last_delta report the sweeps and the final step size. */
+ * ||x_new - x||_1 <= tol_per_vertex * n, or until the step has reached the FP64 rounding floor
+ * (it is below 1e-9 per vertex and has not decreased for 3 sweeps; in exact arithmetic it shrinks
+ * by at least alpha per sweep), or max_iter sweeps.  x_out is on the unnormalised scale (sum ~ n);
+ * divide by its sum for the probability vector.  Returns 0, or 1 if max_iter was hit, or -1 on
+ * bad arguments.  *iters and *last_delta report the sweeps and the final step size. */
 int oracle_pagerank(const int32_t* row_ptr, const int32_t* col, int32_t n, double alpha, double tol_per_vertex,
                     int32_t max_iter, double* x_out, int32_t* iters, double* last_delta) {
   if (!row_ptr || !x_out || n < 1 || !(alpha >= 0.0 && alpha < 1.0) || max_iter < 1) return -1;
@@ -151,8 +153,8 @@ int oracle_pagerank(const int32_t* row_ptr, const int32_t* col, int32_t n, doubl
   }
   for (int32_t v = 0; v < n; ++v) x_out[v] = 1.0;
   int rc = 1;
-  int32_t it = 0;
-  double delta = INFINITY;
+  int32_t it = 0, flat = 0;
+  double delta = INFINITY, prev = INFINITY;
   while (it < max_iter) {
     pr_apply(row_ptr, col, n, alpha, x_out, inv, y, scratch);
     delta = 0.0;
@@ -163,6 +165,12 @@ int oracle_pagerank(const int32_t* row_ptr, const int32_t* col, int32_t n, doubl
       rc = 0;
       break;
     }
+    flat = (delta <= 1e-9 * (double)n && delta >= prev) ? flat + 1 : 0;
+    if (flat >= 3) {
+      rc = 0;
+      break;
+    }
+    prev = delta;
   }
   if (iters) *iters = it;
   if (last_delta) *last_delta = delta;

@@ -27,7 +27,7 @@ def summary(g, sources):
         reached = d[d != oracle.UNREACHED]
         out["bfs"][str(int(s))] = {"reached": int(reached.size),
                                    "depth_histogram": np.bincount(reached).tolist()}
-    x, sweeps, _ = oracle.pagerank(g, 0.85, 1e-13)
+    x, sweeps, _ = oracle.pagerank(g, 0.85)
     q = x / x.sum()
     top = np.argsort(-q, kind="stable")[:8]
     out["pagerank"] = {"alpha": 0.85, "sum_unnormalised": float(x.sum()),

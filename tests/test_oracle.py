@@ -297,9 +297,19 @@ def test_golden_regression(fname, maker):
         r = d[d != UNR]
         assert r.size == info["reached"]
         assert np.bincount(r).tolist() == info["depth_histogram"]
-    x, _, _ = oracle.pagerank(g, 0.85, 1e-13)
+    x, _, _ = oracle.pagerank(g, 0.85)
     assert x.sum() == pytest.approx(ref["pagerank"]["sum_unnormalised"], rel=1e-12)
     q = x / x.sum()
     for v, val in ref["pagerank"]["top"]:
         assert q[v] == pytest.approx(val, rel=1e-10)
     assert oracle.greedy_color(g)[1] == ref["greedy_colors"]
+
+
+def test_pr_rounding_floor_stop():
+    """On a large star the FP64 step cannot fall below 1e-13 per vertex (the centre holds ~n/2);
+    the iteration must still stop, at the rounding floor, with the closed-form values."""
+    k = 1000
+    x, sweeps, last = oracle.pagerank(gg.star(k), ALPHA)
+    centre = (1 + ALPHA * k) / (1 + ALPHA)
+    assert x[0] == pytest.approx(centre, rel=1e-12)
+    assert np.allclose(x[1:], (1 - ALPHA) + ALPHA * centre / k, rtol=1e-12)
