@@ -147,9 +147,13 @@ int ensure_scratch(atos_graph_s* g, int ninst, uint32_t cap) {
   return ATOS_OK;
 }
 
+// Ring slots per instance.  Besides the tasks in flight the ring must cover the span between the
+// oldest ticket a busy worker has not taken yet and the tail, so small graphs get a floor of 2^20
+// slots (8 MiB); large ones 1.5 n plus the virtual prefix.
 uint32_t ring_capacity(const atos_config& cfg, int32_t n, uint32_t prefix) {
-  uint64_t want = cfg.queue_capacity > 0 ? (uint64_t)cfg.queue_capacity : (uint64_t)2 * n + prefix + 1024;
-  return next_pow2(std::max<uint64_t>(want, 1024));
+  if (cfg.queue_capacity > 0) return next_pow2(std::max<uint64_t>((uint64_t)cfg.queue_capacity, 1024));
+  const uint64_t want = (uint64_t)n + (uint64_t)n / 2 + prefix + 1024;
+  return next_pow2(std::max<uint64_t>(want, 1u << 20));
 }
 
 int check_config(const atos_config& c) {

@@ -3,15 +3,18 @@
 // One uberkernel handles two kinds of task, told apart by the sign of the item:
 //   * item v >= 0 (assign): read the colours of v's neighbours, give v the smallest colour none
 //     of them holds (first fit; the colour is at most deg(v)), then push the check task ~v;
-//   * item ~v < 0 (check): if a neighbour u < v holds v's colour, push v to recolour it.
-// Because only the larger id of a conflicting pair recolours, the smallest id of any conflict
-// keeps its colour and the recolouring cannot cycle; when the queue drains, every vertex's last
-// check ran after its last colour change, so the colouring is proper.  The check task is encoded
-// as ~v = -v - 1 so that vertex 0 has a distinct check task.
+//   * item ~v < 0 (check): for every neighbour u holding v's colour, the larger of u and v must
+//     recolour: push v itself (once) if some u < v, and push u for each such u > v.
+// Only the larger id of a conflicting pair recolours, so the smallest id of any conflict keeps its
+// colour.  Pushing the larger endpoint from the smaller one's check closes the race in which the
+// smaller vertex's assign read a stale colour and wrote its own after the larger vertex's last
+// check.  The check task is encoded as ~v = -v - 1 so that vertex 0 has a distinct check task.
 //
-// Colours are read from L2 (ld.global.cg) so a worker sees other workers' recent writes; a colour
-// is written before the check task is published, and the publication is ordered after it by a
-// device-scope fence.
+// Memory ordering: an assign writes its colour and then executes a sequentially consistent
+// device fence; a check executes the same fence before it reads any colour.  For two adjacent
+// vertices x and y this is the store-buffering pattern W(x); fence; R(y) against W(y); fence;
+// R(x), so at least one of the two checks that follow their final writes sees the other's colour,
+// and the conflict is found.  Colours are read from L2 (ld.global.cg).
 #include "engine.cuh"
 #include "launch.cuh"
 #include "state.cuh"
@@ -51,6 +54,8 @@ struct GcBody {
         sm.x.bits[2 * t + 1] = 0u;
       }
     }
+    __threadfence();  // order every earlier colour write of this CTA before the checks' reads
+    __syncthreads();
     int64_t edges = 0;
     int colour = -1;  // result of an assign item (thread t)
     // pass 0 runs every item; later passes only assign items that found no free colour in the
@@ -67,19 +72,25 @@ struct GcBody {
       __syncthreads();
       for (int r = 0; r < total; r += BLOCK) {
         const int e = r + t;
+        bool push_nb = false;
+        int nb = 0;
         if (e < total) {
           const int i = owner_of(sm.off, cnt, e);
-          const int nb = ldg(I.col + sm.start[i] + (e - sm.off[i]));
+          nb = ldg(I.col + sm.start[i] + (e - sm.off[i]));
           const int c = __ldcg(I.color + nb);
           const int item = sm.aux[i];
           if (item >= 0) {
             const int rel = c - base;
             if (rel >= 0 && rel < kGcWindow) atomicOr(&sm.x.bits[2 * i + (rel >> 5)], 1u << (rel & 31));
-          } else if (nb < ~item && c == (int)sm.x.bits[2 * i]) {
-            sm.x.bits[2 * i + 1] = 1u;
+          } else if (c == (int)sm.x.bits[2 * i] && nb != ~item) {
+            if (nb < ~item) sm.x.bits[2 * i + 1] = 1u;  // v is the larger: v recolours
+            else push_nb = true;                        // the neighbour is the larger: it recolours
           }
         }
+        cta_push(sm, push_nb, nb);
+        if (r + BLOCK < total) cta_maybe_flush<BLOCK>(sm, I, L, st);
       }
+      cta_maybe_flush<BLOCK>(sm, I, L, st);
       edges += total;
       __syncthreads();
       bool again = false;
@@ -103,6 +114,7 @@ struct GcBody {
     if (t < cnt) {
       if (assign) {
         st_relaxed(I.color + v, colour);
+        __threadfence();  // the colour is visible before the check task can be taken
         want = true;
         push_item = ~v;
       } else if (sm.x.bits[2 * t + 1]) {
@@ -146,17 +158,31 @@ struct GcBody {
         const unsigned long long used = ((unsigned long long)hi << 32) | lo;
         if (~used) colour = base + __ffsll((long long)~used) - 1;
       }
-      if (lane == 0) st_relaxed(I.color + v, colour);
+      if (lane == 0) {
+        st_relaxed(I.color + v, colour);
+        __threadfence();  // the colour is visible before the check task can be taken
+      }
       __syncwarp();
       warp_push(ws, lane == 0, ~v);
     } else {
+      __threadfence();  // store-buffering pattern with the assign's fence (see the file comment)
       int cv = 0;
       if (lane == 0) cv = __ldcg(I.color + v);
       cv = __shfl_sync(0xffffffffu, cv, 0);
       bool conflict = false;
-      for (int k = s + lane; k < e; k += 32) {
-        const int nb = ldg(I.col + k);
-        conflict |= nb < v && __ldcg(I.color + nb) == cv;
+      for (int k = s; k < e; k += 32) {
+        const int j = k + lane;
+        bool larger = false;
+        int nb = 0;
+        if (j < e) {
+          nb = ldg(I.col + j);
+          if (nb != v && __ldcg(I.color + nb) == cv) {
+            if (nb < v) conflict = true;
+            else larger = true;
+          }
+        }
+        warp_push(ws, larger, nb);  // the larger neighbour recolours
+        warp_maybe_flush(ws, I, L, st);
       }
       edges += e - s;
       conflict = __any_sync(0xffffffffu, conflict);

@@ -25,7 +25,7 @@ def graphs():
 
 
 def pr_reference(g):
-    x, _, _ = oracle.pagerank(g, ALPHA, 1e-13)
+    x, _, _ = oracle.pagerank(g, ALPHA)
     return x / x.sum()
 
 
