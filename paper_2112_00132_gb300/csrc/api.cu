@@ -537,10 +537,8 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   if (!cap) return ATOS_ERR_INVALID_ARG;
   rc = ensure_scratch(g, 1, cap);
   if (rc) return rc;
-  if (!g->d_res) {
-    ATOS_TRY(dev_alloc(&g->d_res, (size_t)n));
-    ATOS_TRY(dev_alloc(&g->d_qbits, (size_t)(n + 31) / 32));
-  }
+  if (!g->d_res) ATOS_TRY(dev_alloc(&g->d_res, (size_t)n));
+  if (!g->d_qbits) ATOS_TRY(dev_alloc(&g->d_qbits, (size_t)(n + 31) / 32));
   Instance I = base_instance(g, 0, kAppPr, cap, (uint32_t)n, -1);
   I.rank = rank;
   I.res = g->d_res;
@@ -587,8 +585,10 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   if (!cap) return ATOS_ERR_INVALID_ARG;
   rc = ensure_scratch(g, 1, cap);
   if (rc) return rc;
+  if (!g->d_qbits) ATOS_TRY(dev_alloc(&g->d_qbits, (size_t)(n + 31) / 32));
   Instance I = base_instance(g, 0, kAppGc, cap, (uint32_t)n, -1);
   I.color = colors;
+  I.qbits = g->d_qbits;
   g->s.h_insts[0] = I;
   cfg.window = 1;
   ATOS_TRY(cudaEventRecord(g->s.ev0, st));

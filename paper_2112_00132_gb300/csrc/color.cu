@@ -6,7 +6,9 @@
 //   * item ~v < 0 (check): for every neighbour u holding v's colour, the larger of u and v must
 //     recolour: push v itself (once) if some u < v, and push u for each such u > v.
 // Only the larger id of a conflicting pair recolours, so the smallest id of any conflict keeps its
-// colour.  Pushing the larger endpoint from the smaller one's check closes the race in which the
+// colour.  A vertex has at most one assign task queued: a bitmap bit is set by whoever queues the
+// assign and cleared when it is popped, before the neighbours' colours are read (a request that
+// finds the bit set is covered by the pending assign, which will read the newer colours).  Pushing the larger endpoint from the smaller one's check closes the race in which the
 // smaller vertex's assign read a stale colour and wrote its own after the larger vertex's last
 // check.  The check task is encoded as ~v = -v - 1 so that vertex 0 has a distinct check task.
 //
@@ -29,6 +31,12 @@ struct GcExtra {
   int pass_base;
 };
 
+// Queues an assign task for u unless one is already queued.
+__device__ __forceinline__ bool gc_claim_assign(const Instance& I, int u) {
+  const unsigned bit = 1u << (u & 31);
+  return !(atomicOr(I.qbits + (u >> 5), bit) & bit);
+}
+
 struct GcBody {
   using Extra = GcExtra;
 
@@ -47,6 +55,7 @@ struct GcBody {
       sm.start[t] = s;
       sm.aux[t] = item;
       if (assign) {
+        atomicAnd(I.qbits + (v >> 5), ~(1u << (v & 31)));  // requests from now on queue a new assign
         sm.x.bits[2 * t] = 0u;
         sm.x.bits[2 * t + 1] = 0u;
       } else {
@@ -83,8 +92,8 @@ struct GcBody {
             const int rel = c - base;
             if (rel >= 0 && rel < kGcWindow) atomicOr(&sm.x.bits[2 * i + (rel >> 5)], 1u << (rel & 31));
           } else if (c == (int)sm.x.bits[2 * i] && nb != ~item) {
-            if (nb < ~item) sm.x.bits[2 * i + 1] = 1u;  // v is the larger: v recolours
-            else push_nb = true;                        // the neighbour is the larger: it recolours
+            if (nb < ~item) sm.x.bits[2 * i + 1] = 1u;        // v is the larger: v recolours
+            else push_nb = gc_claim_assign(I, nb);            // the neighbour is the larger
           }
         }
         cta_push(sm, push_nb, nb);
@@ -117,7 +126,7 @@ struct GcBody {
         __threadfence();  // the colour is visible before the check task can be taken
         want = true;
         push_item = ~v;
-      } else if (sm.x.bits[2 * t + 1]) {
+      } else if (sm.x.bits[2 * t + 1] && gc_claim_assign(I, v)) {
         want = true;
         push_item = v;
       }
@@ -144,6 +153,8 @@ struct GcBody {
     const int s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
     int64_t edges = 0;
     if (assign) {
+      if (lane == 0) atomicAnd(I.qbits + (v >> 5), ~(1u << (v & 31)));
+      __syncwarp();
       int colour = -1;
       for (int base = 0; colour < 0; base += kGcWindow) {
         unsigned lo = 0, hi = 0;
@@ -178,7 +189,7 @@ struct GcBody {
           nb = ldg(I.col + j);
           if (nb != v && __ldcg(I.color + nb) == cv) {
             if (nb < v) conflict = true;
-            else larger = true;
+            else larger = gc_claim_assign(I, nb);
           }
         }
         warp_push(ws, larger, nb);  // the larger neighbour recolours
@@ -186,7 +197,7 @@ struct GcBody {
       }
       edges += e - s;
       conflict = __any_sync(0xffffffffu, conflict);
-      warp_push(ws, lane == 0 && conflict, v);
+      warp_push(ws, lane == 0 && conflict && gc_claim_assign(I, v), v);
     }
     warp_maybe_flush(ws, I, L, st);
     if (lane == 0) st[kStatEdges] += edges;

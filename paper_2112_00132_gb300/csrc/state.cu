@@ -78,9 +78,15 @@ __global__ void prepare_kernel(Instance* insts, DevCtl* ctl, uint32_t flags, uns
       }
       break;
     }
-    case kAppGc:
+    case kAppGc: {
       for (int v = tid; v < n; v += stride) I.color[v] = -1;
+      const int words = (n + 31) >> 5;  // every vertex starts with its assign task queued
+      for (int w = tid; w < words; w += stride) {
+        const int rem = n - (w << 5);
+        I.qbits[w] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+      }
       break;
+    }
   }
 }
 
