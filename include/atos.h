@@ -164,6 +164,30 @@ int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint3
  * threads, all devices); lets a caller count the launches of a region of its own program. */
 uint64_t atos_kernel_launches(void);
 
+/* ------------------------------------------------------------------ allocation-free BFS */
+
+/* Largest graph atos_bfs_noalloc accepts (its fixed ring holds 2^19 slots). */
+#define ATOS_NOALLOC_MAX_VERTICES 262144
+
+/* Single-source BFS (same result as atos_bfs) that allocates no memory, for callers that must
+ * not call cudaMalloc: code living inside an application whose own allocator owns the device
+ * memory, plug-ins forbidden to allocate, or latency-critical loops that cannot pay the device
+ * synchronisation an allocation may imply.  The paper has no counterpart of this entry point.
+ *   row_ptr, col: DEVICE int32 CSR of an undirected graph (n + 1 and nnz entries), unchanged
+ *   during the call; source in [0, n); depth: DEVICE int32[n] receiving the hop distances
+ *   (INT32_MAX outside the source's component).
+ * Scratch: one fixed array of about 4.1 MiB of device memory inside the library image, held by
+ * every GPU that loads the library until the process exits, and shared by all calls on that GPU.
+ * The first call on a device obtains the array's device address (cudaGetSymbolAddress) and
+ * initialises it; make that first call before any stream capture.  Calls that overlap on the
+ * GPU (other streams, other host threads) race on the shared scratch and must be serialised by
+ * the caller.  The call synchronises `stream` and returns the device status (ATOS_OK,
+ * ATOS_ERR_TIMEOUT, ATOS_ERR_QUEUE_OVERFLOW) or ATOS_ERR_CUDA; it returns ATOS_ERR_INVALID_ARG
+ * for NULL pointers, a source out of range, or n < 1 or n > ATOS_NOALLOC_MAX_VERTICES (checked
+ * before any GPU work). */
+int atos_bfs_noalloc(const int32_t* row_ptr, const int32_t* col, int32_t n, int64_t nnz, int32_t source,
+                     int32_t* depth, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* atos_status_string(int status);
 

@@ -102,6 +102,8 @@ def lib() -> ctypes.CDLL:
         L.atos_color.argtypes = [vp, vp, P(i32), P(Config), vp, P(Stats)]
         L.atos_debug_queue_state.argtypes = [vp, i32, vp, vp, P(i32)]
         L.atos_debug_queue_state.restype = ctypes.c_int
+        L.atos_bfs_noalloc.argtypes = [vp, vp, i32, i64, i32, vp, vp]
+        L.atos_bfs_noalloc.restype = ctypes.c_int
         L.atos_kernel_launches.argtypes = []
         L.atos_kernel_launches.restype = ctypes.c_uint64
         L.atos_status_string.argtypes = [ctypes.c_int]
