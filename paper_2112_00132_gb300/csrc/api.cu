@@ -19,7 +19,7 @@ const void* pr_discrete_kernel(int worker);
 const void* gc_persistent_kernel(int worker);
 const void* gc_discrete_kernel(int worker);
 cudaError_t pr_verify_sweep(Instance* d_insts, int ninst, int max_n, DevCtl* d_ctl, cudaStream_t s);
-cudaError_t pr_finish(Instance* d_insts, int ninst, int n, float alpha, DevCtl* d_ctl, bool certificate,
+cudaError_t pr_finish(Instance* d_insts, int ninst, int n, int64_t nnz, DevCtl* d_ctl, double* certificate_y,
                       double exact_sum, cudaStream_t s);
 cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s);
 unsigned long long launches_so_far();
@@ -98,6 +98,7 @@ struct atos_graph_s {
   // application state that is not a caller output
   float* d_res = nullptr;
   uint32_t* d_qbits = nullptr;
+  double* d_cert = nullptr;  // PageRank FP64 certificate scratch (n entries)
   void* d_bsp = nullptr;  // BSP comparator frontiers and scan space
   size_t bsp_bytes = 0;
 };
@@ -213,6 +214,7 @@ int run_instances(atos_graph_s* g, int ninst, int max_n, const atos_config& cfg,
   int rc = upload_instances(s, ninst, st);
   if (rc) return rc;
   ATOS_TRY(launch_prepare(s.d_insts, ninst, max_n, s.d_ctl, cfg.flags, (unsigned)window, st));
+  if (app == kAppPr) ATOS_TRY(launch_pr_init(s.d_insts, ninst, g->nnz, st));
   int64_t iters = 0;
   if (cfg.strategy == ATOS_PERSISTENT) {
     const void* fn = kp(worker);
@@ -428,7 +430,7 @@ int atos_graph_destroy(atos_graph_t g) {
   if (!g) return ATOS_OK;
   cudaDeviceSynchronize();
   if (g->owned) cudaFree(g->row_ptr), cudaFree(g->col);
-  cudaFree(g->d_res), cudaFree(g->d_qbits), cudaFree(g->d_bsp);
+  cudaFree(g->d_res), cudaFree(g->d_qbits), cudaFree(g->d_bsp), cudaFree(g->d_cert);
   g->s.release();
   delete g;
   return ATOS_OK;
@@ -553,7 +555,8 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   int64_t iters = 0;
   rc = run_instances(g, 1, n, cfg, pr_persistent_kernel, pr_discrete_kernel, kAppPr, st, &iters);
   if (rc) return rc;
-  ATOS_TRY(pr_finish(g->s.d_insts, 1, n, alpha, g->s.d_ctl, stats != nullptr, exact_sum, st));
+  if (stats && !g->d_cert) ATOS_TRY(dev_alloc(&g->d_cert, (size_t)n));
+  ATOS_TRY(pr_finish(g->s.d_insts, 1, n, g->nnz, g->s.d_ctl, stats ? g->d_cert : nullptr, exact_sum, st));
   ATOS_TRY(cudaEventRecord(g->s.ev1, st));
   if (stats) {
     rc = collect_stats(g, 1, st, stats);

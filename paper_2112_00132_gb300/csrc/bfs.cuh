@@ -27,19 +27,22 @@ struct BfsBody {
     if ((int)threadIdx.x < cnt) sm.off[threadIdx.x] = off;
     __syncthreads();
     int32_t* __restrict__ depth = I.depth;
-    const int32_t* __restrict__ col = I.col;
-    for (int base = 0; base < total; base += BLOCK) {
-      const int e = base + threadIdx.x;
-      bool want = false;
-      int nb = 0;
-      if (e < total) {
-        const int i = owner_of(sm.off, cnt, e);
-        nb = ldg(col + sm.start[i] + (e - sm.off[i]));
-        const int nd = sm.aux[i];
-        if (nd < __ldcg(depth + nb)) want = nd < atomicMin(depth + nb, nd);
+    constexpr int R = LbsRun<BLOCK>::R;
+    for (int base = 0; base < total; base += BLOCK * R) {
+      int item[R], nb[R], cur[R];
+      lbs_round<BLOCK>(sm, I.col, cnt, total, base, item, nb);
+#pragma unroll
+      for (int j = 0; j < R; ++j) cur[j] = item[j] >= 0 ? __ldcg(depth + nb[j]) : 0;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        bool want = false;
+        if (item[j] >= 0) {
+          const int nd = sm.aux[item[j]];
+          if (nd < cur[j]) want = nd < atomicMin(depth + nb[j], nd);
+        }
+        cta_push(sm, want, nb[j]);
       }
-      cta_push(sm, want, nb);
-      if (base + BLOCK < total) cta_maybe_flush<BLOCK>(sm, I, L, st);
+      if (base + BLOCK * R < total) cta_maybe_flush<BLOCK>(sm, I, L, st);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -79,25 +79,29 @@ struct GcBody {
       if (t < cnt) sm.off[t] = off;
       if (total == 0 && base > 0) break;
       __syncthreads();
-      for (int r = 0; r < total; r += BLOCK) {
-        const int e = r + t;
-        bool push_nb = false;
-        int nb = 0;
-        if (e < total) {
-          const int i = owner_of(sm.off, cnt, e);
-          nb = ldg(I.col + sm.start[i] + (e - sm.off[i]));
-          const int c = __ldcg(I.color + nb);
-          const int item = sm.aux[i];
-          if (item >= 0) {
-            const int rel = c - base;
-            if (rel >= 0 && rel < kGcWindow) atomicOr(&sm.x.bits[2 * i + (rel >> 5)], 1u << (rel & 31));
-          } else if (c == (int)sm.x.bits[2 * i] && nb != ~item) {
-            if (nb < ~item) sm.x.bits[2 * i + 1] = 1u;        // v is the larger: v recolours
-            else push_nb = gc_claim_assign(I, nb);            // the neighbour is the larger
+      constexpr int R = LbsRun<BLOCK>::R;
+      for (int r = 0; r < total; r += BLOCK * R) {
+        int owner[R], nb[R], c[R];
+        lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
+#pragma unroll
+        for (int j = 0; j < R; ++j) c[j] = owner[j] >= 0 ? __ldcg(I.color + nb[j]) : 0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          bool push_nb = false;
+          const int i = owner[j];
+          if (i >= 0) {
+            const int item = sm.aux[i];
+            if (item >= 0) {
+              const int rel = c[j] - base;
+              if (rel >= 0 && rel < kGcWindow) atomicOr(&sm.x.bits[2 * i + (rel >> 5)], 1u << (rel & 31));
+            } else if (c[j] == (int)sm.x.bits[2 * i] && nb[j] != ~item) {
+              if (nb[j] < ~item) sm.x.bits[2 * i + 1] = 1u;   // v is the larger: v recolours
+              else push_nb = gc_claim_assign(I, nb[j]);       // the neighbour is the larger
+            }
           }
+          cta_push(sm, push_nb, nb[j]);
         }
-        cta_push(sm, push_nb, nb);
-        if (r + BLOCK < total) cta_maybe_flush<BLOCK>(sm, I, L, st);
+        if (r + BLOCK * R < total) cta_maybe_flush<BLOCK>(sm, I, L, st);
       }
       cta_maybe_flush<BLOCK>(sm, I, L, st);
       edges += total;

@@ -280,10 +280,18 @@ __device__ __forceinline__ int owner_of(const int* off, int cnt, int e) {
   return lo;
 }
 
+// Consecutive edges each thread handles per round of a CTA worker's load-balancing loop: one
+// owner search per run, and R independent loads in flight per thread.
+template <int BLOCK>
+struct LbsRun {
+  static constexpr int R = BLOCK <= 256 ? 4 : (BLOCK == 512 ? 2 : 1);
+};
+
 // Shared memory of a CTA worker.  `Extra` is the task body's own per-item state.
 template <int BLOCK, class Extra>
 struct CtaSmem {
-  static constexpr int kPushCap = 2 * BLOCK;
+  static constexpr int kRoundPushes = LbsRun<BLOCK>::R * BLOCK;  // most pushes one round can add
+  static constexpr int kPushCap = 2 * kRoundPushes;
   int items[BLOCK];
   int start[BLOCK];
   int off[BLOCK + 1];
@@ -334,11 +342,33 @@ __device__ __forceinline__ void cta_flush(S& sm, const Instance& I, int done, co
   __syncthreads();
 }
 
-// Flush only when the buffer could overflow in the next round of BLOCK appends.
+// Flush only when the buffer could overflow in the next round of appends.
 template <int BLOCK, class S>
 __device__ __forceinline__ void cta_maybe_flush(S& sm, const Instance& I, const Launch& L, unsigned long long* st) {
   __syncthreads();
-  if (sm.npush > S::kPushCap - BLOCK) cta_flush<BLOCK>(sm, I, 0, L, st);
+  if (sm.npush > S::kPushCap - S::kRoundPushes) cta_flush<BLOCK>(sm, I, 0, L, st);
+}
+
+// One round of the load-balancing search: thread t takes the R consecutive flattened edges
+// starting at e0 = base + t * R; for each it returns the owning item and the neighbour id.
+template <int BLOCK, class S>
+__device__ __forceinline__ void lbs_round(const S& sm, const int32_t* __restrict__ col, int cnt, int total,
+                                          int base, int (&item)[LbsRun<BLOCK>::R], int (&nb)[LbsRun<BLOCK>::R]) {
+  constexpr int R = LbsRun<BLOCK>::R;
+  const int e0 = base + (int)threadIdx.x * R;
+#pragma unroll
+  for (int j = 0; j < R; ++j) item[j] = -1;
+  if (e0 >= total) return;
+  int i = owner_of(sm.off, cnt, e0);
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int e = e0 + j;
+    if (e < total) {
+      while (i + 1 < cnt && sm.off[i + 1] <= e) ++i;
+      item[j] = i;
+      nb[j] = ldg(col + sm.start[i] + (e - sm.off[i]));
+    }
+  }
 }
 
 // After a batch: stop if the launch failed or this worker has outlived the launch budget.
@@ -464,8 +494,15 @@ __device__ void cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const
   }
 }
 
+// Minimum resident CTAs per SM the compiler must allow (75% of the 2048 threads of an SM): caps
+// registers near 42 per thread, trading some per-thread ILP for resident warps.
+template <int BLOCK>
+struct MinBlocks {
+  static constexpr int value = BLOCK >= 1024 ? 1 : 1536 / BLOCK;
+};
+
 template <class Body, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) cta_persistent_kernel(Launch L) {
+__global__ void __launch_bounds__(BLOCK, MinBlocks<BLOCK>::value) cta_persistent_kernel(Launch L) {
   __shared__ CtaSmem<BLOCK, typename Body::Extra> sm;
   unsigned long long st[kNumStats] = {0, 0, 0, 0};
   const unsigned long long t0 = globaltimer();

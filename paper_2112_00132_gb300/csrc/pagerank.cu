@@ -120,14 +120,13 @@ struct PrBody {
     if ((int)threadIdx.x < cnt) sm.off[threadIdx.x] = off;
     __syncthreads();
     float* __restrict__ res = I.res;
-    const int32_t* __restrict__ col = I.col;
-    for (int base = 0; base < total; base += BLOCK) {
-      const int e = base + threadIdx.x;
-      if (e < total) {
-        const int i = owner_of(sm.off, cnt, e);
-        const int nb = ldg(col + sm.start[i] + (e - sm.off[i]));
-        atomicAdd(res + nb, __int_as_float(sm.aux[i]));
-      }
+    constexpr int R = LbsRun<BLOCK>::R;
+    for (int base = 0; base < total; base += BLOCK * R) {
+      int item[R], nb[R];
+      lbs_round<BLOCK>(sm, I.col, cnt, total, base, item, nb);
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (item[j] >= 0) atomicAdd(res + nb[j], __int_as_float(sm.aux[item[j]]));
     }
     if (threadIdx.x == 0) {
       st[kStatTasks] += cnt;
@@ -312,26 +311,53 @@ __global__ void pr_sums_kernel(const Instance* inst, DevCtl* ctl) {
 }
 
 // A posteriori certificate in FP64: with x = rank * (S / sum_rank), where S = n - alpha * (isolated
-// vertices) is the exact sum of the fixed point, accumulate ||(1 - alpha) 1 + alpha P x - x||_1.
-__global__ void pr_certificate_kernel(const Instance* inst, DevCtl* ctl, double S) {
+// vertices) is the exact sum of the fixed point, ||(1 - alpha) 1 + alpha P x - x||_1.  First
+// y[v] = sum_{u in N(v)} rank[u] / deg(u) is accumulated edge-balanced (kCertRun consecutive CSR
+// entries per thread, FP64 atomics per row touched), then a vertex pass sums |rho_v|.
+constexpr int kCertRun = 8;
+
+__device__ __forceinline__ int cert_row_of(const int32_t* row_ptr, int lo, int hi, int k) {
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(row_ptr + mid) <= k) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void pr_cert_pull_kernel(const Instance* inst, double* y) {
+  const Instance I = *inst;
+  const int64_t nnz = __ldg(I.row_ptr + I.n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kCertRun;
+  for (int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kCertRun; k0 < nnz; k0 += stride) {
+    const int k1 = (int)(k0 + kCertRun < nnz ? k0 + kCertRun : nnz);
+    int r = cert_row_of(I.row_ptr, 0, I.n, (int)k0);
+    int next = __ldg(I.row_ptr + r + 1);
+    double acc = 0.0;
+    for (int k = (int)k0; k < k1; ++k) {
+      while (k >= next) {
+        if (acc != 0.0) atomicAdd(y + r, acc);
+        acc = 0.0;
+        ++r;
+        next = __ldg(I.row_ptr + r + 1);
+      }
+      const int u = __ldg(I.col + k);
+      acc += (double)I.rank[u] / (double)(__ldg(I.row_ptr + u + 1) - __ldg(I.row_ptr + u));
+    }
+    if (acc != 0.0) atomicAdd(y + r, acc);
+  }
+}
+
+__global__ void pr_cert_sum_kernel(const Instance* inst, const double* y, DevCtl* ctl, double S) {
   const Instance I = *inst;
   const double scale = S / ctl->sum_rank;
   const double a = (double)I.alpha;
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   double acc = 0.0;
-  for (int v = gw; v < I.n; v += nw) {
-    const int s = __ldg(I.row_ptr + v), e = __ldg(I.row_ptr + v + 1);
-    double p = 0.0;
-    for (int k = s + lane; k < e; k += 32) {
-      const int u = __ldg(I.col + k);
-      p += (double)I.rank[u] / (double)(__ldg(I.row_ptr + u + 1) - __ldg(I.row_ptr + u));
-    }
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < I.n; v += gridDim.x * blockDim.x)
+    acc += fabs((1.0 - a) + a * y[v] * scale - (double)I.rank[v] * scale);
 #pragma unroll
-    for (int o = 16; o; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-    if (lane == 0) acc += fabs((1.0 - a) + a * p * scale - (double)I.rank[v] * scale);
-  }
-  if (lane == 0) atomicAdd(&ctl->cert_l1, acc);
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&ctl->cert_l1, acc);
 }
 
 __global__ void pr_normalise_kernel(const Instance* inst, const DevCtl* ctl) {
@@ -341,16 +367,23 @@ __global__ void pr_normalise_kernel(const Instance* inst, const DevCtl* ctl) {
     I.rank[v] = (float)((double)I.rank[v] * inv);
 }
 
-cudaError_t pr_finish(Instance* d_insts, int ninst, int n, float alpha, DevCtl* d_ctl, bool certificate,
+// certificate_y: FP64 scratch of n entries (needed only when `certificate`).
+cudaError_t pr_finish(Instance* d_insts, int ninst, int n, int64_t nnz, DevCtl* d_ctl, double* certificate_y,
                       double exact_sum, cudaStream_t s) {
   (void)ninst;
-  (void)alpha;
   cudaMemsetAsync(&d_ctl->sum_rank, 0, 3 * sizeof(double), s);
   int gx = (n + 255) / 256;
   gx = gx < 1 ? 1 : (gx > 2048 ? 2048 : gx);
-  count_launches(certificate ? 3 : 2);
+  count_launches(2);
   pr_sums_kernel<<<gx, 256, 0, s>>>(d_insts, d_ctl);
-  if (certificate) pr_certificate_kernel<<<gx, 256, 0, s>>>(d_insts, d_ctl, exact_sum);
+  if (certificate_y) {
+    cudaMemsetAsync(certificate_y, 0, sizeof(double) * (size_t)n, s);
+    int64_t per = (nnz + 256 * kCertRun - 1) / (256 * kCertRun);
+    const int gy = (int)(per < 1 ? 1 : (per > 4096 ? 4096 : per));
+    count_launches(2);
+    pr_cert_pull_kernel<<<gy, 256, 0, s>>>(d_insts, certificate_y);
+    pr_cert_sum_kernel<<<gx, 256, 0, s>>>(d_insts, certificate_y, d_ctl, exact_sum);
+  }
   pr_normalise_kernel<<<gx, 256, 0, s>>>(d_insts, d_ctl);
   return cudaGetLastError();
 }

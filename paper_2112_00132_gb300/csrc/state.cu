@@ -60,22 +60,9 @@ __global__ void prepare_kernel(Instance* insts, DevCtl* ctl, uint32_t flags, uns
         const int rem = n - (w << 5);
         I.qbits[w] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
       }
-      // residue[v] = base * sum_{u in N(v)} 1/deg(u): a pull over v's row (the graph is
-      // symmetric); one warp per vertex so that hub rows are read with coalesced loads.
-      const int lane = threadIdx.x & 31;
-      const int gw = tid >> 5, nw = stride >> 5;
-      for (int v = gw; v < n; v += nw) {
-        const int s = __ldg(I.row_ptr + v), e = __ldg(I.row_ptr + v + 1);
-        float acc = 0.0f;
-#pragma unroll 4
-        for (int k = s + lane; k < e; k += 32) {
-          const int u = __ldg(I.col + k);
-          acc += 1.0f / (float)(__ldg(I.row_ptr + u + 1) - __ldg(I.row_ptr + u));
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) I.res[v] = base * acc;
-      }
+      // the initial residue is accumulated by pr_init_residue_kernel (edge-balanced)
+      for (int v = tid; v < n; v += stride) I.res[v] = 0.0f;
+      (void)base;
       break;
     }
     case kAppGc: {
@@ -88,6 +75,54 @@ __global__ void prepare_kernel(Instance* insts, DevCtl* ctl, uint32_t flags, uns
       break;
     }
   }
+}
+
+// Largest i in [lo, hi) with row_ptr[i] <= k (the row holding CSR entry k).
+__device__ __forceinline__ int row_of(const int32_t* row_ptr, int lo, int hi, int k) {
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(row_ptr + mid) <= k) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// residue[v] = (1 - alpha) alpha sum_{u in N(v)} 1/deg(u), edge-balanced: each thread takes
+// kRun consecutive CSR entries (so a hub row is spread over many threads), finds the row of its
+// first entry by binary search, and adds one partial sum per row it touches.
+constexpr int kInitRun = 8;
+
+__global__ void pr_init_residue_kernel(Instance* insts) {
+  const Instance I = insts[blockIdx.y];
+  if (I.app != kAppPr) return;
+  const int64_t nnz = __ldg(I.row_ptr + I.n);
+  const float base = (1.0f - I.alpha) * I.alpha;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kInitRun;
+  for (int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kInitRun; k0 < nnz; k0 += stride) {
+    const int k1 = (int)(k0 + kInitRun < nnz ? k0 + kInitRun : nnz);
+    int r = row_of(I.row_ptr, 0, I.n, (int)k0);
+    int next = __ldg(I.row_ptr + r + 1);
+    float acc = 0.0f;
+    for (int k = (int)k0; k < k1; ++k) {
+      while (k >= next) {  // entry k starts a later row: flush the finished one
+        if (acc != 0.0f) atomicAdd(I.res + r, base * acc);
+        acc = 0.0f;
+        ++r;
+        next = __ldg(I.row_ptr + r + 1);
+      }
+      const int u = __ldg(I.col + k);
+      acc += 1.0f / (float)(__ldg(I.row_ptr + u + 1) - __ldg(I.row_ptr + u));
+    }
+    if (acc != 0.0f) atomicAdd(I.res + r, base * acc);
+  }
+}
+
+cudaError_t launch_pr_init(Instance* d_insts, int ninst, int64_t max_nnz, cudaStream_t s) {
+  int64_t per = (max_nnz + 256 * kInitRun - 1) / (256 * kInitRun);
+  int gx = (int)(per < 1 ? 1 : (per > 4096 ? 4096 : per));
+  count_launches(1);
+  pr_init_residue_kernel<<<dim3(gx, ninst), 256, 0, s>>>(d_insts);
+  return cudaGetLastError();
 }
 
 __global__ void next_generation_kernel(Instance* insts, int ninst, DevCtl* ctl) {

@@ -25,6 +25,7 @@ struct alignas(128) DevCtl {
 
 cudaError_t launch_prepare(Instance* d_insts, int ninst, int max_n, DevCtl* d_ctl, uint32_t flags, unsigned window,
                            cudaStream_t s);
+cudaError_t launch_pr_init(Instance* d_insts, int ninst, int64_t max_nnz, cudaStream_t s);
 cudaError_t launch_next_generation(Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
 cudaError_t launch_finalize(DevCtl* d_ctl, cudaStream_t s);
 
