@@ -160,9 +160,65 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
  * ATOS_ERR_INVALID_ARG if ninst exceeds the instances g's scratch holds. */
 int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint32_t* heads, int32_t* fail_site);
 
+/* Diagnostics: after synchronising the device, counts the set bits of g's queued-vertex bitmap
+ * (PageRank / colouring) and the occupied slots of its rings; after a successful run both are
+ * zero.  Either pointer may be NULL. */
+int atos_debug_scratch_check(atos_graph_t g, uint64_t* set_bits, uint64_t* busy_slots);
+
 /* Number of CUDA kernels this library has launched in this process (monotone counter, all
  * threads, all devices); lets a caller count the launches of a region of its own program. */
 uint64_t atos_kernel_launches(void);
+
+/* ------------------------------------------------------------------ batched launches */
+
+#define ATOS_APP_BFS 0
+#define ATOS_APP_PAGERANK 1
+#define ATOS_APP_COLOR 2
+
+/* One instance of a batch: an application on one of the batch's graphs. */
+typedef struct atos_instance {
+  int32_t app;    /* ATOS_APP_BFS, ATOS_APP_PAGERANK or ATOS_APP_COLOR */
+  int32_t graph;  /* index into the graphs array given to atos_batch_create */
+  int32_t source; /* BFS: source vertex */
+  float alpha;    /* PageRank: damping in (0, 1) */
+  float eps;      /* PageRank: residue threshold > 0 (unnormalised scale) */
+  int32_t reserved;
+  void* out;      /* DEVICE output of n entries: int32 depths (BFS), float ranks summing to 1
+                     (PageRank) or int32 colours (colouring); owned by the caller */
+} atos_instance;
+
+typedef struct atos_batch_s* atos_batch_t;
+
+/* Creates a batch of ninst instances over ngraphs graphs (extension of the paper's single queue
+ * to one worklist per instance; Section 3's scheduler, several problems at once).  Everything a
+ * run needs (instance table, rings, control blocks, PageRank and colouring scratch) is
+ * allocated here; the graphs and output buffers must stay alive until atos_batch_destroy.
+ * cfg: persistent strategy only (ATOS_ERR_UNSUPPORTED otherwise); cfg->window instances are
+ * active at a time (0 = as many as fit in about half of L2).  Errors: ATOS_ERR_INVALID_ARG for
+ * NULL pointers, ninst outside [1, 65535], a bad graph index, source, alpha or eps. */
+int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_instance* inst, int32_t ninst,
+                      const atos_config* cfg, atos_batch_t* out);
+
+/* Enqueues one run of every instance on `stream` (stream-ordered kernel launches and memsets
+ * only: no host synchronisation, no allocation, so the call can be captured in a CUDA graph).
+ * Calls on one batch must not overlap on the device. */
+int atos_batch_run(atos_batch_t b, void* stream);
+
+/* Same as atos_batch_run, but the first call captures the run into a CUDA graph (on a private
+ * stream) and every call replays it with one graph launch on `stream`. */
+int atos_batch_run_graph(atos_batch_t b, void* stream);
+
+/* Synchronises `stream` and reports the last run: *total sums the instances' counters (ms = the
+ * run's device time); per_instance (ninst entries, may be NULL) gets each instance's counters,
+ * PageRank residual_l1 and error_bound (2 ||r||_1 / ((1 - alpha) sum p), from the residue
+ * invariant) and colouring num_colors.  Returns the device status of the run. */
+int atos_batch_stats(atos_batch_t b, atos_stats* total, atos_stats* per_instance, void* stream);
+
+/* Instances, active window and persistent grid size of a batch (any pointer may be NULL). */
+int atos_batch_info(atos_batch_t b, int32_t* ninst, int32_t* window, int32_t* grid);
+
+/* Frees a batch (synchronises the device first).  NULL is a no-op. */
+int atos_batch_destroy(atos_batch_t b);
 
 /* ------------------------------------------------------------------ allocation-free BFS */
 

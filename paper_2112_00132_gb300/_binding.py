@@ -73,6 +73,21 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+APP_BFS, APP_PAGERANK, APP_COLOR = 0, 1, 2
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [
+        ("app", ctypes.c_int32),
+        ("graph", ctypes.c_int32),
+        ("source", ctypes.c_int32),
+        ("alpha", ctypes.c_float),
+        ("eps", ctypes.c_float),
+        ("reserved", ctypes.c_int32),
+        ("out", ctypes.c_void_p),
+    ]
+
+
 class AtosError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -102,8 +117,19 @@ def lib() -> ctypes.CDLL:
         L.atos_color.argtypes = [vp, vp, P(i32), P(Config), vp, P(Stats)]
         L.atos_debug_queue_state.argtypes = [vp, i32, vp, vp, P(i32)]
         L.atos_debug_queue_state.restype = ctypes.c_int
+        L.atos_batch_create.argtypes = [vp, i32, P(Instance), i32, P(Config), P(vp)]
+        L.atos_batch_run.argtypes = [vp, vp]
+        L.atos_batch_run_graph.argtypes = [vp, vp]
+        L.atos_batch_stats.argtypes = [vp, P(Stats), P(Stats), vp]
+        L.atos_batch_info.argtypes = [vp, P(i32), P(i32), P(i32)]
+        L.atos_batch_destroy.argtypes = [vp]
+        for name in ("atos_batch_create", "atos_batch_run", "atos_batch_run_graph", "atos_batch_stats",
+                     "atos_batch_info", "atos_batch_destroy"):
+            getattr(L, name).restype = ctypes.c_int
         L.atos_bfs_noalloc.argtypes = [vp, vp, i32, i64, i32, vp, vp]
         L.atos_bfs_noalloc.restype = ctypes.c_int
+        L.atos_debug_scratch_check.argtypes = [vp, P(ctypes.c_uint64), P(ctypes.c_uint64)]
+        L.atos_debug_scratch_check.restype = ctypes.c_int
         L.atos_kernel_launches.argtypes = []
         L.atos_kernel_launches.restype = ctypes.c_uint64
         L.atos_status_string.argtypes = [ctypes.c_int]
@@ -236,6 +262,13 @@ class Graph:
                                             ctypes.byref(site)), "atos_debug_queue_state")
         return [(int(w >> 32), int(w & 0xffffffff), int(h)) for w, h in zip(words, heads)], site.value
 
+    def scratch_check(self):
+        """(set queued bits, occupied ring slots) after the last run; both 0 after a clean run."""
+        bits, slots = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().atos_debug_scratch_check(self._h, ctypes.byref(bits), ctypes.byref(slots)),
+               "atos_debug_scratch_check")
+        return bits.value, slots.value
+
     # ------------------------------------------------------------------------------ apps
 
     def bfs(self, sources, depths=None, cfg: Config | None = None, stream=None, stats: bool = True):
@@ -277,3 +310,74 @@ class Graph:
                               ctypes.byref(st) if st is not None else None)
         _check(rc, "atos_color")
         return colors, (k.value if stats else None), st
+
+
+class Batch:
+    """Many instances over several graphs in one persistent launch (wraps an atos_batch_t).
+
+    ``specs`` is a list of ("bfs", graph_index, source), ("pagerank", graph_index[, alpha, eps])
+    or ("color", graph_index); an output tensor is allocated for each instance (``outputs``).
+    The graphs must stay open while the batch lives."""
+
+    def __init__(self, graphs, specs, cfg: Config | None = None):
+        import torch
+        self._h = ctypes.c_void_p()
+        self.graphs = list(graphs)
+        self.specs = list(specs)
+        arr = (Instance * len(self.specs))()
+        self.outputs = []
+        for i, spec in enumerate(self.specs):
+            kind, gi = spec[0], int(spec[1])
+            n = self.graphs[gi].n if 0 <= gi < len(self.graphs) else 1  # a bad index is the C ABI's to reject
+            q = arr[i]
+            q.graph = gi
+            if kind == "bfs":
+                q.app, q.source = APP_BFS, int(spec[2])
+                out = torch.empty(n, dtype=torch.int32, device="cuda")
+            elif kind == "pagerank":
+                q.app = APP_PAGERANK
+                q.alpha = float(spec[2]) if len(spec) > 2 else 0.85
+                q.eps = float(spec[3]) if len(spec) > 3 else 1e-9
+                out = torch.empty(n, dtype=torch.float32, device="cuda")
+            elif kind == "color":
+                q.app = APP_COLOR
+                out = torch.empty(n, dtype=torch.int32, device="cuda")
+            else:
+                raise ValueError(kind)
+            q.out = out.data_ptr()
+            self.outputs.append(out)
+        handles = (ctypes.c_void_p * len(self.graphs))(*[g._h.value for g in self.graphs])
+        _check(lib().atos_batch_create(handles, len(self.graphs), arr, len(self.specs),
+                                       ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(self._h)),
+               "atos_batch_create")
+        ni, w, grid = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        lib().atos_batch_info(self._h, ctypes.byref(ni), ctypes.byref(w), ctypes.byref(grid))
+        self.window, self.grid = w.value, grid.value
+
+    def run(self, stream=None, graph: bool = False):
+        fn = lib().atos_batch_run_graph if graph else lib().atos_batch_run
+        _check(fn(self._h, _stream_handle(stream)), "atos_batch_run")
+
+    def stats(self, stream=None):
+        total = Stats()
+        per = (Stats * len(self.specs))()
+        rc = lib().atos_batch_stats(self._h, ctypes.byref(total), per, _stream_handle(stream))
+        _check(rc, "atos_batch_stats")
+        return total, list(per)
+
+    def close(self):
+        if self._h:
+            lib().atos_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

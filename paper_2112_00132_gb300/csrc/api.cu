@@ -2,6 +2,7 @@
 // host side of the persistent / discrete scheduling loops.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -23,6 +24,12 @@ cudaError_t pr_finish(Instance* d_insts, int ninst, int n, int64_t nnz, DevCtl* 
                       double exact_sum, cudaStream_t s);
 cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s);
 unsigned long long launches_so_far();
+int bsp_pagerank(const int32_t* row_ptr, const int32_t* col, int32_t n, float alpha, float eps, float* rank,
+                 float* res, void* scratch, size_t scratch_bytes, int32_t* hcount, cudaStream_t s,
+                 int64_t* iterations, int64_t* edges, int64_t* tasks);
+int bsp_color(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t* color, void* scratch,
+              size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges,
+              int64_t* tasks);
 int bsp_bfs(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t src, int32_t* depth, void* scratch,
             size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges);
 }  // namespace atos
@@ -151,6 +158,24 @@ int ensure_scratch(atos_graph_s* g, int ninst, uint32_t cap) {
 // Ring slots per instance.  Besides the tasks in flight the ring must cover the span between the
 // oldest ticket a busy worker has not taken yet and the tail, so small graphs get a floor of 2^20
 // slots (8 MiB); large ones 1.5 n plus the virtual prefix.
+// BSP comparator scratch: frontiers, scan offsets and per-item values, grown on demand.
+int ensure_bsp(atos_graph_s* g, size_t bytes) {
+  if (!g->s.ev0) {
+    int rc = ensure_scratch(g, 1, 1024);
+    if (rc) return rc;
+  }
+  if (g->bsp_bytes >= bytes) return ATOS_OK;
+  cudaDeviceSynchronize();
+  cudaFree(g->d_bsp);
+  g->d_bsp = nullptr;
+  g->bsp_bytes = 0;
+  ATOS_TRY(cudaMalloc(&g->d_bsp, bytes));
+  g->bsp_bytes = bytes;
+  return ATOS_OK;
+}
+
+size_t bsp_bytes_for(int32_t n) { return sizeof(int32_t) * (4 * (size_t)n + (size_t)n / 1024 + 4096); }
+
 uint32_t ring_capacity(const atos_config& cfg, int32_t n, uint32_t prefix) {
   if (cfg.queue_capacity > 0) return next_pow2(std::max<uint64_t>((uint64_t)cfg.queue_capacity, 1024));
   const uint64_t want = (uint64_t)n + (uint64_t)n / 2 + prefix + 1024;
@@ -256,7 +281,7 @@ int run_instances(atos_graph_s* g, int ninst, int max_n, const atos_config& cfg,
       gen = s.h_ctl->maxgen;
     }
   }
-  ATOS_TRY(launch_finalize(s.d_ctl, st));
+  ATOS_TRY(launch_finalize(s.d_insts, ninst, s.d_ctl, st));
   if (iterations) *iterations = iters;
   return ATOS_OK;
 }
@@ -299,6 +324,17 @@ Instance base_instance(atos_graph_s* g, int i, int app, uint32_t cap, uint32_t p
 }
 
 }  // namespace
+
+namespace atos {
+// Device CSR of a graph, for the batch API.
+int graph_device_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, int32_t* n_isolated) {
+  if (!g) return ATOS_ERR_INVALID_ARG;
+  *row_ptr = g->row_ptr;
+  *col = g->col;
+  *n_isolated = g->n_isolated;
+  return ATOS_OK;
+}
+}  // namespace atos
 
 // ============================================================================ C ABI
 
@@ -457,19 +493,8 @@ int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* dept
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = g->n;
   if (cfg.strategy == ATOS_BSP) {
-    if (!g->s.ev0) {
-      rc = ensure_scratch(g, 1, 1024);
-      if (rc) return rc;
-    }
-    const size_t need = sizeof(int32_t) * (3 * (size_t)n + (size_t)n / 1024 + 4096);
-    if (g->bsp_bytes < need) {
-      cudaDeviceSynchronize();
-      cudaFree(g->d_bsp);
-      g->d_bsp = nullptr;
-      g->bsp_bytes = 0;
-      ATOS_TRY(cudaMalloc(&g->d_bsp, need));
-      g->bsp_bytes = need;
-    }
+    rc = ensure_bsp(g, bsp_bytes_for(g->n));
+    if (rc) return rc;
     ATOS_TRY(cudaEventRecord(g->s.ev0, st));
     int64_t iters = 0, edges = 0;
     for (int32_t i = 0; i < nsrc; ++i) {
@@ -534,7 +559,12 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   if (g->n == 0) return ATOS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const int32_t n = g->n;
-  if (cfg.strategy == ATOS_BSP) return ATOS_ERR_UNSUPPORTED;
+  const bool bsp = cfg.strategy == ATOS_BSP;
+  if (bsp) {
+    cfg.strategy = ATOS_PERSISTENT;  // the prepare step below is shared; the loop is not run
+    rc = ensure_bsp(g, bsp_bytes_for(n));
+    if (rc) return rc;
+  }
   const uint32_t cap = ring_capacity(cfg, n, (uint32_t)n);
   if (!cap) return ATOS_ERR_INVALID_ARG;
   rc = ensure_scratch(g, 1, cap);
@@ -552,9 +582,20 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   cfg.window = 1;
   const double exact_sum = (double)n - (double)alpha * (double)g->n_isolated;
   ATOS_TRY(cudaEventRecord(g->s.ev0, st));
-  int64_t iters = 0;
-  rc = run_instances(g, 1, n, cfg, pr_persistent_kernel, pr_discrete_kernel, kAppPr, st, &iters);
-  if (rc) return rc;
+  int64_t iters = 0, bsp_edges = 0, bsp_tasks = 0;
+  if (bsp) {
+    // Algorithm 3: same initial state (prepare + initial residue), then level-synchronous sweeps
+    rc = upload_instances(g->s, 1, st);
+    if (rc) return rc;
+    ATOS_TRY(launch_prepare(g->s.d_insts, 1, n, g->s.d_ctl, 0u, 1u, st));
+    ATOS_TRY(launch_pr_init(g->s.d_insts, 1, g->nnz, st));
+    rc = bsp_pagerank(g->row_ptr, g->col, n, alpha, eps, rank, g->d_res, g->d_bsp, g->bsp_bytes,
+                      (int32_t*)&g->s.h_ctl->maxgen, st, &iters, &bsp_edges, &bsp_tasks);
+    if (rc) return rc;
+  } else {
+    rc = run_instances(g, 1, n, cfg, pr_persistent_kernel, pr_discrete_kernel, kAppPr, st, &iters);
+    if (rc) return rc;
+  }
   if (stats && !g->d_cert) ATOS_TRY(dev_alloc(&g->d_cert, (size_t)n));
   ATOS_TRY(pr_finish(g->s.d_insts, 1, n, g->nnz, g->s.d_ctl, stats ? g->d_cert : nullptr, exact_sum, st));
   ATOS_TRY(cudaEventRecord(g->s.ev1, st));
@@ -562,6 +603,11 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
     rc = collect_stats(g, 1, st, stats);
     if (rc) return rc;
     stats->iterations = iters;
+    if (bsp) {
+      stats->tasks = bsp_tasks;
+      stats->edges = bsp_edges;
+      stats->pushes = bsp_tasks;
+    }
     stats->residual_l1 = g->s.h_ctl->sum_res;
     const double denom = (1.0 - (double)alpha) * exact_sum;
     stats->error_bound = g->s.h_ctl->cert_l1 / denom + 5.96e-8;  // + FP32 rounding of the output
@@ -583,7 +629,38 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   if (g->n == 0) return ATOS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const int32_t n = g->n;
-  if (cfg.strategy == ATOS_BSP) return ATOS_ERR_UNSUPPORTED;
+  if (cfg.strategy == ATOS_BSP) {
+    rc = ensure_bsp(g, bsp_bytes_for(n));
+    if (rc) return rc;
+    ATOS_TRY(cudaEventRecord(g->s.ev0, st));
+    int64_t iters = 0, edges = 0, tasks = 0;
+    rc = bsp_color(g->row_ptr, g->col, n, colors, g->d_bsp, g->bsp_bytes, (int32_t*)&g->s.h_ctl->maxgen, st, &iters,
+                   &edges, &tasks);
+    if (rc) return rc;
+    Instance I;
+    memset(&I, 0, sizeof(I));
+    I.n = n;
+    I.color = colors;
+    ATOS_TRY(gc_finish(&I, g->s.d_ctl, st));
+    ATOS_TRY(cudaEventRecord(g->s.ev1, st));
+    if (stats || num_colors) {
+      ATOS_TRY(cudaMemcpyAsync(g->s.h_ctl, g->s.d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+      ATOS_TRY(cudaStreamSynchronize(st));
+      if (num_colors) *num_colors = g->s.h_ctl->num_colors;
+      if (stats) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g->s.ev0, g->s.ev1);
+        stats->ms = ms;
+        stats->iterations = iters;
+        stats->edges = edges;
+        stats->tasks = tasks;
+        stats->pushes = tasks;
+        stats->num_colors = g->s.h_ctl->num_colors;
+        stats->status = ATOS_OK;
+      }
+    }
+    return ATOS_OK;
+  }
   const uint32_t cap = ring_capacity(cfg, n, (uint32_t)n);
   if (!cap) return ATOS_ERR_INVALID_ARG;
   rc = ensure_scratch(g, 1, cap);
@@ -632,5 +709,32 @@ int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint3
 }
 
 uint64_t atos_kernel_launches(void) { return (uint64_t)launches_so_far(); }
+
+int atos_debug_scratch_check(atos_graph_t g, uint64_t* set_bits, uint64_t* busy_slots) {
+  if (!g) return ATOS_ERR_INVALID_ARG;
+  ATOS_TRY(cudaDeviceSynchronize());
+  if (set_bits) {
+    *set_bits = 0;
+    if (g->d_qbits && g->n) {
+      std::vector<uint32_t> b((g->n + 31) / 32);
+      ATOS_TRY(cudaMemcpy(b.data(), g->d_qbits, b.size() * 4, cudaMemcpyDeviceToHost));
+      for (uint32_t w : b) *set_bits += (uint64_t)__builtin_popcount(w);
+    }
+  }
+  if (busy_slots) {
+    *busy_slots = 0;
+    if (g->s.d_ring && g->s.cap) {
+      std::vector<unsigned long long> r((size_t)g->s.cap * g->s.ninst);
+      ATOS_TRY(cudaMemcpy(r.data(), g->s.d_ring, r.size() * 8, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < r.size(); ++i)
+        if (r[i] != ~0ull) {
+          if (*busy_slots < 4)
+            fprintf(stderr, "atos: busy slot %zu holds ticket %u item %d\n", i, (unsigned)(r[i] >> 32), (int)(unsigned)r[i]);
+          *busy_slots += 1;
+        }
+    }
+  }
+  return ATOS_OK;
+}
 
 }  // extern "C"

@@ -1,216 +1,11 @@
-// color.cu -- asynchronous speculative greedy colouring (Section 5.3, Algorithm 6).
-//
-// One uberkernel handles two kinds of task, told apart by the sign of the item:
-//   * item v >= 0 (assign): read the colours of v's neighbours, give v the smallest colour none
-//     of them holds (first fit; the colour is at most deg(v)), then push the check task ~v;
-//   * item ~v < 0 (check): for every neighbour u holding v's colour, the larger of u and v must
-//     recolour: push v itself (once) if some u < v, and push u for each such u > v.
-// Only the larger id of a conflicting pair recolours, so the smallest id of any conflict keeps its
-// colour.  A vertex has at most one assign task queued: a bitmap bit is set by whoever queues the
-// assign and cleared when it is popped, before the neighbours' colours are read (a request that
-// finds the bit set is covered by the pending assign, which will read the newer colours).  Pushing the larger endpoint from the smaller one's check closes the race in which the
-// smaller vertex's assign read a stale colour and wrote its own after the larger vertex's last
-// check.  The check task is encoded as ~v = -v - 1 so that vertex 0 has a distinct check task.
-//
-// Memory ordering: an assign writes its colour and then executes a sequentially consistent
-// device fence; a check executes the same fence before it reads any colour.  For two adjacent
-// vertices x and y this is the store-buffering pattern W(x); fence; R(y) against W(y); fence;
-// R(x), so at least one of the two checks that follow their final writes sees the other's colour,
-// and the conflict is found.  Colours are read from L2 (ld.global.cg).
+// color.cu -- colouring kernels: persistent / discrete instantiations of the task body in
+// color.cuh and the colour-count reduction.
+#include "color.cuh"
 #include "engine.cuh"
 #include "launch.cuh"
 #include "state.cuh"
 
 namespace atos {
-
-constexpr int kGcWindow = 64;  // colours examined per pass: two 32-bit words per item
-
-struct GcExtra {
-  unsigned bits[2 * 1024];  // per item: forbidden colours [base, base + 64) (assign) or
-                            // (own colour, conflict flag) (check)
-  int pass_base;
-};
-
-// Queues an assign task for u unless one is already queued.
-__device__ __forceinline__ bool gc_claim_assign(const Instance& I, int u) {
-  const unsigned bit = 1u << (u & 31);
-  return !(atomicOr(I.qbits + (u >> 5), bit) & bit);
-}
-
-struct GcBody {
-  using Extra = GcExtra;
-
-  template <int BLOCK, class S>
-  __device__ static void cta_batch(S& sm, int cnt, const Launch& L, unsigned long long* st) {
-    const Instance& I = sm.I;
-    const int t = threadIdx.x;
-    int v = 0, deg = 0, s = 0;
-    bool assign = false;
-    if (t < cnt) {
-      const int item = sm.items[t];
-      assign = item >= 0;
-      v = assign ? item : ~item;
-      s = ldg(I.row_ptr + v);
-      deg = ldg(I.row_ptr + v + 1) - s;
-      sm.start[t] = s;
-      sm.aux[t] = item;
-      if (assign) {
-        atomicAnd(I.qbits + (v >> 5), ~(1u << (v & 31)));  // requests from now on queue a new assign
-        sm.x.bits[2 * t] = 0u;
-        sm.x.bits[2 * t + 1] = 0u;
-      } else {
-        sm.x.bits[2 * t] = (unsigned)__ldcg(I.color + v);
-        sm.x.bits[2 * t + 1] = 0u;
-      }
-    }
-    __threadfence();  // order every earlier colour write of this CTA before the checks' reads
-    __syncthreads();
-    int64_t edges = 0;
-    int colour = -1;  // result of an assign item (thread t)
-    // pass 0 runs every item; later passes only assign items that found no free colour in the
-    // window [base, base + 64).
-    bool active = t < cnt;
-    for (int base = 0;; base += kGcWindow) {
-      const int mydeg = active ? deg : 0;
-      int total;
-      const int off = block_exclusive_scan<BLOCK>(mydeg, sm.tmp, total);
-      // inactive items have degree 0 here, so the offsets stay non-decreasing and the owner
-      // search never lands on them
-      if (t < cnt) sm.off[t] = off;
-      if (total == 0 && base > 0) break;
-      __syncthreads();
-      constexpr int R = LbsRun<BLOCK>::R;
-      for (int r = 0; r < total; r += BLOCK * R) {
-        int owner[R], nb[R], c[R];
-        lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
-#pragma unroll
-        for (int j = 0; j < R; ++j) c[j] = owner[j] >= 0 ? __ldcg(I.color + nb[j]) : 0;
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          bool push_nb = false;
-          const int i = owner[j];
-          if (i >= 0) {
-            const int item = sm.aux[i];
-            if (item >= 0) {
-              const int rel = c[j] - base;
-              if (rel >= 0 && rel < kGcWindow) atomicOr(&sm.x.bits[2 * i + (rel >> 5)], 1u << (rel & 31));
-            } else if (c[j] == (int)sm.x.bits[2 * i] && nb[j] != ~item) {
-              if (nb[j] < ~item) sm.x.bits[2 * i + 1] = 1u;   // v is the larger: v recolours
-              else push_nb = gc_claim_assign(I, nb[j]);       // the neighbour is the larger
-            }
-          }
-          cta_push(sm, push_nb, nb[j]);
-        }
-        if (r + BLOCK * R < total) cta_maybe_flush<BLOCK>(sm, I, L, st);
-      }
-      cta_maybe_flush<BLOCK>(sm, I, L, st);
-      edges += total;
-      __syncthreads();
-      bool again = false;
-      if (active && assign) {
-        const unsigned lo = sm.x.bits[2 * t], hi = sm.x.bits[2 * t + 1];
-        const unsigned long long used = ((unsigned long long)hi << 32) | lo;
-        if (~used) {
-          colour = base + __ffsll((long long)~used) - 1;
-        } else {
-          again = true;
-          sm.x.bits[2 * t] = 0u;
-          sm.x.bits[2 * t + 1] = 0u;
-        }
-      }
-      active = again;
-      if (!__syncthreads_or(again)) break;
-    }
-    // results: write colours, then push check tasks / recolourings
-    bool want = false;
-    int push_item = 0;
-    if (t < cnt) {
-      if (assign) {
-        st_relaxed(I.color + v, colour);
-        __threadfence();  // the colour is visible before the check task can be taken
-        want = true;
-        push_item = ~v;
-      } else if (sm.x.bits[2 * t + 1] && gc_claim_assign(I, v)) {
-        want = true;
-        push_item = v;
-      }
-    }
-    cta_push(sm, want, push_item);
-    __syncthreads();
-    if (t == 0) {
-      st[kStatTasks] += cnt;
-      st[kStatEdges] += edges;
-    }
-    cta_flush<BLOCK>(sm, I, cnt, L, st);
-  }
-
-  template <int BLOCK, class S>
-  __device__ static int cta_idle(S& sm, const Launch&, unsigned long long*) {
-    return threadIdx.x == 0 ? (instance_quiescent(sm.I) ? 1 : 0) : 0;
-  }
-
-  __device__ static void warp_item(WarpSmem& ws, const Instance& I, int item, const Launch& L,
-                                   unsigned long long* st) {
-    const int lane = threadIdx.x & 31;
-    const bool assign = item >= 0;
-    const int v = assign ? item : ~item;
-    const int s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
-    int64_t edges = 0;
-    if (assign) {
-      if (lane == 0) atomicAnd(I.qbits + (v >> 5), ~(1u << (v & 31)));
-      __syncwarp();
-      int colour = -1;
-      for (int base = 0; colour < 0; base += kGcWindow) {
-        unsigned lo = 0, hi = 0;
-        for (int k = s + lane; k < e; k += 32) {
-          const int rel = __ldcg(I.color + ldg(I.col + k)) - base;
-          if (rel >= 0 && rel < 32) lo |= 1u << rel;
-          else if (rel >= 32 && rel < 64) hi |= 1u << (rel - 32);
-        }
-        edges += e - s;
-        lo = __reduce_or_sync(0xffffffffu, lo);
-        hi = __reduce_or_sync(0xffffffffu, hi);
-        const unsigned long long used = ((unsigned long long)hi << 32) | lo;
-        if (~used) colour = base + __ffsll((long long)~used) - 1;
-      }
-      if (lane == 0) {
-        st_relaxed(I.color + v, colour);
-        __threadfence();  // the colour is visible before the check task can be taken
-      }
-      __syncwarp();
-      warp_push(ws, lane == 0, ~v);
-    } else {
-      __threadfence();  // store-buffering pattern with the assign's fence (see the file comment)
-      int cv = 0;
-      if (lane == 0) cv = __ldcg(I.color + v);
-      cv = __shfl_sync(0xffffffffu, cv, 0);
-      bool conflict = false;
-      for (int k = s; k < e; k += 32) {
-        const int j = k + lane;
-        bool larger = false;
-        int nb = 0;
-        if (j < e) {
-          nb = ldg(I.col + j);
-          if (nb != v && __ldcg(I.color + nb) == cv) {
-            if (nb < v) conflict = true;
-            else larger = gc_claim_assign(I, nb);
-          }
-        }
-        warp_push(ws, larger, nb);  // the larger neighbour recolours
-        warp_maybe_flush(ws, I, L, st);
-      }
-      edges += e - s;
-      conflict = __any_sync(0xffffffffu, conflict);
-      warp_push(ws, lane == 0 && conflict && gc_claim_assign(I, v), v);
-    }
-    warp_maybe_flush(ws, I, L, st);
-    if (lane == 0) st[kStatEdges] += edges;
-  }
-
-  __device__ static int warp_idle(WarpSmem&, const Instance& I, const Launch&, unsigned long long*) {
-    return (threadIdx.x & 31) == 0 ? (instance_quiescent(I) ? 1 : 0) : 0;
-  }
-};
 
 const void* gc_persistent_kernel(int worker) { return persistent_kernel_ptr<GcBody>(worker); }
 const void* gc_discrete_kernel(int worker) { return discrete_kernel_ptr<GcBody>(worker); }

@@ -129,7 +129,7 @@ extern "C" int atos_bfs_noalloc(const int32_t* row_ptr, const int32_t* col, int3
   L.lifetime_ns = 16 * L.spin_limit_ns;
   L.fail_site = &s->dctl.fail_site;
   if (launch_kernel(fn, dim3(nb), worker, L, st) != cudaSuccess) return ATOS_ERR_CUDA;
-  if (launch_finalize(&s->dctl, st) != cudaSuccess) return ATOS_ERR_CUDA;
+  if (launch_finalize(&s->inst, 1, &s->dctl, st) != cudaSuccess) return ATOS_ERR_CUDA;
 
   // report the device status: a plain copy into a host stack variable, then wait for the stream
   int status = 0;

@@ -1,4 +1,7 @@
-// pagerank.cu -- asynchronous push-residual PageRank task body (Section 5.2, Algorithm 4).
+// pagerank.cu -- PageRank kernels: the persistent / discrete instantiations of the task body in
+// pagerank.cuh, the discrete final sweep, and the FP64 result reductions and certificate.
+//
+// Task body summary (Section 5.2, Algorithm 4):
 //
 // A task is a vertex v.  The worker takes v's residue with an atomic exchange, adds it to
 // rank[v], and scatters alpha * residue / deg(v) to every neighbour (red.global.add.f32, no
@@ -18,237 +21,10 @@
 //     during such a sweep, so every residue is then at most epsilon.
 #include "engine.cuh"
 #include "launch.cuh"
+#include "pagerank.cuh"
 #include "state.cuh"
 
 namespace atos {
-
-__device__ __forceinline__ bool pr_try_enqueue(const Instance& I, int u) {
-  if (!(__ldcg(I.res + u) > I.eps)) return false;
-  const unsigned bit = 1u << (u & 31);
-  return !(atomicOr(I.qbits + (u >> 5), bit) & bit);
-}
-
-// Verification sweep protocol (see the file comment).  Returns the claimed chunk (>= 0), -1 when
-// the epoch has no chunk left, -2 when the instance is not quiescent or the epoch is stale.
-__device__ __forceinline__ int pr_claim_chunk(const Instance& I, int chunk, unsigned& T) {
-  const unsigned long long w = ld_relaxed_u64(&I.ctl->word);
-  T = (unsigned)(w >> 32);
-  if (T != (unsigned)w) return -2;
-  const unsigned nchunks = ((unsigned)I.n + chunk - 1) / chunk;
-  for (int tries = 0; tries < 64; ++tries) {
-    const unsigned long long vw = ld_relaxed_u64(&I.ctl->vword);
-    const unsigned e = (unsigned)(vw >> 32);
-    if (e != T) {
-      if ((int)(e - T) > 0) return -2;  // a newer epoch exists: our view is stale
-      atomicCAS(&I.ctl->vword, vw, (unsigned long long)T << 32);
-      continue;
-    }
-    const unsigned k = (unsigned)vw;
-    if (k >= nchunks) return -1;
-    if (atomicCAS(&I.ctl->vword, vw, vw + 1) == vw) return (int)k;
-  }
-  return -1;
-}
-
-// Records `len` clean vertices for epoch T; returns true if that completes a clean sweep while
-// the instance is still quiescent at T (then the instance is finished).
-__device__ __forceinline__ bool pr_record_clean(const Instance& I, unsigned T, unsigned len) {
-  for (int tries = 0; tries < 1 << 20; ++tries) {
-    const unsigned long long vd = ld_relaxed_u64(&I.ctl->vdone);
-    const unsigned e = (unsigned)(vd >> 32);
-    unsigned long long nv;
-    if (e == T) nv = vd + len;
-    else if ((int)(e - T) < 0) nv = ((unsigned long long)T << 32) | len;
-    else return false;
-    if (atomicCAS(&I.ctl->vdone, vd, nv) == vd) {
-      if ((unsigned)nv < (unsigned)I.n) return false;
-      const unsigned long long w = ld_relaxed_u64(&I.ctl->word);
-      if (w == (((unsigned long long)T << 32) | T)) {
-        atomicExch(&I.ctl->finished, 1);
-        return true;
-      }
-      return false;
-    }
-  }
-  return false;
-}
-
-struct PrBody {
-  using Extra = NoExtra;
-
-  template <int BLOCK, class S>
-  __device__ static void check_scan(S& sm, int nchk, const Launch& L, unsigned long long* st) {
-    const Instance& I = sm.I;
-    if (threadIdx.x == 0) sm.base = atomicAdd(&I.ctl->check, (unsigned)nchk);
-    __syncthreads();
-    const unsigned base = sm.base;
-    for (int r = 0; r < nchk; r += BLOCK) {
-      const int k = r + threadIdx.x;
-      int u = 0;
-      bool want = false;
-      if (k < nchk) {
-        u = (int)((base + (unsigned)k) % (unsigned)I.n);
-        want = pr_try_enqueue(I, u);
-      }
-      cta_push(sm, want, u);
-      if (r + BLOCK < nchk) cta_maybe_flush<BLOCK>(sm, I, L, st);
-    }
-  }
-
-  template <int BLOCK, class S>
-  __device__ static void cta_batch(S& sm, int cnt, const Launch& L, unsigned long long* st) {
-    const Instance& I = sm.I;
-    int deg = 0;
-    if ((int)threadIdx.x < cnt) {
-      const int v = sm.items[threadIdx.x];
-      atomicAnd(I.qbits + (v >> 5), ~(1u << (v & 31)));
-      const float r = atomicExch(I.res + v, 0.0f);
-      const int s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
-      float share = 0.0f;
-      if (r != 0.0f) {
-        atomicAdd(I.rank + v, r);
-        if (e > s) {
-          share = I.alpha * r / (float)(e - s);
-          deg = e - s;
-        }
-      }
-      sm.start[threadIdx.x] = s;
-      sm.aux[threadIdx.x] = __float_as_int(share);
-    }
-    int total;
-    const int off = block_exclusive_scan<BLOCK>(deg, sm.tmp, total);
-    if ((int)threadIdx.x < cnt) sm.off[threadIdx.x] = off;
-    __syncthreads();
-    float* __restrict__ res = I.res;
-    constexpr int R = LbsRun<BLOCK>::R;
-    for (int base = 0; base < total; base += BLOCK * R) {
-      int item[R], nb[R];
-      lbs_round<BLOCK>(sm, I.col, cnt, total, base, item, nb);
-#pragma unroll
-      for (int j = 0; j < R; ++j)
-        if (item[j] >= 0) atomicAdd(res + nb[j], __int_as_float(sm.aux[item[j]]));
-    }
-    if (threadIdx.x == 0) {
-      st[kStatTasks] += cnt;
-      st[kStatEdges] += total;
-    }
-    check_scan<BLOCK>(sm, cnt * (int)I.check_size, L, st);
-    __syncthreads();
-    cta_flush<BLOCK>(sm, I, cnt, L, st);
-  }
-
-  template <int BLOCK, class S>
-  __device__ static int cta_idle(S& sm, const Launch& L, unsigned long long* st) {
-    const Instance& I = sm.I;
-    constexpr int kChunk = BLOCK * 2;  // at most one push per vertex: fits the push buffer
-    if (threadIdx.x == 0) {
-      unsigned T = 0;
-      int k = -3;
-      if (ld_relaxed(&I.ctl->finished)) k = -4;
-      else k = pr_claim_chunk(I, kChunk, T);
-      sm.cnt = k;
-      sm.base = T;
-    }
-    __syncthreads();
-    const int k = sm.cnt;
-    const unsigned T = sm.base;
-    __syncthreads();
-    if (k == -4) return 1;
-    if (k == -1) return 0;  // the rest of the sweep is in other workers' hands
-    if (k == -2) {
-      // not quiescent: Algorithm 4's scan as the idle function
-      check_scan<BLOCK>(sm, BLOCK, L, st);
-      __syncthreads();
-      cta_flush<BLOCK>(sm, I, 0, L, st);
-      return 0;
-    }
-    const int v0 = k * kChunk;
-    const int v1 = min(I.n, v0 + kChunk);
-    for (int r = v0; r < v1; r += BLOCK) {
-      const int u = r + threadIdx.x;
-      const bool want = u < v1 && pr_try_enqueue(I, u);
-      cta_push(sm, want, u);
-    }
-    __syncthreads();
-    const int pushed = sm.npush;
-    cta_flush<BLOCK>(sm, I, 0, L, st);
-    if (pushed) return 0;
-    if (threadIdx.x == 0) sm.cnt = pr_record_clean(I, T, (unsigned)(v1 - v0)) ? 1 : 0;
-    __syncthreads();
-    return sm.cnt;
-  }
-
-  // Warp worker.
-  __device__ static void warp_item(WarpSmem& ws, const Instance& I, int v, const Launch& L, unsigned long long* st) {
-    const int lane = threadIdx.x & 31;
-    float share = 0.0f;
-    int s = 0, e = 0;
-    if (lane == 0) {
-      atomicAnd(I.qbits + (v >> 5), ~(1u << (v & 31)));
-      const float r = atomicExch(I.res + v, 0.0f);
-      s = ldg(I.row_ptr + v);
-      e = ldg(I.row_ptr + v + 1);
-      if (r != 0.0f) {
-        atomicAdd(I.rank + v, r);
-        if (e > s) share = I.alpha * r / (float)(e - s);
-      }
-      if (share == 0.0f) e = s;
-    }
-    share = __shfl_sync(0xffffffffu, share, 0);
-    s = __shfl_sync(0xffffffffu, s, 0);
-    e = __shfl_sync(0xffffffffu, e, 0);
-    for (int k = s + lane; k < e; k += 32) atomicAdd(I.res + ldg(I.col + k), share);
-    unsigned base = 0;
-    if (lane == 0) {
-      base = atomicAdd(&I.ctl->check, I.check_size);
-      st[kStatEdges] += e - s;
-    }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    for (unsigned r = 0; r < I.check_size; r += 32) {
-      const unsigned k = r + lane;
-      int u = 0;
-      bool want = false;
-      if (k < I.check_size) {
-        u = (int)((base + k) % (unsigned)I.n);
-        want = pr_try_enqueue(I, u);
-      }
-      warp_push(ws, want, u);
-      warp_maybe_flush(ws, I, L, st);
-    }
-  }
-
-  __device__ static int warp_idle(WarpSmem& ws, const Instance& I, const Launch& L, unsigned long long* st) {
-    const int lane = threadIdx.x & 31;
-    constexpr int kChunk = kWarpPushCap;  // at most one push per vertex: fits the push buffer
-    int k = 0;
-    unsigned T = 0;
-    if (lane == 0) k = ld_relaxed(&I.ctl->finished) ? -4 : pr_claim_chunk(I, kChunk, T);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    T = __shfl_sync(0xffffffffu, T, 0);
-    if (k == -4) return 1;
-    if (k == -1) return 0;
-    if (k == -2) {
-      unsigned base = 0;
-      if (lane == 0) base = atomicAdd(&I.ctl->check, 32u);
-      base = __shfl_sync(0xffffffffu, base, 0);
-      const int u = (int)((base + lane) % (unsigned)I.n);
-      warp_push(ws, pr_try_enqueue(I, u), u);
-      warp_flush(ws, I, 0, L, st);
-      return 0;
-    }
-    const int v0 = k * kChunk, v1 = min(I.n, v0 + kChunk);
-    for (int r = v0; r < v1; r += 32) {
-      const int u = r + lane;
-      warp_push(ws, u < v1 && pr_try_enqueue(I, u), u);
-    }
-    const int pushed = ws.npush;
-    warp_flush(ws, I, 0, L, st);
-    if (pushed) return 0;
-    int done = 0;
-    if (lane == 0) done = pr_record_clean(I, T, (unsigned)(v1 - v0)) ? 1 : 0;
-    return __shfl_sync(0xffffffffu, done, 0);
-  }
-};
 
 const void* pr_persistent_kernel(int worker) { return persistent_kernel_ptr<PrBody>(worker); }
 const void* pr_discrete_kernel(int worker) { return discrete_kernel_ptr<PrBody>(worker); }

@@ -149,8 +149,18 @@ __global__ void next_generation_kernel(Instance* insts, int ninst, DevCtl* ctl) 
   }
 }
 
-__global__ void finalize_kernel(DevCtl* ctl) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) ctl->dirty = ctl->status != 0 ? 1 : 0;
+// The rings are clean after a run only if it succeeded and every instance ended with as many
+// tasks completed as pushed (then every written slot was taken and freed).
+__global__ void finalize_kernel(const Instance* insts, int ninst, DevCtl* ctl) {
+  __shared__ int unbalanced;
+  if (threadIdx.x == 0) unbalanced = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < ninst; i += blockDim.x) {
+    const unsigned long long w = insts[i].ctl->word;
+    if ((unsigned)(w >> 32) != (unsigned)w) unbalanced = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ctl->dirty = (ctl->status != 0 || unbalanced) ? 1 : 0;
 }
 
 cudaError_t launch_prepare(Instance* d_insts, int ninst, int max_n, DevCtl* d_ctl, uint32_t flags, unsigned window,
@@ -169,9 +179,9 @@ cudaError_t launch_next_generation(Instance* d_insts, int ninst, DevCtl* d_ctl, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(DevCtl* d_ctl, cudaStream_t s) {
+cudaError_t launch_finalize(const Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s) {
   count_launches(1);
-  finalize_kernel<<<1, 32, 0, s>>>(d_ctl);
+  finalize_kernel<<<1, 256, 0, s>>>(d_insts, ninst, d_ctl);
   return cudaGetLastError();
 }
 

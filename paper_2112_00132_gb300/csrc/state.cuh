@@ -27,7 +27,7 @@ cudaError_t launch_prepare(Instance* d_insts, int ninst, int max_n, DevCtl* d_ct
                            cudaStream_t s);
 cudaError_t launch_pr_init(Instance* d_insts, int ninst, int64_t max_nnz, cudaStream_t s);
 cudaError_t launch_next_generation(Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
-cudaError_t launch_finalize(DevCtl* d_ctl, cudaStream_t s);
+cudaError_t launch_finalize(const Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
 
 const void* bfs_persistent_kernel(int worker);
 const void* bfs_discrete_kernel(int worker);

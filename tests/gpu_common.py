@@ -58,4 +58,5 @@ def configs(atos):
         "discrete-cta": q("discrete-cta"),
         "discrete-cta64": q("discrete-cta", worker_size=64, fetch_size=32),
         "discrete-warp": q("discrete-warp"),
+        "bsp": q("bsp"),
     }

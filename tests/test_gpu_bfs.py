@@ -26,7 +26,7 @@ def test_bfs_bit_exact_all_configs(atos, graphs, gname):
     srcs = bfs_sources(g)
     refs = {s: oracle.bfs(g, s) for s in srcs}
     with atos.Graph.from_csr(g) as G:
-        for cname, cfg in list(configs(atos).items()) + [("bsp", atos.queue_config("bsp"))]:
+        for cname, cfg in configs(atos).items():
             try:
                 depths, st = G.bfs(srcs, cfg=cfg)
             except atos.AtosError as e:

@@ -138,3 +138,22 @@ def test_pagerank_full_size_rmat22_certificate(atos):
     assert st.status == 0 and bound <= PR_L1_TOL and st.error_bound <= PR_L1_TOL
     print(f"rmat22 pagerank: bound {bound:.3e} (device {st.error_bound:.3e}), {st.tasks} tasks, "
           f"{st.edges} edge pushes, {st.ms:.1f} ms")
+
+
+@pytest.mark.parametrize("worker", [1024, 512, 32])
+def test_repeated_runs_leave_scratch_clean(atos, worker):
+    """Every successful run must leave no queued bit set and no ring slot occupied, or the next
+    run on the same graph object could take a stale item (a race in the final PageRank sweep
+    once left items pushed after termination)."""
+    g = gg.clique(40)
+    ref = pr_reference(g)
+    cfg = atos.queue_config(worker_size=worker, fetch_size=32 if worker == 32 else worker)
+    with atos.Graph.from_csr(g) as G:
+        for rep in range(12):
+            rank, st = G.pagerank(ALPHA, EPS, cfg=cfg)
+            assert np.abs(rank.cpu().numpy() - ref).sum() <= PR_L1_TOL, f"rep {rep}"
+            assert G.scratch_check() == (0, 0), f"rep {rep}: {G.scratch_check()}"
+            colors, k, _ = G.color(cfg=cfg)
+            assert k == 40 and G.scratch_check() == (0, 0)
+            G.bfs([rep % 40], cfg=cfg)
+            assert G.scratch_check()[1] == 0
