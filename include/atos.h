@@ -44,6 +44,7 @@ extern "C" {
 #define ATOS_ERR_TIMEOUT (-5)        /* a device-side wait exceeded spin_limit_ns */
 #define ATOS_ERR_CUDA (-6)           /* a CUDA runtime call failed (no device, launch error...) */
 #define ATOS_ERR_UNSUPPORTED (-7)    /* configuration not built (e.g. this worker size) */
+#define ATOS_ERR_BUSY (-8)           /* serving: no free slot or not enough arena memory now */
 
 /* ------------------------------------------------------------------ configuration */
 #define ATOS_WORKER_WARP 32 /* worker_size == 32: one warp per worker (persist-32) */
@@ -219,6 +220,72 @@ int atos_batch_info(atos_batch_t b, int32_t* ninst, int32_t* window, int32_t* gr
 
 /* Frees a batch (synchronises the device first).  NULL is a no-op. */
 int atos_batch_destroy(atos_batch_t b);
+
+/* ------------------------------------------------------------------ serving */
+
+/* Completion record of a served request. */
+typedef struct atos_completion {
+  int64_t id;          /* the id atos_server_submit returned */
+  int32_t status;      /* ATOS_OK or the device status of the epoch that ended the request */
+  int32_t app;         /* ATOS_APP_* */
+  int32_t graph;
+  int32_t num_colors;  /* colouring */
+  int64_t tasks;       /* tasks processed for this request */
+  int64_t edges;       /* neighbour entries read for this request */
+  int64_t epochs;      /* server epochs run so far (when the request completed) */
+  double error_bound;  /* PageRank: 2 ||r||_1 / ((1 - alpha) sum p) from the residue invariant */
+} atos_completion;
+
+typedef struct atos_server_s* atos_server_t;
+
+/* A request server over resident graphs (continuous batching).  max_slots: requests in flight
+ * at most; budget_bytes: device memory for the requests' scratch (ring, pending tickets,
+ * PageRank residues, queued bits), allocated first-fit per request and released at completion.
+ * cfg: persistent CTA workers only (ATOS_ERR_UNSUPPORTED otherwise).  Graphs must outlive the
+ * server. */
+int atos_server_create(const atos_graph_t* graphs, int32_t ngraphs, int32_t max_slots, int64_t budget_bytes,
+                       const atos_config* cfg, atos_server_t* out);
+
+/* Admits a request if a slot is free and its scratch fits in the arena now (else ATOS_ERR_BUSY,
+ * nothing changed) and initialises its state on the server's stream; it runs from the next
+ * atos_server_step on.  req->out is the caller's DEVICE output (as in atos_instance), written
+ * when the request completes.  *id receives the request id. */
+int atos_server_submit(atos_server_t s, const atos_instance* req, int64_t* id);
+
+/* Runs one epoch: one persistent launch over every admitted request, in which each worker
+ * pauses at a safe point once slice_ns have passed (0 = 1 ms) and leaves the tickets it holds to
+ * the next epoch.  Requests that terminated are finished (PageRank normalised, colours counted),
+ * their completion records queued and their slots and memory released.  Synchronises the
+ * server's stream.  *active_left (may be NULL) receives the requests still in flight.  A lap of
+ * a request's ring must take longer than a slice (rings hold at least 2^20 slots). */
+int atos_server_step(atos_server_t s, int64_t slice_ns, int32_t* active_left);
+
+/* Moves up to max queued completion records to out; *count receives how many. */
+int atos_server_poll(atos_server_t s, atos_completion* out, int32_t max, int32_t* count);
+
+/* Requests in flight, arena bytes in use and in total, epochs run (any pointer may be NULL). */
+int atos_server_info(atos_server_t s, int32_t* active, int64_t* arena_used, int64_t* arena_size, int64_t* epochs);
+
+/* Frees a server (synchronises the device first).  NULL is a no-op. */
+int atos_server_destroy(atos_server_t s);
+
+/* ------------------------------------------------------------------ autotuning */
+
+/* Times candidate configurations of `app` (ATOS_APP_*) on g and returns the fastest in *best
+ * (its device time in *best_ms): CTA workers of 128..1024 threads and warp workers, fixed /
+ * greedy / spread fetch policies, persistent, discrete and BSP strategies, plus the instance
+ * window for multi-source BFS and Check_Size for PageRank (Figure 4's worker-size x
+ * FETCH_SIZE sweep with the kernel strategy of Section 3.4).  Each candidate runs repeats + 1
+ * times (the first warms up); failing candidates are skipped.  sources/nsrc: BFS sources (HOST).
+ * scratch_out: DEVICE output buffer the runs write into (nsrc * n int32 for BFS, n floats for
+ * PageRank, n int32 for colouring).  The winner is cached per graph class (application, log2 n,
+ * log2 average degree, log2 max/average degree).  Synchronises `stream`. */
+int atos_autotune(atos_graph_t g, int32_t app, const int32_t* sources, int32_t nsrc, void* scratch_out,
+                  int32_t repeats, atos_config* best, double* best_ms, void* stream);
+
+/* The configuration cached by atos_autotune for g's graph class and `app`: ATOS_OK, or
+ * ATOS_ERR_UNSUPPORTED (and the defaults in *cfg) when that class has not been tuned. */
+int atos_tuned_config(atos_graph_t g, int32_t app, atos_config* cfg);
 
 /* ------------------------------------------------------------------ allocation-free BFS */
 

@@ -26,6 +26,7 @@ ERR_QUEUE_OVERFLOW = -4
 ERR_TIMEOUT = -5
 ERR_CUDA = -6
 ERR_UNSUPPORTED = -7
+ERR_BUSY = -8
 
 WORKER_WARP = 32
 PERSISTENT, DISCRETE, BSP = 0, 1, 2
@@ -88,6 +89,23 @@ class Instance(ctypes.Structure):
     ]
 
 
+class Completion(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_int64),
+        ("status", ctypes.c_int32),
+        ("app", ctypes.c_int32),
+        ("graph", ctypes.c_int32),
+        ("num_colors", ctypes.c_int32),
+        ("tasks", ctypes.c_int64),
+        ("edges", ctypes.c_int64),
+        ("epochs", ctypes.c_int64),
+        ("error_bound", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class AtosError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -126,6 +144,19 @@ def lib() -> ctypes.CDLL:
         for name in ("atos_batch_create", "atos_batch_run", "atos_batch_run_graph", "atos_batch_stats",
                      "atos_batch_info", "atos_batch_destroy"):
             getattr(L, name).restype = ctypes.c_int
+        L.atos_server_create.argtypes = [vp, i32, i32, i64, P(Config), P(vp)]
+        L.atos_server_submit.argtypes = [vp, P(Instance), P(i64)]
+        L.atos_server_step.argtypes = [vp, i64, P(i32)]
+        L.atos_server_poll.argtypes = [vp, P(Completion), i32, P(i32)]
+        L.atos_server_info.argtypes = [vp, P(i32), P(i64), P(i64), P(i64)]
+        L.atos_server_destroy.argtypes = [vp]
+        for name in ("atos_server_create", "atos_server_submit", "atos_server_step", "atos_server_poll",
+                     "atos_server_info", "atos_server_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+        L.atos_autotune.argtypes = [vp, i32, vp, i32, vp, i32, P(Config), P(ctypes.c_double), vp]
+        L.atos_autotune.restype = ctypes.c_int
+        L.atos_tuned_config.argtypes = [vp, i32, P(Config)]
+        L.atos_tuned_config.restype = ctypes.c_int
         L.atos_bfs_noalloc.argtypes = [vp, vp, i32, i64, i32, vp, vp]
         L.atos_bfs_noalloc.restype = ctypes.c_int
         L.atos_debug_scratch_check.argtypes = [vp, P(ctypes.c_uint64), P(ctypes.c_uint64)]
@@ -269,6 +300,27 @@ class Graph:
                "atos_debug_scratch_check")
         return bits.value, slots.value
 
+    def autotune(self, app: str, sources=None, repeats: int = 2, stream=None):
+        """Times the candidate configurations of ``app`` ("bfs", "pagerank", "color") on this
+        graph; returns (best Config, its device ms) and caches it for the graph's class."""
+        import torch
+        code = {"bfs": APP_BFS, "pagerank": APP_PAGERANK, "color": APP_COLOR}[app]
+        src = np.ascontiguousarray(np.atleast_1d(np.asarray(sources if sources is not None else [0])),
+                                   dtype=np.int32)
+        rows = src.shape[0] if code == APP_BFS else 1
+        scratch = torch.empty((rows, max(self.n, 1)), dtype=torch.int32, device="cuda")
+        best, ms = Config(), ctypes.c_double(0)
+        _check(lib().atos_autotune(self._h, code, src.ctypes.data, src.shape[0], scratch.data_ptr(), repeats,
+                                   ctypes.byref(best), ctypes.byref(ms), _stream_handle(stream)), "atos_autotune")
+        return best, ms.value
+
+    def tuned_config(self, app: str):
+        """The cached tuned Config for this graph's class, or None if the class was not tuned."""
+        code = {"bfs": APP_BFS, "pagerank": APP_PAGERANK, "color": APP_COLOR}[app]
+        cfg = Config()
+        rc = lib().atos_tuned_config(self._h, code, ctypes.byref(cfg))
+        return cfg if rc == OK else None
+
     # ------------------------------------------------------------------------------ apps
 
     def bfs(self, sources, depths=None, cfg: Config | None = None, stream=None, stats: bool = True):
@@ -368,6 +420,88 @@ class Batch:
     def close(self):
         if self._h:
             lib().atos_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching request server over resident graphs (wraps an atos_server_t).
+
+    ``submit`` admits a request now if a slot and arena memory are free (else returns None);
+    ``step`` runs one epoch (a persistent launch bounded by ``slice_ns``) over every admitted
+    request; ``poll`` returns the completion records."""
+
+    def __init__(self, graphs, max_slots: int = 64, budget_bytes: int = 8 << 30, cfg: Config | None = None):
+        self._h = ctypes.c_void_p()
+        self.graphs = list(graphs)
+        handles = (ctypes.c_void_p * len(self.graphs))(*[g._h.value for g in self.graphs])
+        _check(lib().atos_server_create(handles, len(self.graphs), max_slots, int(budget_bytes),
+                                        ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(self._h)),
+               "atos_server_create")
+        self._outputs = {}
+
+    def submit(self, kind: str, graph: int, source: int = 0, alpha: float = 0.85, eps: float = 1e-9, out=None):
+        """Returns (request id, output tensor), or None when the request cannot be admitted now."""
+        import torch
+        n = self.graphs[graph].n
+        q = Instance()
+        q.graph = graph
+        if kind == "bfs":
+            q.app, q.source = APP_BFS, int(source)
+            out = out if out is not None else torch.empty(n, dtype=torch.int32, device="cuda")
+        elif kind == "pagerank":
+            q.app, q.alpha, q.eps = APP_PAGERANK, float(alpha), float(eps)
+            out = out if out is not None else torch.empty(n, dtype=torch.float32, device="cuda")
+        elif kind == "color":
+            q.app = APP_COLOR
+            out = out if out is not None else torch.empty(n, dtype=torch.int32, device="cuda")
+        else:
+            raise ValueError(kind)
+        q.out = out.data_ptr()
+        rid = ctypes.c_int64(-1)
+        rc = lib().atos_server_submit(self._h, ctypes.byref(q), ctypes.byref(rid))
+        if rc == ERR_BUSY:
+            return None
+        _check(rc, "atos_server_submit")
+        self._outputs[rid.value] = out
+        return rid.value, out
+
+    def step(self, slice_ns: int = 1_000_000) -> int:
+        left = ctypes.c_int32(0)
+        _check(lib().atos_server_step(self._h, int(slice_ns), ctypes.byref(left)), "atos_server_step")
+        return left.value
+
+    def poll(self, max_records: int = 4096):
+        buf = (Completion * max_records)()
+        cnt = ctypes.c_int32(0)
+        _check(lib().atos_server_poll(self._h, buf, max_records, ctypes.byref(cnt)), "atos_server_poll")
+        out = []
+        for c in buf[:cnt.value]:
+            d = c.as_dict()
+            d["out"] = self._outputs.pop(c.id, None)
+            out.append(d)
+        return out
+
+    def info(self):
+        a, used, size, ep = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().atos_server_info(self._h, ctypes.byref(a), ctypes.byref(used), ctypes.byref(size),
+                                      ctypes.byref(ep)), "atos_server_info")
+        return {"active": a.value, "arena_used": used.value, "arena_size": size.value, "epochs": ep.value}
+
+    def close(self):
+        if self._h:
+            lib().atos_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

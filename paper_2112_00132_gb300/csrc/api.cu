@@ -350,6 +350,7 @@ const char* atos_status_string(int status) {
     case ATOS_ERR_TIMEOUT: return "device wait exceeded its time budget";
     case ATOS_ERR_CUDA: return "CUDA runtime error";
     case ATOS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case ATOS_ERR_BUSY: return "no free slot or arena memory for the request now";
   }
   return "unknown status";
 }

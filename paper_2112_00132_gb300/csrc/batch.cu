@@ -111,6 +111,26 @@ __global__ void batch_normalise_kernel(const Instance* insts, const InstResult* 
 
 const void* mixed_persistent_kernel(int worker) { return persistent_kernel_ptr<MixedBody>(worker); }
 
+// Finish one instance (PageRank normalisation, colour count) into *d_result (an InstResult).
+cudaError_t batch_finish(Instance* d_inst, int max_n, void* d_result, cudaStream_t s) {
+  cudaMemsetAsync(d_result, 0, sizeof(InstResult), s);
+  int gx = (max_n + 255) / 256;
+  gx = gx < 1 ? 1 : (gx > 256 ? 256 : gx);
+  count_launches(2);
+  batch_reduce_kernel<<<dim3(gx, 1), 256, 0, s>>>(d_inst, (InstResult*)d_result);
+  batch_normalise_kernel<<<dim3(gx, 1), 256, 0, s>>>(d_inst, (const InstResult*)d_result);
+  return cudaGetLastError();
+}
+
+size_t batch_result_bytes() { return sizeof(InstResult); }
+
+void batch_result_read(const void* h_result, double* sum_rank, double* sum_res, int* num_colors) {
+  const InstResult* r = (const InstResult*)h_result;
+  *sum_rank = r->sum_rank;
+  *sum_res = r->sum_res;
+  *num_colors = r->num_colors;
+}
+
 }  // namespace atos
 
 using namespace atos;

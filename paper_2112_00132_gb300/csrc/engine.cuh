@@ -49,7 +49,9 @@ struct alignas(128) QueueCtl {
   int succ;                  // batched launch: instance that takes over this one's workers
   unsigned int gen_begin;    // discrete strategy: current generation [gen_begin, gen_end)
   unsigned int gen_end;
-  char pad3[96];
+  unsigned int orphan_count[2];  // serving: pop tickets left pending by paused workers, per epoch parity
+  unsigned int orphan_head;      // serving: orphans of the previous epoch handed out so far
+  char pad3[84];
 };
 static_assert(sizeof(QueueCtl) == 512, "QueueCtl layout");
 
@@ -75,6 +77,9 @@ struct Instance {
   int32_t _pad1;
   int32_t* color;        // colouring
   unsigned long long* stats;  // kNumStats counters
+  unsigned* orphans[2];  // serving: pending tickets recorded at a pause, by epoch parity
+  uint32_t orphan_cap;
+  int32_t _pad2;
 };
 
 struct Launch {
@@ -90,6 +95,8 @@ struct Launch {
   long long spin_limit_ns;  // budget of any single wait
   long long lifetime_ns;    // budget of a worker's whole run (bounds livelock as well as waits)
   int* fail_site;           // which wait gave up first (diagnostics)
+  long long slice_ns;       // serving: a worker pauses at its next safe point after this long (0 = never)
+  unsigned epoch;           // serving: epoch number (its parity selects the orphan buffers)
 };
 
 // ------------------------------------------------------------------------------------ PTX
@@ -297,6 +304,7 @@ struct CtaSmem {
   int off[BLOCK + 1];
   int aux[BLOCK];
   int push[kPushCap];
+  unsigned tk[BLOCK];  // the pop tickets this CTA holds (a contiguous range or previous-epoch orphans)
   int tmp[33];
   int npush;
   int h, n, flag, cnt;
@@ -439,25 +447,60 @@ __device__ __forceinline__ void flush_stats(const Instance& I, unsigned long lon
 //       called by the whole block when its reserved slots hold nothing: returns 1 when the
 //       instance has terminated, 0 to keep waiting (it may push work, e.g. PageRank's f2).
 
+// Serving: true once this worker's time slice is over (it then pauses at a safe point).
+__device__ __forceinline__ bool slice_over(const Launch& L, unsigned long long t0) {
+  return L.slice_ns > 0 && (long long)(globaltimer() - t0) > L.slice_ns;
+}
+
+// Serving pause: record the tickets this CTA still waits for, so that the next epoch's workers
+// take them over (they may be filled later by a push of this epoch).
+template <int BLOCK, class S>
+__device__ __forceinline__ void cta_orphan_pending(S& sm, bool pending, const Launch& L) {
+  const Instance& I = sm.I;
+  if (pending) {
+    const unsigned w = (L.epoch + 1) & 1;
+    const unsigned idx = atomicAdd(&I.ctl->orphan_count[w], 1u);
+    if (idx < I.orphan_cap) I.orphans[w][idx] = sm.tk[threadIdx.x];
+    else raise_status(L.status, ATOS_ERR_QUEUE_OVERFLOW);
+  }
+}
+
+// Returns 1 when the worker paused (serving slice over), 0 when the instance ended for it
+// (terminated, or the launch failed).
 template <class Body, int BLOCK>
-__device__ void cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const Launch& L,
-                                 unsigned long long* st, unsigned long long t0) {
+__device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const Launch& L,
+                                unsigned long long* st, unsigned long long t0) {
   const Instance& I = sm.I;
   Waiter wait;
   for (;;) {
     if (threadIdx.x == 0) {
       int n = pop_size(I, L, L.fetch);
-      sm.h = (int)atomicAdd(&I.ctl->head, (unsigned)n);
+      int from_orphans = 0;
+      if (L.slice_ns > 0) {  // serving: the previous epoch's pending tickets come first
+        const unsigned r = L.epoch & 1;
+        const unsigned cnt = ld_relaxed_u32(&I.ctl->orphan_count[r]);
+        if (ld_relaxed_u32(&I.ctl->orphan_head) < cnt) {
+          const unsigned o = atomicAdd(&I.ctl->orphan_head, (unsigned)n);
+          if (o < cnt) {
+            n = (int)min((unsigned)n, cnt - o);
+            sm.h = (int)o;
+            from_orphans = 1;
+          }
+        }
+      }
+      if (!from_orphans) sm.h = (int)atomicAdd(&I.ctl->head, (unsigned)n);
       sm.n = n;
+      sm.cnt = from_orphans;
     }
     __syncthreads();
-    const unsigned h = (unsigned)sm.h;
     const int n = sm.n;
+    if ((int)threadIdx.x < n)
+      sm.tk[threadIdx.x] = sm.cnt ? I.orphans[L.epoch & 1][(unsigned)sm.h + threadIdx.x] : (unsigned)sm.h + threadIdx.x;
     bool pending = (int)threadIdx.x < n;
     for (;;) {
       int item = kEmpty;
       if (pending) {
-        item = take_ticket(I, h + threadIdx.x);
+        item = take_ticket(I, sm.tk[threadIdx.x]);
         if (item != kEmpty) pending = false;
       }
       // compact the items taken this round into sm.items
@@ -469,17 +512,22 @@ __device__ void cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const
       if (total > 0) {
         Body::template cta_batch<BLOCK>(sm, total, L, st);
         wait.reset();
-        if (threadIdx.x == 0) sm.flag = must_stop(L, t0) ? 1 : 0;
+        if (threadIdx.x == 0) sm.flag = must_stop(L, t0) ? 1 : (slice_over(L, t0) ? 2 : 0);
         __syncthreads();
-        if (sm.flag) return;
+        if (sm.flag == 1) return 0;
+        if (sm.flag == 2) {
+          cta_orphan_pending<BLOCK>(sm, pending, L);
+          return 1;
+        }
         if (still == 0) break;
         continue;
       }
-      // nothing arrived: termination / failure / budget
+      // nothing arrived: termination / failure / budget / end of the serving slice
       int verdict = Body::template cta_idle<BLOCK>(sm, L, st);
       if (threadIdx.x == 0) {
         int f = verdict;
         if (!f && ld_relaxed(L.status) != 0) f = 2;
+        if (!f && slice_over(L, t0)) f = 3;
         if (!f && !wait.step(L.spin_limit_ns)) {
           raise_timeout(L, kSiteCtaIdle);
           f = 2;
@@ -488,7 +536,11 @@ __device__ void cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const
         sm.flag = f;
       }
       __syncthreads();
-      if (sm.flag) return;
+      if (sm.flag == 3) {
+        cta_orphan_pending<BLOCK>(sm, pending, L);
+        return 1;
+      }
+      if (sm.flag) return 0;
       if (still == 0) break;
     }
   }
@@ -515,15 +567,16 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<BLOCK>::value) cta_persistent
       sm.flag = ld_relaxed(&sm.I.ctl->finished);  // one thread decides for the block
     }
     __syncthreads();
-    if (!sm.flag) cta_run_instance<Body, BLOCK>(sm, L, st, t0);
+    int paused = 0;
+    if (!sm.flag) paused = cta_run_instance<Body, BLOCK>(sm, L, st, t0);
     if (threadIdx.x == 0) {
       flush_stats(sm.I, st);
       int next = -1;
-      if (ld_relaxed(L.status) == 0) {
+      if (!paused && ld_relaxed(L.status) == 0) {
         atomicExch(&sm.I.ctl->finished, 1);
         next = next_instance(inst, L);
       }
-      sm.flag = next;
+      sm.flag = next;  // a paused worker leaves the launch (serving epochs end this way)
     }
     __syncthreads();
     inst = sm.flag;

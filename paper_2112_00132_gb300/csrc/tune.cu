@@ -1,0 +1,128 @@
+// tune.cu -- autotuner: picks worker size, fetch size, fetch policy, strategy and (BFS with many
+// sources) the instance window for one application on one graph by timing the candidates, the
+// sweep of Figure 4 (worker size x FETCH_SIZE) extended with the kernel strategy (Section 3.4).
+//
+// Candidates are run on the caller's graph through the public entry points (each run is checked:
+// a candidate that fails is skipped), timed with the library's own CUDA events, best of
+// `repeats` runs.  The winner is cached per graph class -- application, log2 of the vertex count,
+// log2 of the average degree and log2 of the max/average degree ratio -- so graphs of the same
+// shape reuse it through atos_tuned_config without a new sweep.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "atos.h"
+
+namespace {
+
+using ClassKey = std::tuple<int, int, int, int>;
+std::mutex g_cache_mu;
+std::map<ClassKey, std::pair<atos_config, double>> g_cache;
+
+ClassKey class_of(atos_graph_t g, int app) {
+  int32_t n = 0, maxd = 0;
+  int64_t nnz = 0;
+  atos_graph_info(g, &n, &nnz, &maxd);
+  const double avg = n > 0 ? (double)nnz / n : 0.0;
+  const int ln = n > 0 ? (int)floor(log2((double)n)) : 0;
+  const int ld = avg > 0 ? (int)floor(log2(avg)) : -1;
+  const int lr = avg > 0 ? (int)floor(log2(std::max(1.0, (double)maxd / avg))) : 0;
+  return ClassKey(app, ln, ld, lr);
+}
+
+atos_config make(const char* preset, int worker, int fetch, int policy) {
+  atos_config c;
+  atos_queue_config(&c, preset);
+  if (worker) c.worker_size = worker;
+  if (fetch) c.fetch_size = fetch;
+  if (policy >= 0) c.fetch_policy = policy;
+  return c;
+}
+
+std::vector<atos_config> candidates(int app, int nsrc) {
+  std::vector<atos_config> out;
+  for (int w : {128, 256, 512, 1024}) out.push_back(make(nullptr, w, w, ATOS_FETCH_SPREAD));
+  out.push_back(make(nullptr, 256, 256, ATOS_FETCH_FIXED));
+  out.push_back(make(nullptr, 256, 64, ATOS_FETCH_GREEDY));
+  out.push_back(make(nullptr, 32, 32, ATOS_FETCH_SPREAD));
+  out.push_back(make("persist-warp", 0, 0, -1));
+  out.push_back(make("discrete-cta", 0, 0, -1));
+  out.push_back(make("bsp", 0, 0, -1));
+  if (app == ATOS_APP_PAGERANK) {
+    for (int cs : {8, 128}) {
+      atos_config c = make(nullptr, 512, 512, ATOS_FETCH_SPREAD);
+      c.check_size = cs;
+      out.push_back(c);
+    }
+  }
+  if (app == ATOS_APP_BFS && nsrc > 1) {
+    for (int win : {1, 2, 8, 32}) {
+      if (win >= nsrc) break;
+      atos_config c = make(nullptr, 256, 256, ATOS_FETCH_SPREAD);
+      c.window = win;
+      out.push_back(c);
+    }
+  }
+  return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+int atos_autotune(atos_graph_t g, int32_t app, const int32_t* sources, int32_t nsrc, void* scratch_out,
+                  int32_t repeats, atos_config* best, double* best_ms, void* stream) {
+  if (!g || !best || !scratch_out || repeats < 1) return ATOS_ERR_INVALID_ARG;
+  if (app == ATOS_APP_BFS && (!sources || nsrc < 1)) return ATOS_ERR_INVALID_ARG;
+  if (app != ATOS_APP_BFS && app != ATOS_APP_PAGERANK && app != ATOS_APP_COLOR) return ATOS_ERR_INVALID_ARG;
+  double best_t = INFINITY;
+  atos_config best_c;
+  atos_queue_config(&best_c, nullptr);
+  int tried = 0;
+  for (const atos_config& c : candidates(app, app == ATOS_APP_BFS ? nsrc : 1)) {
+    double t = INFINITY;
+    bool ok = true;
+    for (int r = 0; r <= repeats && ok; ++r) {  // run 0 warms up
+      atos_stats st;
+      int rc;
+      if (app == ATOS_APP_BFS) rc = atos_bfs(g, sources, nsrc, (int32_t*)scratch_out, &c, stream, &st);
+      else if (app == ATOS_APP_PAGERANK) rc = atos_pagerank(g, 0.85f, 1e-9f, (float*)scratch_out, &c, stream, &st);
+      else rc = atos_color(g, (int32_t*)scratch_out, nullptr, &c, stream, &st);
+      if (rc != ATOS_OK) ok = false;
+      else if (r > 0) t = std::min(t, st.ms);
+    }
+    if (!ok) continue;
+    tried++;
+    if (t < best_t) {
+      best_t = t;
+      best_c = c;
+    }
+  }
+  if (!tried) return ATOS_ERR_CUDA;
+  *best = best_c;
+  if (best_ms) *best_ms = best_t;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  g_cache[class_of(g, app)] = std::make_pair(best_c, best_t);
+  return ATOS_OK;
+}
+
+int atos_tuned_config(atos_graph_t g, int32_t app, atos_config* cfg) {
+  if (!g || !cfg) return ATOS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  auto it = g_cache.find(class_of(g, app));
+  if (it == g_cache.end()) {
+    atos_queue_config(cfg, nullptr);
+    return ATOS_ERR_UNSUPPORTED;
+  }
+  *cfg = it->second.first;
+  return ATOS_OK;
+}
+
+}  // extern "C"
