@@ -49,8 +49,10 @@ def parse():
     ap.add_argument("--scale", type=int, default=22, help="RMAT scale of the workload graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--worker", type=int, default=256)
-    ap.add_argument("--fetch", type=int, default=256)
+    ap.add_argument("--worker", type=int, default=256, help="with --no-tune: worker size for every app")
+    ap.add_argument("--fetch", type=int, default=256, help="with --no-tune: fetch size for every app")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use --worker / --fetch")
+    ap.add_argument("--no-compare", action="store_true", help="skip the BSP / unbatched comparisons")
     return ap.parse_args()
 
 
@@ -153,21 +155,30 @@ def run_atos(args, rank: int, world: int):
     atos.lib()
     g, srcs = workload(args.scale)
     stream = torch.cuda.current_stream()
-    cfg = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch)
     G = atos.Graph.from_csr(g, skip_validation=False)
     depths = torch.empty((NSRC, g.n), dtype=torch.int32, device="cuda")
     rank_t = torch.empty(g.n, dtype=torch.float32, device="cuda")
     colors = torch.empty(g.n, dtype=torch.int32, device="cuda")
     deg_t = torch.from_numpy(np.diff(g.row_ptr).astype(np.int64)).cuda()
 
+    # configuration per application: the autotuner's choice (untimed sweep), unless fixed
+    if args.no_tune:
+        cfg_bfs = cfg_pr = cfg_gc = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch)
+        tune_ms = {}
+    else:
+        cfg_bfs, t_b = G.autotune("bfs", srcs, repeats=1, stream=stream)
+        cfg_pr, t_p = G.autotune("pagerank", repeats=1, stream=stream)
+        cfg_gc, t_c = G.autotune("color", repeats=1, stream=stream)
+        tune_ms = {"bfs": round(t_b, 3), "pagerank": round(t_p, 3), "color": round(t_c, 3)}
+
     # warm-up steps with statistics (synchronising), to count the work of a step
     bfs_edges = pr_edges = gc_edges = 0
     pr_tasks = 0
     bfs_stats = pr_stats = gc_stats = None
     for w in range(max(args.warmup, 3)):
-        _, bfs_stats = G.bfs(srcs, depths, cfg=cfg, stream=stream)
-        _, pr_stats = G.pagerank(ALPHA, EPS, rank_t, cfg=cfg, stream=stream)
-        _, ncol, gc_stats = G.color(colors, cfg=cfg, stream=stream)
+        _, bfs_stats = G.bfs(srcs, depths, cfg=cfg_bfs, stream=stream)
+        _, pr_stats = G.pagerank(ALPHA, EPS, rank_t, cfg=cfg_pr, stream=stream)
+        _, ncol, gc_stats = G.color(colors, cfg=cfg_gc, stream=stream)
         pr_edges += pr_stats.edges
         pr_tasks += pr_stats.tasks
         gc_edges += gc_stats.edges
@@ -181,7 +192,6 @@ def run_atos(args, rank: int, world: int):
     comp_nnz = 2 * bfs_edges
 
     # timed steps: no statistics, no host synchronisation inside a step
-    ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)] for k in ("bfs", "pr", "gc")}
     l0 = atos.kernel_launches()
     if world > 1:
         torch.distributed.barrier()
@@ -197,11 +207,11 @@ def run_atos(args, rank: int, world: int):
             e2 = torch.cuda.Event(enable_timing=True)
             e3 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            G.bfs(srcs, depths, cfg=cfg, stream=stream, stats=False)
+            G.bfs(srcs, depths, cfg=cfg_bfs, stream=stream, stats=False)
             e1.record(stream)
-            G.pagerank(ALPHA, EPS, rank_t, cfg=cfg, stream=stream, stats=False)
+            G.pagerank(ALPHA, EPS, rank_t, cfg=cfg_pr, stream=stream, stats=False)
             e2.record(stream)
-            G.color(colors, cfg=cfg, stream=stream, stats=False)
+            G.color(colors, cfg=cfg_gc, stream=stream, stats=False)
             e3.record(stream)
             step_ev.append((e0, e1, e2, e3))
         t_end.record(stream)
@@ -244,12 +254,48 @@ def run_atos(args, rank: int, world: int):
                 "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src, "traffic": None,
                 "algorithmic_bytes": dom_bytes, "launch_ms": round(dom_ms, 3)}
 
+    def brief(c):
+        names = {0: "persistent", 1: "discrete", 2: "bsp"}
+        return {"worker": c.worker_size, "fetch": c.fetch_size, "strategy": names.get(c.strategy, c.strategy),
+                "fetch_policy": c.fetch_policy, "window": c.window, "check_size": c.check_size}
+
+    # comparators (untimed by the step, timed here with the same events): the level-synchronous
+    # BSP form and the unbatched single-query form of the same work
+    comparisons = {}
+    if not args.no_compare:
+        def timed(fn):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            fn()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b)
+        bsp = atos.queue_config("bsp")
+        comparisons["bfs64_bsp_ms"] = round(timed(lambda: G.bfs(srcs, depths, cfg=bsp, stream=stream,
+                                                                  stats=False)), 3)
+        one = torch.empty((1, g.n), dtype=torch.int32, device="cuda")
+
+        def unbatched():
+            for s0 in srcs:
+                G.bfs([int(s0)], one, cfg=cfg_bfs, stream=stream, stats=False)
+        comparisons["bfs64_unbatched_ms"] = round(timed(unbatched), 3)
+        comparisons["pagerank_bsp_ms"] = round(timed(lambda: G.pagerank(ALPHA, EPS, rank_t, cfg=bsp, stream=stream,
+                                                                         stats=False)), 3)
+        comparisons["color_bsp_ms"] = round(timed(lambda: G.color(colors, cfg=bsp, stream=stream, stats=False)), 3)
+        comparisons["step_bsp_ms"] = round(comparisons["bfs64_bsp_ms"] + comparisons["pagerank_bsp_ms"]
+                                           + comparisons["color_bsp_ms"], 3)
+        comparisons["bfs64_batched_ms"] = round(mean(bfs_ms), 3)
+
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32 (BFS, colouring) + f32 (PageRank)", "data": "synthetic",
-        "config": workload_config(g, args, {"worker_size": args.worker, "fetch_size": args.fetch,
-                                            "strategy": "persistent", "parallelism": f"replicas x{world}"}),
+        "config": workload_config(g, args, {"bfs_cfg": brief(cfg_bfs), "pagerank_cfg": brief(cfg_pr),
+                                            "color_cfg": brief(cfg_gc), "autotuned": not args.no_tune,
+                                            "autotune_best_ms": tune_ms, "parallelism": f"replicas x{world}"}),
+        "comparisons": comparisons,
         "roofline": roofline,
         "gpu_launches": launches,
         "breakdown": {
@@ -264,12 +310,12 @@ def run_atos(args, rank: int, world: int):
         "clocks": clocks.summary(),
     }
     if not args.no_e2e:
-        result["e2e"] = run_e2e(args, g, srcs, cfg, bfs_edges + pr_edges + gc_edges, world)
+        result["e2e"] = run_e2e(args, g, srcs, (cfg_bfs, cfg_pr, cfg_gc), bfs_edges + pr_edges + gc_edges, world)
     G.close()
     return result
 
 
-def run_e2e(args, g, srcs, cfg, work, world):
+def run_e2e(args, g, srcs, cfgs, work, world):
     """The same step through the public API from pinned host buffers: upload the CSR, run the
     three calls, read the results back, destroy the graph."""
     import torch
@@ -285,11 +331,13 @@ def run_e2e(args, g, srcs, cfg, work, world):
     rank_t = torch.empty(g.n, dtype=torch.float32, device="cuda")
     colors = torch.empty(g.n, dtype=torch.int32, device="cuda")
 
+    cfg_bfs, cfg_pr, cfg_gc = cfgs
+
     def step():
         G = atos.Graph(rp_h.numpy(), col_h.numpy(), skip_validation=True, stream=stream)
-        G.bfs(srcs, depths, cfg=cfg, stream=stream, stats=False)
-        G.pagerank(ALPHA, EPS, rank_t, cfg=cfg, stream=stream, stats=False)
-        G.color(colors, cfg=cfg, stream=stream, stats=False)
+        G.bfs(srcs, depths, cfg=cfg_bfs, stream=stream, stats=False)
+        G.pagerank(ALPHA, EPS, rank_t, cfg=cfg_pr, stream=stream, stats=False)
+        G.color(colors, cfg=cfg_gc, stream=stream, stats=False)
         depths_h.copy_(depths, non_blocking=True)
         rank_h.copy_(rank_t, non_blocking=True)
         colors_h.copy_(colors, non_blocking=True)

@@ -97,6 +97,7 @@ int atos_autotune(atos_graph_t g, int32_t app, const int32_t* sources, int32_t n
       else rc = atos_color(g, (int32_t*)scratch_out, nullptr, &c, stream, &st);
       if (rc != ATOS_OK) ok = false;
       else if (r > 0) t = std::min(t, st.ms);
+      else if (st.ms > 4.0 * best_t) ok = false;  // the warm-up alone is far slower: not a contender
     }
     if (!ok) continue;
     tried++;

@@ -111,3 +111,15 @@ def test_server_admission_by_footprint(atos, graphs):
         assert S.submit("bfs", 0, 5) is not None  # memory came back
         drain(S, 1_000_000)
     G.close()
+
+
+def test_serving_loop_short_run(atos, graphs):
+    """The Poisson serving loop: every request completes, latencies are reported, and sampled
+    results are correct."""
+    from paper_2112_00132_gb300 import serve
+    res = serve.serve(graphs, rate=400.0, duration=1.5, warmup=0.3, slice_ns=500_000, max_slots=64,
+                      budget_bytes=4 << 30, keep=40)
+    assert res["unfinished"] == 0 and res["completed"] == res["requests"] > 100
+    assert res["p50_ms"] is not None and res["p99_ms"] >= res["p50_ms"] > 0
+    for r in res["kept"]:
+        assert check(graphs[r["graph"]], r["kind"], r["source"], r["out"]), r["kind"]
