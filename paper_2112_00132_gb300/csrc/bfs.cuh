@@ -28,6 +28,7 @@ struct BfsBody {
     __syncthreads();
     int32_t* __restrict__ depth = I.depth;
     constexpr int R = LbsRun<BLOCK>::R;
+    int rounds = 0;
     for (int base = 0; base < total; base += BLOCK * R) {
       int item[R], nb[R], cur[R];
       lbs_round<BLOCK>(sm, I.col, cnt, total, base, item, nb);
@@ -42,7 +43,7 @@ struct BfsBody {
         }
         cta_push(sm, want, nb[j]);
       }
-      if (base + BLOCK * R < total) cta_maybe_flush<BLOCK>(sm, I, L, st);
+      if (base + BLOCK * R < total && flush_round<S>(rounds)) cta_maybe_flush<BLOCK>(sm, I, L, st);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

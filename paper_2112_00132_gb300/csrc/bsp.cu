@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kBlock) pr_bsp_scatter(const int32_t* __restri
       while (i + 1 < F && __ldg(offs + i + 1) <= e) ++i;
       const int v = __ldg(frontier + i);
       const int nb = __ldg(col + __ldg(row_ptr + v) + (e - __ldg(offs + i)));
-      atomicAdd(res + nb, __ldg(share + i));
+      red_add_f32(res + nb, __ldg(share + i));
     }
   }
 }

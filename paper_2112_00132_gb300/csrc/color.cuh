@@ -80,6 +80,7 @@ struct GcBody {
       if (total == 0 && base > 0) break;
       __syncthreads();
       constexpr int R = LbsRun<BLOCK>::R;
+      int rounds = 0;
       for (int r = 0; r < total; r += BLOCK * R) {
         int owner[R], nb[R], c[R];
         lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
@@ -101,7 +102,7 @@ struct GcBody {
           }
           cta_push(sm, push_nb, nb[j]);
         }
-        if (r + BLOCK * R < total) cta_maybe_flush<BLOCK>(sm, I, L, st);
+        if (r + BLOCK * R < total && flush_round<S>(rounds)) cta_maybe_flush<BLOCK>(sm, I, L, st);
       }
       cta_maybe_flush<BLOCK>(sm, I, L, st);
       edges += total;

@@ -137,6 +137,10 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
   asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+// Fire-and-forget float add at L2 (no value returned, so the thread does not wait for it).
+__device__ __forceinline__ void red_add_f32(float* p, float v) {
+  asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -298,7 +302,11 @@ struct LbsRun {
 template <int BLOCK, class Extra>
 struct CtaSmem {
   static constexpr int kRoundPushes = LbsRun<BLOCK>::R * BLOCK;  // most pushes one round can add
-  static constexpr int kPushCap = 2 * kRoundPushes;
+  // push buffer: room for several rounds, so the load-balancing loops check it (a block barrier)
+  // only every kFlushEvery rounds
+  static constexpr int kPushCap = 4 * kRoundPushes < 4096 ? 4 * kRoundPushes
+                                  : (2 * kRoundPushes > 4096 ? 2 * kRoundPushes : 4096);
+  static constexpr int kFlushEvery = kPushCap / kRoundPushes - 1;
   int items[BLOCK];
   int start[BLOCK];
   int off[BLOCK + 1];
@@ -350,11 +358,19 @@ __device__ __forceinline__ void cta_flush(S& sm, const Instance& I, int done, co
   __syncthreads();
 }
 
-// Flush only when the buffer could overflow in the next round of appends.
+// Flush when the buffer could overflow within the next kFlushEvery rounds of appends.
 template <int BLOCK, class S>
 __device__ __forceinline__ void cta_maybe_flush(S& sm, const Instance& I, const Launch& L, unsigned long long* st) {
   __syncthreads();
-  if (sm.npush > S::kPushCap - S::kRoundPushes) cta_flush<BLOCK>(sm, I, 0, L, st);
+  if (sm.npush > S::kPushCap - S::kFlushEvery * S::kRoundPushes) cta_flush<BLOCK>(sm, I, 0, L, st);
+}
+
+// Round counter of a load-balancing loop: true on the rounds after which the buffer is checked.
+template <class S>
+__device__ __forceinline__ bool flush_round(int& rounds) {
+  if (++rounds < S::kFlushEvery) return false;
+  rounds = 0;
+  return true;
 }
 
 // One round of the load-balancing search: thread t takes the R consecutive flattened edges

@@ -93,6 +93,7 @@ struct PrBody {
     if (threadIdx.x == 0) sm.base = atomicAdd(&I.ctl->check, (unsigned)nchk);
     __syncthreads();
     const unsigned base = sm.base;
+    int rounds = 0;
     for (int r = 0; r < nchk; r += BLOCK) {
       const int k = r + threadIdx.x;
       int u = 0;
@@ -102,7 +103,7 @@ struct PrBody {
         want = pr_try_enqueue(I, u);
       }
       cta_push(sm, want, u);
-      if (r + BLOCK < nchk) cta_maybe_flush<BLOCK>(sm, I, L, st);
+      if (r + BLOCK < nchk && flush_round<S>(rounds)) cta_maybe_flush<BLOCK>(sm, I, L, st);
     }
   }
 
@@ -137,7 +138,7 @@ struct PrBody {
       lbs_round<BLOCK>(sm, I.col, cnt, total, base, item, nb);
 #pragma unroll
       for (int j = 0; j < R; ++j)
-        if (item[j] >= 0) atomicAdd(res + nb[j], __int_as_float(sm.aux[item[j]]));
+        if (item[j] >= 0) red_add_f32(res + nb[j], __int_as_float(sm.aux[item[j]]));
     }
     if (threadIdx.x == 0) {
       st[kStatTasks] += cnt;
@@ -208,7 +209,7 @@ struct PrBody {
     share = __shfl_sync(0xffffffffu, share, 0);
     s = __shfl_sync(0xffffffffu, s, 0);
     e = __shfl_sync(0xffffffffu, e, 0);
-    for (int k = s + lane; k < e; k += 32) atomicAdd(I.res + ldg(I.col + k), share);
+    for (int k = s + lane; k < e; k += 32) red_add_f32(I.res + ldg(I.col + k), share);
     unsigned base = 0;
     if (lane == 0) {
       base = atomicAdd(&I.ctl->check, I.check_size);
