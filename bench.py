@@ -43,7 +43,7 @@ L2_BYTES = 129 * 2**20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="atos", choices=["atos", "reference"])
     ap.add_argument("--scale", type=int, default=22, help="RMAT scale of the workload graph")
@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--fetch", type=int, default=256, help="with --no-tune: fetch size for every app")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use --worker / --fetch")
     ap.add_argument("--no-compare", action="store_true", help="skip the BSP / unbatched comparisons")
+    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "batched"],
+                    help="rmat22: the single-graph step (default); batched: 256 graphs x (4 BFS + 1 PageRank) "
+                         "in one batched launch")
     return ap.parse_args()
 
 
@@ -130,6 +133,26 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- replicas (N > 1)
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest replica's time: every rank contributes its own timed-region length and all get
+    the maximum (the job is done when the last replica is)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(work_per_replica: float, total_ms: float, steps: int, world: int):
+    """(ms per step, whole-job GTEPS): `world` independent replicas each did `work_per_replica`
+    edges per step; the job took the slowest replica's time (weak scaling)."""
+    ms_step = total_ms / steps
+    return ms_step, world * work_per_replica / (ms_step * 1e-3) / 1e9
 
 
 # ------------------------------------------------------------------------------- atos arm
@@ -221,14 +244,11 @@ def run_atos(args, rank: int, world: int):
     bfs_ms = [a.elapsed_time(b) for a, b, _, _ in step_ev]
     pr_ms = [b.elapsed_time(c) for _, b, c, _ in step_ev]
     gc_ms = [c.elapsed_time(d) for _, _, c, d in step_ev]
+    total_ms = max_over_ranks(total_ms, world, "cuda")
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
-    ms_step = total_ms / args.steps
     work = bfs_edges + pr_edges + gc_edges
-    value = world * work / (ms_step * 1e-3) / 1e9
+    ms_step, value = replica_throughput(work, total_ms, args.steps, world)
 
     # roofline of the dominant kernel (the call whose kernels take the most time)
     peaks = {}
@@ -239,12 +259,14 @@ def run_atos(args, rank: int, world: int):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     mean = lambda xs: sum(xs) / len(xs)  # noqa: E731
+    pct = lambda xs, q: float(np.percentile(np.asarray(xs), q))  # noqa: E731
     parts = {
         # bytes per launch: PageRank 20 B per push + 8 B per edge push (a col read and a residue
-        # update); BFS 4 B per component entry + 12 B per vertex, per source; colouring 16 B per
-        # entry + 24 B per vertex (assign + check passes)
+        # update); BFS, per source, 8 B per component entry (col read + neighbour depth read) +
+        # 12 B per vertex (row_ptr, depth init and final write); colouring 16 B per entry + 24 B
+        # per vertex (assign + check passes)
         "pagerank_persistent": (mean(pr_ms), 20.0 * pr_tasks + 8.0 * pr_edges),
-        "bfs_persistent_batched": (mean(bfs_ms), NSRC * 12.0 * g.n + 4.0 * comp_nnz),
+        "bfs_persistent_batched": (mean(bfs_ms), NSRC * 12.0 * g.n + 8.0 * comp_nnz),
         "color_persistent": (mean(gc_ms), 16.0 * g.nnz + 24.0 * g.n),
     }
     dom = max(parts, key=lambda k: parts[k][0])
@@ -300,6 +322,8 @@ def run_atos(args, rank: int, world: int):
         "gpu_launches": launches,
         "breakdown": {
             "bfs_ms": round(mean(bfs_ms), 3), "pagerank_ms": round(mean(pr_ms), 3), "color_ms": round(mean(gc_ms), 3),
+            "p50_ms": {k: round(pct(v, 50), 3) for k, v in (("bfs", bfs_ms), ("pagerank", pr_ms), ("color", gc_ms))},
+            "p99_ms": {k: round(pct(v, 99), 3) for k, v in (("bfs", bfs_ms), ("pagerank", pr_ms), ("color", gc_ms))},
             "bfs_gteps": round(bfs_edges / (mean(bfs_ms) * 1e-3) / 1e9, 3),
             "pagerank_gteps": round(pr_edges / (mean(pr_ms) * 1e-3) / 1e9, 3),
             "color_gteps": round(gc_edges / (mean(gc_ms) * 1e-3) / 1e9, 3),
@@ -346,17 +370,226 @@ def run_e2e(args, g, srcs, cfgs, work, world):
 
     step()
     steps = max(1, min(args.steps, 3))
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
-    dt = (time.perf_counter() - t0) / steps
+    dt = max_over_ranks(time.perf_counter() - t0, world, "cuda") / steps
     h2d = 4 * (g.n + 1) + 4 * g.nnz + 4 * NSRC
     d2h = 4 * NSRC * g.n + 4 * g.n + 4 * g.n
     return {"value": round(world * work / dt / 1e9, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 3),
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
             "note": "graph created from pinned host CSR (validation skipped: checked once before), "
                     "results copied back to pinned host memory, inside the timed region"}
+
+
+# ------------------------------------------------------------------- batched-mix workload
+
+BATCH_METRIC = "GTEPS (batched mix: 256 graphs x (4 BFS + 1 PageRank), one batched launch)"
+BATCH_BFS = 4
+
+
+def batched_workload(seed: int = 1):
+    """128 RMAT graphs (scale 10..18) and 128 grids (side 64..1024), 10% of edges deleted each;
+    per graph 4 BFS instances from seeded sources of nonzero degree and one PageRank."""
+    graphs = [gg.materialise(spec) for spec in gg.batched_mix(seed=seed)]
+    specs = []
+    for gi, g in enumerate(graphs):
+        for src in gg.sources(g, BATCH_BFS, seed=seed + gi):
+            specs.append(("bfs", gi, int(src)))
+        specs.append(("pagerank", gi, ALPHA, EPS))
+    return graphs, specs
+
+
+def batched_config(graphs, specs, extra=None):
+    n = sum(g.n for g in graphs)
+    nnz = sum(g.nnz for g in graphs)
+    cfg = {"workload": "batched_mix_256g_bfs4_pr1", "graphs": "128 RMAT (scale U{10..18}, edge factor 16) + 128 "
+           "grids (side U{64..1024}), 10% edge deletion, seed 1", "instances": len(specs),
+           "bfs_instances": sum(1 for sp in specs if sp[0] == "bfs"), "n_total": n, "nnz_total": nnz,
+           "alpha": ALPHA, "eps": EPS,
+           "l2": f"inputs larger than L2: col is {nnz * 4 / 2**20:.0f} MiB in total vs 129 MiB L2 (no flush)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def run_batched(args, rank: int, world: int):
+    import torch
+
+    import paper_2112_00132_gb300 as atos
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    atos.build() if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    atos.lib()
+    graphs, specs = batched_workload()
+    stream = torch.cuda.current_stream()
+    Gs = [atos.Graph.from_csr(g) for g in graphs]
+    cfg = atos.queue_config()
+    B = atos.Batch(Gs, specs, cfg)
+
+    # warm-up through the captured graph; the last one with statistics counts the work
+    for _ in range(max(args.warmup, 3)):
+        B.run(stream=stream, graph=True)
+    _, per = B.stats(stream=stream)
+    bfs_edges = pr_edges = pr_tasks = 0
+    bfs_bytes = 0.0
+    for (kind, gi, *rest), out, st in zip(specs, B.outputs, per):
+        if st.status != 0:
+            raise RuntimeError(f"batched instance {kind} on graph {gi} failed: {st.status}")
+        g = graphs[gi]
+        if kind == "bfs":
+            deg = torch.from_numpy(np.diff(g.row_ptr).astype(np.int64)).cuda()
+            comp = int(((out != 2**31 - 1).to(torch.int64) * deg).sum().item())  # directed entries
+            bfs_edges += comp // 2
+            bfs_bytes += 12.0 * g.n + 8.0 * comp
+        else:
+            pr_edges += st.edges
+            pr_tasks += st.tasks
+    work = bfs_edges + pr_edges
+
+    l0 = atos.kernel_launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clocks:
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        for k in range(args.steps):
+            B.run(stream=stream, graph=True)
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+    launches = atos.kernel_launches() - l0
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), world, "cuda")
+    if world > 1:
+        torch.distributed.barrier()
+    ms_step, value = replica_throughput(work, total_ms, args.steps, world)
+
+    comparisons = {}
+    if not args.no_compare:
+        def timed(fn):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            fn()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b)
+        comparisons["batched_no_graph_ms"] = round(timed(lambda: B.run(stream=stream)), 3)
+        outs = [(torch.empty((BATCH_BFS, g.n), dtype=torch.int32, device="cuda"),
+                 torch.empty(g.n, dtype=torch.float32, device="cuda")) for g in graphs]
+        srcs = [[sp[2] for sp in specs if sp[0] == "bfs" and sp[1] == gi] for gi in range(len(graphs))]
+
+        def unbatched():
+            for gi, G in enumerate(Gs):
+                G.bfs(srcs[gi], outs[gi][0], cfg=cfg, stream=stream, stats=False)
+                G.pagerank(ALPHA, EPS, outs[gi][1], cfg=cfg, stream=stream, stats=False)
+        comparisons["per_graph_calls_ms"] = round(timed(unbatched), 3)
+        del outs
+        comparisons["batched_graph_replay_ms"] = round(statistics.mean(step_ms), 3)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    dom_bytes = bfs_bytes + 20.0 * pr_tasks + 8.0 * pr_edges
+    dom_ms = statistics.mean(step_ms)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    roofline = {"kernel": "batched_mixed_persistent", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "traffic": None,
+                "algorithmic_bytes": dom_bytes, "launch_ms": round(dom_ms, 3)}
+    result = {
+        "metric": BATCH_METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32 (BFS) + f32 (PageRank)", "data": "synthetic",
+        "config": batched_config(graphs, specs, {"window": B.window, "grid": B.grid, "worker": cfg.worker_size,
+                                                 "fetch": cfg.fetch_size, "cuda_graph": True,
+                                                 "parallelism": f"replicas x{world}"}),
+        "comparisons": comparisons, "roofline": roofline, "gpu_launches": launches,
+        "breakdown": {"p50_ms": round(float(np.percentile(step_ms, 50)), 3),
+                      "p99_ms": round(float(np.percentile(step_ms, 99)), 3),
+                      "bfs_graph500_edges": bfs_edges, "pagerank_edge_pushes": pr_edges,
+                      "pagerank_tasks": pr_tasks},
+        "clocks": clocks.summary(),
+    }
+    B.close()
+    for G in Gs:
+        G.close()
+    if not args.no_e2e:
+        result["e2e"] = run_batched_e2e(args, graphs, specs, cfg, work, world)
+    return result
+
+
+def run_batched_e2e(args, graphs, specs, cfg, work, world):
+    """The batched step through the public API from pinned host buffers: create the 256 graphs,
+    build and run the batch, read every instance's output back, destroy everything."""
+    import torch
+
+    import paper_2112_00132_gb300 as atos
+    stream = torch.cuda.current_stream()
+    host = [(torch.from_numpy(g.row_ptr).pin_memory(), torch.from_numpy(g.col).pin_memory()) for g in graphs]
+    outs_h = [torch.empty(graphs[sp[1]].n, dtype=torch.int32 if sp[0] == "bfs" else torch.float32).pin_memory()
+              for sp in specs]
+
+    def step():
+        Gs = [atos.Graph(rp.numpy(), col.numpy(), skip_validation=True, stream=stream) for rp, col in host]
+        with atos.Batch(Gs, specs, cfg) as B:
+            B.run(stream=stream)
+            for o_h, o in zip(outs_h, B.outputs):
+                o_h.copy_(o, non_blocking=True)
+            torch.cuda.synchronize()
+        for G in Gs:
+            G.close()
+
+    step()
+    steps = max(1, min(args.steps, 3))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = max_over_ranks(time.perf_counter() - t0, world, "cuda") / steps
+    h2d = sum(4 * (g.n + 1) + 4 * g.nnz for g in graphs)
+    d2h = sum(4 * graphs[sp[1]].n for sp in specs)
+    return {"value": round(world * work / dt / 1e9, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 3),
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "note": "256 graphs created from pinned host CSR, batch built and run (no graph capture), every "
+                    "instance's output copied back to pinned host memory, inside the timed region"}
+
+
+BATCH_SAMPLE_STRIDE = 4
+
+
+def cpu_baseline_batched(graphs, specs, stride=BATCH_SAMPLE_STRIDE):
+    """Serial oracle on a bounded sample of the batched workload: the BFS instances and two
+    power-iteration sweeps (nnz edge operations each) of every `stride`-th graph."""
+    import oracle
+    oracle.build()
+    work = 0.0
+    t0 = time.perf_counter()
+    for kind, gi, *rest in specs:
+        if gi % stride:
+            continue
+        g = graphs[gi]
+        if kind == "bfs":
+            d = oracle.bfs(g, rest[0])
+            work += np.diff(g.row_ptr)[d != oracle.UNREACHED].sum() / 2
+        else:
+            oracle.pagerank_sweeps(g, ALPHA, 2)
+            work += 2 * g.nnz
+    dt = time.perf_counter() - t0
+    return work, dt
 
 
 # --------------------------------------------------------------------------- CPU oracle arm
@@ -391,6 +624,8 @@ def cpu_baseline(g, srcs):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    if getattr(args, "workload", "rmat22") == "batched":
+        return run_reference_batched(args, world)
     g, srcs = workload(args.scale)
     for _ in range(args.warmup):
         oracle_sample(g, srcs, nbfs=1, sweeps=1, color=False)
@@ -411,6 +646,25 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_reference_batched(args, world):
+    graphs, specs = batched_workload()
+    for _ in range(args.warmup):
+        cpu_baseline_batched(graphs, specs, stride=64)
+    works, times = [], []
+    for _ in range(args.steps):
+        w, dt = cpu_baseline_batched(graphs, specs)
+        works.append(w)
+        times.append(dt)
+    value = sum(works) / sum(times) / 1e9
+    sample = "per step: the 4 BFS instances and 2 FP64 power-iteration sweeps of every 4th graph (64 graphs)"
+    return {"impl": "reference", "metric": BATCH_METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32 + f64",
+            "data": "synthetic", "config": batched_config(graphs, specs, {"strategy": "serial CPU oracle"}),
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -421,6 +675,15 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.impl == "reference":
         res = run_reference(args, rank, world)
+    elif args.workload == "batched":
+        res = run_batched(args, rank, world)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            graphs, specs = batched_workload()
+            w, dt = cpu_baseline_batched(graphs, specs)
+            res["cpu_baseline"] = {"value": round(w / dt / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": "serial C oracle, one thread: the 4 BFS instances and 2 FP64 "
+                                             "power-iteration sweeps of every 4th graph (64 graphs)",
+                                   "seconds": round(dt, 2), "host_cores": os.cpu_count()}
     else:
         res = run_atos(args, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

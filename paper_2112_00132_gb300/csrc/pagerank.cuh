@@ -118,7 +118,7 @@ struct PrBody {
       const int s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
       float share = 0.0f;
       if (r != 0.0f) {
-        atomicAdd(I.rank + v, r);
+        red_add_f32(I.rank + v, r);
         if (e > s) {
           share = I.alpha * r / (float)(e - s);
           deg = e - s;
@@ -201,7 +201,7 @@ struct PrBody {
       s = ldg(I.row_ptr + v);
       e = ldg(I.row_ptr + v + 1);
       if (r != 0.0f) {
-        atomicAdd(I.rank + v, r);
+        red_add_f32(I.rank + v, r);
         if (e > s) share = I.alpha * r / (float)(e - s);
       }
       if (share == 0.0f) e = s;
