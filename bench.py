@@ -279,7 +279,7 @@ def run_atos(args, rank: int, world: int):
     def brief(c):
         names = {0: "persistent", 1: "discrete", 2: "bsp"}
         return {"worker": c.worker_size, "fetch": c.fetch_size, "strategy": names.get(c.strategy, c.strategy),
-                "fetch_policy": c.fetch_policy, "window": c.window, "check_size": c.check_size}
+                "fetch_policy": c.fetch_policy, "window": c.window, "check_size": c.check_size, "flags": c.flags}
 
     # comparators (untimed by the step, timed here with the same events): the level-synchronous
     # BSP form and the unbatched single-query form of the same work

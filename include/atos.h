@@ -61,6 +61,11 @@ extern "C" {
 #define ATOS_FLAG_PHANTOM_TASK 1u /* test hook: count one task that is never pushed, so that the
                                      workers wait for it until spin_limit_ns and report
                                      ATOS_ERR_TIMEOUT (exercises the bounded waits) */
+#define ATOS_FLAG_PR_CROSSING 2u  /* PageRank: a push that lifts a neighbour's residue from <= eps to
+                                     > eps enqueues that neighbour (threshold crossing), in place of
+                                     the Check_Size scan of Algorithm 4 (Section 5.2).  Same fixed
+                                     point and the same final verification sweep; check_size is
+                                     ignored.  Persistent and discrete strategies; BSP ignores it. */
 
 typedef struct atos_config {
   int32_t worker_size;    /* 32 (warp worker) or a CTA worker of 64, 128, 256, 512 or 1024 threads */
@@ -89,6 +94,9 @@ typedef struct atos_stats {
                              to the exact fixed point, residual_l1 / ((1 - alpha) * sum) */
   int32_t num_colors;     /* colouring: colours used */
   int32_t status;         /* device-side status (ATOS_OK or ATOS_ERR_*) */
+  int64_t batches;        /* worker batches that processed at least one task (tasks / batches is
+                             the mean batch; 0 for the BSP strategy) */
+  int64_t idle_polls;     /* pops of persistent workers that found nothing to run */
 } atos_stats;
 
 typedef struct atos_graph_s* atos_graph_t;
@@ -271,12 +279,18 @@ int atos_server_destroy(atos_server_t s);
 
 /* ------------------------------------------------------------------ autotuning */
 
+/* PageRank candidates of atos_autotune whose reported FP64 error bound (atos_stats.error_bound,
+ * L1 distance of the normalised result to the fixed point) exceeds this are not chosen. */
+#define ATOS_TUNE_PR_MAX_ERROR 1e-4
+
 /* Times candidate configurations of `app` (ATOS_APP_*) on g and returns the fastest in *best
  * (its device time in *best_ms): CTA workers of 128..1024 threads and warp workers, fixed /
  * greedy / spread fetch policies, persistent, discrete and BSP strategies, plus the instance
- * window for multi-source BFS and Check_Size for PageRank (Figure 4's worker-size x
- * FETCH_SIZE sweep with the kernel strategy of Section 3.4).  Each candidate runs repeats + 1
- * times (the first warms up); failing candidates are skipped.  sources/nsrc: BFS sources (HOST).
+ * window for multi-source BFS, and Check_Size and the threshold-crossing enqueue for PageRank
+ * (Figure 4's worker-size x FETCH_SIZE sweep with the kernel strategy of Section 3.4).  Each
+ * candidate runs repeats + 1 times (the first warms up); failing candidates, and PageRank
+ * candidates whose error bound exceeds ATOS_TUNE_PR_MAX_ERROR, are skipped.  sources/nsrc: BFS
+ * sources (HOST).
  * scratch_out: DEVICE output buffer the runs write into (nsrc * n int32 for BFS, n floats for
  * PageRank, n int32 for colouring).  The winner is cached per graph class (application, log2 n,
  * log2 average degree, log2 max/average degree).  Synchronises `stream`. */

@@ -32,6 +32,7 @@ WORKER_WARP = 32
 PERSISTENT, DISCRETE, BSP = 0, 1, 2
 FETCH_FIXED, FETCH_GREEDY, FETCH_SPREAD = 0, 1, 2
 FLAG_PHANTOM_TASK = 1
+FLAG_PR_CROSSING = 2
 DEVICE_PTRS, BORROW, CHECK_SYMMETRIC, SKIP_VALIDATION = 1, 2, 4, 8
 UNREACHED = 2**31 - 1
 
@@ -68,6 +69,8 @@ class Stats(ctypes.Structure):
         ("error_bound", ctypes.c_double),
         ("num_colors", ctypes.c_int32),
         ("status", ctypes.c_int32),
+        ("batches", ctypes.c_int64),
+        ("idle_polls", ctypes.c_int64),
     ]
 
     def as_dict(self):

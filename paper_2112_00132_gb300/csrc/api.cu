@@ -190,6 +190,7 @@ int check_config(const atos_config& c) {
   if (c.fetch_policy < ATOS_FETCH_FIXED || c.fetch_policy > ATOS_FETCH_SPREAD) return ATOS_ERR_INVALID_ARG;
   if (c.num_blocks < 0 || c.check_size < 0 || c.window < 0 || c.queue_capacity < 0 || c.spin_limit_ns < 0)
     return ATOS_ERR_INVALID_ARG;
+  if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING)) return ATOS_ERR_INVALID_ARG;
   return ATOS_OK;
 }
 
@@ -296,11 +297,13 @@ int collect_stats(atos_graph_s* g, int ninst, cudaStream_t st, atos_stats* out) 
   float ms = 0.f;
   cudaEventElapsedTime(&ms, s.ev0, s.ev1);
   out->ms = ms;
-  out->tasks = out->edges = out->pushes = 0;
+  out->tasks = out->edges = out->pushes = out->batches = out->idle_polls = 0;
   for (int i = 0; i < ninst; ++i) {
     out->tasks += (int64_t)s.h_stats[i * kNumStats + kStatTasks];
     out->edges += (int64_t)s.h_stats[i * kNumStats + kStatEdges];
     out->pushes += (int64_t)s.h_stats[i * kNumStats + kStatPushes];
+    out->batches += (int64_t)s.h_stats[i * kNumStats + kStatBatches];
+    out->idle_polls += (int64_t)s.h_stats[i * kNumStats + kStatIdle];
   }
   out->status = s.h_ctl->status;
   return ATOS_OK;
@@ -579,6 +582,7 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   I.alpha = alpha;
   I.eps = eps;
   I.check_size = cfg.check_size > 0 ? (uint32_t)cfg.check_size : 32u;
+  I.pr_crossing = (cfg.flags & ATOS_FLAG_PR_CROSSING) ? 1 : 0;
   g->s.h_insts[0] = I;
   cfg.window = 1;
   const double exact_sum = (double)n - (double)alpha * (double)g->n_isolated;

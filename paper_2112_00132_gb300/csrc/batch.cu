@@ -173,6 +173,7 @@ struct atos_batch_s {
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  unsigned graph_kernels = 0;  // library kernels one replay of the captured graph launches
 
   ~atos_batch_s() {
     cudaDeviceSynchronize();
@@ -349,6 +350,7 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
       I.alpha = q.alpha;
       I.eps = q.eps;
       I.check_size = cfg.check_size > 0 ? (uint32_t)cfg.check_size : 32u;
+      I.pr_crossing = (cfg.flags & ATOS_FLAG_PR_CROSSING) ? 1 : 0;
       b->exact_sum[i] = (double)I.n - (double)q.alpha * iso;
       b->alpha[i] = q.alpha;
     } else {
@@ -403,7 +405,10 @@ int atos_batch_run_graph(atos_batch_t b, void* stream) {
     BATCH_TRY(cudaStreamSynchronize(st));
     if (!b->cap_stream) BATCH_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     BATCH_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const unsigned long long before = launches_so_far();
     int rc = enqueue_run(b, b->cap_stream);
+    b->graph_kernels = (unsigned)(launches_so_far() - before);
+    uncount_launches(b->graph_kernels);  // captured, not run: each replay counts them
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
     if (rc) {
@@ -416,6 +421,7 @@ int atos_batch_run_graph(atos_batch_t b, void* stream) {
   }
   BATCH_TRY(cudaEventRecord(b->ev0, st));
   BATCH_TRY(cudaGraphLaunch(b->exec, st));
+  count_launches(b->graph_kernels);
   BATCH_TRY(cudaEventRecord(b->ev1, st));
   return ATOS_OK;
 }

@@ -33,7 +33,7 @@ constexpr unsigned long long kFreeSlot = ~0ull;  // a free ring slot (tag 0xffff
 constexpr int32_t kUnreached = INT32_MAX;
 
 enum : int32_t { kAppBfs = 0, kAppPr = 1, kAppGc = 2 };
-enum : int32_t { kStatTasks = 0, kStatEdges = 1, kStatPushes = 2, kStatIdle = 3, kNumStats = 4 };
+enum : int32_t { kStatTasks = 0, kStatEdges = 1, kStatPushes = 2, kStatIdle = 3, kStatBatches = 4, kNumStats = 5 };
 
 // Per-instance queue control block; each hot counter sits on its own 128-byte line.
 struct alignas(128) QueueCtl {
@@ -74,7 +74,7 @@ struct Instance {
   float alpha;
   float eps;
   uint32_t check_size;
-  int32_t _pad1;
+  int32_t pr_crossing;   // PageRank: 1 = threshold-crossing enqueue instead of the Check_Size scan
   int32_t* color;        // colouring
   unsigned long long* stats;  // kNumStats counters
   unsigned* orphans[2];  // serving: pending tickets recorded at a pause, by epoch parity
@@ -526,6 +526,7 @@ __device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const 
       if (got) sm.items[pos] = item;
       const int still = __syncthreads_count(pending);
       if (total > 0) {
+        if (threadIdx.x == 0) st[kStatBatches]++;
         Body::template cta_batch<BLOCK>(sm, total, L, st);
         wait.reset();
         if (threadIdx.x == 0) sm.flag = must_stop(L, t0) ? 1 : (slice_over(L, t0) ? 2 : 0);
@@ -572,7 +573,7 @@ struct MinBlocks {
 template <class Body, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, MinBlocks<BLOCK>::value) cta_persistent_kernel(Launch L) {
   __shared__ CtaSmem<BLOCK, typename Body::Extra> sm;
-  unsigned long long st[kNumStats] = {0, 0, 0, 0};
+  unsigned long long st[kNumStats] = {};
   const unsigned long long t0 = globaltimer();
   int inst = (int)(blockIdx.x % (unsigned)min(L.window, L.ninst));
   if (threadIdx.x == 0) sm.npush = 0;
@@ -605,7 +606,7 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<BLOCK>::value) cta_persistent
 template <class Body, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) cta_discrete_kernel(Launch L) {
   __shared__ CtaSmem<BLOCK, typename Body::Extra> sm;
-  unsigned long long st[kNumStats] = {0, 0, 0, 0};
+  unsigned long long st[kNumStats] = {};
   const int inst = blockIdx.y;
   if (threadIdx.x == 0) {
     sm.I = L.insts[inst];
@@ -625,7 +626,7 @@ __global__ void __launch_bounds__(BLOCK) cta_discrete_kernel(Launch L) {
   if (item != kEmpty) sm.items[pos] = item;
   __syncthreads();
   if (cnt > 0) Body::template cta_batch<BLOCK>(sm, cnt, L, st);
-  if (threadIdx.x == 0) flush_stats(I, st);
+  if (threadIdx.x == 0) st[kStatBatches] += cnt > 0, flush_stats(I, st);
 }
 
 // ----------------------------------------------------------------------- warp worker engine
@@ -711,7 +712,7 @@ __device__ void warp_run_instance(WarpSmem& ws, const Instance& I, const Launch&
           const int it = __shfl_sync(0xffffffffu, item, src);
           Body::warp_item(ws, I, it, L, st);
         }
-        if (lane == 0) st[kStatTasks] += cnt;
+        if (lane == 0) st[kStatTasks] += cnt, st[kStatBatches]++;
         warp_flush(ws, I, cnt, L, st);
         wait.reset();
         int stop = 0;
@@ -743,7 +744,7 @@ __global__ void __launch_bounds__(kWarpBlock) warp_persistent_kernel(Launch L) {
   __shared__ WarpSmem wsm[kWarpBlock / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpSmem& ws = wsm[wid];
-  unsigned long long st[kNumStats] = {0, 0, 0, 0};
+  unsigned long long st[kNumStats] = {};
   const int gw = blockIdx.x * (kWarpBlock / 32) + wid;
   const unsigned long long t0 = globaltimer();
   int inst = gw % min(L.window, L.ninst);
@@ -772,7 +773,7 @@ __global__ void __launch_bounds__(kWarpBlock) warp_discrete_kernel(Launch L) {
   __shared__ WarpSmem wsm[kWarpBlock / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpSmem& ws = wsm[wid];
-  unsigned long long st[kNumStats] = {0, 0, 0, 0};
+  unsigned long long st[kNumStats] = {};
   const Instance I = L.insts[blockIdx.y];
   const int fetch = min(L.fetch, 32);
   const unsigned b = I.ctl->gen_begin, e = I.ctl->gen_end;
@@ -789,7 +790,7 @@ __global__ void __launch_bounds__(kWarpBlock) warp_discrete_kernel(Launch L) {
     got &= got - 1;
     Body::warp_item(ws, I, __shfl_sync(0xffffffffu, item, src), L, st);
   }
-  if (lane == 0) st[kStatTasks] += cnt;
+  if (lane == 0) st[kStatTasks] += cnt, st[kStatBatches] += cnt > 0;
   warp_flush(ws, I, cnt, L, st);
   if (lane == 0) flush_stats(I, st);
 }

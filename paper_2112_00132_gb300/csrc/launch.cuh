@@ -49,6 +49,8 @@ inline int resident_blocks(const void* fn, int threads) {
 
 // Kernels this library has launched (all launch sites add to it; read by atos_kernel_launches).
 void count_launches(unsigned n);
+void uncount_launches(unsigned n);  // launches recorded into a CUDA graph, not run
+unsigned long long launches_so_far();
 
 inline cudaError_t launch_kernel(const void* fn, dim3 grid, int threads, const Launch& L, cudaStream_t s) {
   Launch copy = L;

@@ -16,6 +16,13 @@
 //     instance ends when a sweep that started at quiescence T has covered all n vertices without
 //     enqueueing anything and the queue word still reads (T, T).  Nothing can change a residue
 //     during such a sweep, so every residue is then at most epsilon.
+//
+// Variant (ATOS_FLAG_PR_CROSSING): instead of the Check_Size scan, the scatter uses an atomic add
+// that returns the old residue, and the push that lifts a neighbour from <= epsilon to above it
+// enqueues that neighbour (through the same queued bit).  Every residue above epsilon is then
+// queued or being processed without any scan; the verification sweep above still decides
+// termination (it also catches the rare residue stranded by a pop that clears the bit after a
+// concurrent crossing set it).
 #pragma once
 
 #include "engine.cuh"
@@ -84,6 +91,15 @@ __device__ __forceinline__ bool pr_record_clean(const Instance& I, unsigned T, u
   return false;
 }
 
+// Threshold-crossing scatter: adds s to u's residue; true if this add lifted it from <= eps to
+// above eps and claimed u's queued bit (the caller then enqueues u).
+__device__ __forceinline__ bool pr_add_crossing(const Instance& I, int u, float s) {
+  const float old = atomicAdd(I.res + u, s);
+  if (!(old <= I.eps && old + s > I.eps)) return false;
+  const unsigned bit = 1u << (u & 31);
+  return !(atomicOr(I.qbits + (u >> 5), bit) & bit);
+}
+
 struct PrBody {
   using Extra = NoExtra;
 
@@ -133,18 +149,32 @@ struct PrBody {
     __syncthreads();
     float* __restrict__ res = I.res;
     constexpr int R = LbsRun<BLOCK>::R;
-    for (int base = 0; base < total; base += BLOCK * R) {
-      int item[R], nb[R];
-      lbs_round<BLOCK>(sm, I.col, cnt, total, base, item, nb);
+    if (I.pr_crossing) {
+      int rounds = 0;
+      for (int base = 0; base < total; base += BLOCK * R) {
+        int item[R], nb[R];
+        lbs_round<BLOCK>(sm, I.col, cnt, total, base, item, nb);
 #pragma unroll
-      for (int j = 0; j < R; ++j)
-        if (item[j] >= 0) red_add_f32(res + nb[j], __int_as_float(sm.aux[item[j]]));
+        for (int j = 0; j < R; ++j) {
+          const bool want = item[j] >= 0 && pr_add_crossing(I, nb[j], __int_as_float(sm.aux[item[j]]));
+          cta_push(sm, want, nb[j]);
+        }
+        if (base + BLOCK * R < total && flush_round<S>(rounds)) cta_maybe_flush<BLOCK>(sm, I, L, st);
+      }
+    } else {
+      for (int base = 0; base < total; base += BLOCK * R) {
+        int item[R], nb[R];
+        lbs_round<BLOCK>(sm, I.col, cnt, total, base, item, nb);
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          if (item[j] >= 0) red_add_f32(res + nb[j], __int_as_float(sm.aux[item[j]]));
+      }
     }
     if (threadIdx.x == 0) {
       st[kStatTasks] += cnt;
       st[kStatEdges] += total;
     }
-    check_scan<BLOCK>(sm, cnt * (int)I.check_size, L, st);
+    if (!I.pr_crossing) check_scan<BLOCK>(sm, cnt * (int)I.check_size, L, st);
     __syncthreads();
     cta_flush<BLOCK>(sm, I, cnt, L, st);
   }
@@ -168,6 +198,7 @@ struct PrBody {
     if (k == -4) return 1;
     if (k == -1) return 0;  // the rest of the sweep is in other workers' hands
     if (k == -2) {
+      if (I.pr_crossing) return 0;  // crossings enqueue everything: wait for work or quiescence
       // not quiescent: Algorithm 4's scan as the idle function
       check_scan<BLOCK>(sm, BLOCK, L, st);
       __syncthreads();
@@ -209,12 +240,24 @@ struct PrBody {
     share = __shfl_sync(0xffffffffu, share, 0);
     s = __shfl_sync(0xffffffffu, s, 0);
     e = __shfl_sync(0xffffffffu, e, 0);
+    if (lane == 0) st[kStatEdges] += e - s;
+    if (I.pr_crossing) {
+      for (int k0 = s; k0 < e; k0 += 32) {
+        const int k = k0 + lane;
+        int u = 0;
+        bool want = false;
+        if (k < e) {
+          u = ldg(I.col + k);
+          want = pr_add_crossing(I, u, share);
+        }
+        warp_push(ws, want, u);
+        warp_maybe_flush(ws, I, L, st);
+      }
+      return;
+    }
     for (int k = s + lane; k < e; k += 32) red_add_f32(I.res + ldg(I.col + k), share);
     unsigned base = 0;
-    if (lane == 0) {
-      base = atomicAdd(&I.ctl->check, I.check_size);
-      st[kStatEdges] += e - s;
-    }
+    if (lane == 0) base = atomicAdd(&I.ctl->check, I.check_size);
     base = __shfl_sync(0xffffffffu, base, 0);
     for (unsigned r = 0; r < I.check_size; r += 32) {
       const unsigned k = r + lane;
@@ -240,6 +283,7 @@ struct PrBody {
     if (k == -4) return 1;
     if (k == -1) return 0;
     if (k == -2) {
+      if (I.pr_crossing) return 0;
       unsigned base = 0;
       if (lane == 0) base = atomicAdd(&I.ctl->check, 32u);
       base = __shfl_sync(0xffffffffu, base, 0);

@@ -337,6 +337,7 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
     I.alpha = q->alpha;
     I.eps = q->eps;
     I.check_size = s->cfg.check_size > 0 ? (uint32_t)s->cfg.check_size : 32u;
+    I.pr_crossing = (s->cfg.flags & ATOS_FLAG_PR_CROSSING) ? 1 : 0;
     sl.alpha = q->alpha;
     sl.exact_sum = (double)n - (double)q->alpha * iso;
   } else {

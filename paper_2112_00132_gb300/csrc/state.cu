@@ -19,6 +19,7 @@ namespace atos {
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(unsigned n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 __global__ void prepare_kernel(Instance* insts, DevCtl* ctl, uint32_t flags, unsigned window) {

@@ -3,7 +3,8 @@
 // sweep of Figure 4 (worker size x FETCH_SIZE) extended with the kernel strategy (Section 3.4).
 //
 // Candidates are run on the caller's graph through the public entry points (each run is checked:
-// a candidate that fails is skipped), timed with the library's own CUDA events, best of
+// a candidate that fails, or a PageRank candidate whose FP64 error bound exceeds
+// ATOS_TUNE_PR_MAX_ERROR, is skipped), timed with the library's own CUDA events, best of
 // `repeats` runs.  The winner is cached per graph class -- application, log2 of the vertex count,
 // log2 of the average degree and log2 of the max/average degree ratio -- so graphs of the same
 // shape reuse it through atos_tuned_config without a new sweep.
@@ -61,6 +62,11 @@ std::vector<atos_config> candidates(int app, int nsrc) {
       c.check_size = cs;
       out.push_back(c);
     }
+    for (int w : {256, 512, 1024}) {  // threshold-crossing enqueue instead of the Check_Size scan
+      atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
+      c.flags |= ATOS_FLAG_PR_CROSSING;
+      out.push_back(c);
+    }
   }
   if (app == ATOS_APP_BFS && nsrc > 1) {
     for (int win : {1, 2, 8, 32}) {
@@ -96,6 +102,7 @@ int atos_autotune(atos_graph_t g, int32_t app, const int32_t* sources, int32_t n
       else if (app == ATOS_APP_PAGERANK) rc = atos_pagerank(g, 0.85f, 1e-9f, (float*)scratch_out, &c, stream, &st);
       else rc = atos_color(g, (int32_t*)scratch_out, nullptr, &c, stream, &st);
       if (rc != ATOS_OK) ok = false;
+      else if (app == ATOS_APP_PAGERANK && !(st.error_bound <= ATOS_TUNE_PR_MAX_ERROR)) ok = false;
       else if (r > 0) t = std::min(t, st.ms);
       else if (st.ms > 4.0 * best_t) ok = false;  // the warm-up alone is far slower: not a contender
     }

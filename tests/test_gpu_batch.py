@@ -74,7 +74,9 @@ def test_batch_cuda_graph_replay(atos, graphs):
         check_results(graphs, specs, B.outputs, per)
         for out in B.outputs:
             out.fill_(-5)
+        l0 = atos.kernel_launches()
         B.run(graph=True)  # replay of the captured graph recomputes everything
+        assert atos.kernel_launches() > l0  # a replay counts the library kernels it runs
         total, per = B.stats()
         check_results(graphs, specs, B.outputs, per)
         stream = torch.cuda.Stream()
@@ -118,3 +120,19 @@ def test_batch_invalid(atos, graphs):
         atos.Batch([G], [("bfs", 0, 0)], atos.queue_config("discrete-cta"))
     assert e.value.status == atos.abi.ERR_UNSUPPORTED
     G.close()
+
+
+@pytest.mark.parametrize("worker", [256, 1024, 32])
+def test_mixed_batch_pagerank_crossing(atos, graphs, worker):
+    """The threshold-crossing PageRank variant inside a mixed batch: per-instance results unchanged."""
+    Gs = [atos.Graph.from_csr(g) for g in graphs]
+    specs = mixed_specs(graphs, per_graph_bfs=2)
+    cfg = atos.queue_config(worker_size=worker, fetch_size=32 if worker == 32 else worker,
+                            flags=atos.FLAG_PR_CROSSING)
+    with atos.Batch(Gs, specs, cfg) as B:
+        B.run(graph=True)
+        total, per = B.stats()
+        assert total.status == 0
+        check_results(graphs, specs, B.outputs, per)
+    for G in Gs:
+        G.close()

@@ -127,16 +127,18 @@ def test_color_full_size_rmat22(atos):
     print(f"rmat22 colouring: {k} colours (serial greedy {greedy}), {st.tasks / g.n:.3f} tasks per vertex")
 
 
-def test_pagerank_full_size_rmat22_certificate(atos):
+@pytest.mark.parametrize("worker", [256, 1024])
+def test_pagerank_full_size_rmat22_certificate(atos, worker):
     """RMAT 22 is too large for the FP64 power iteration in a test; the FP64 residual certificate
     (computed on the CPU from the GPU result) bounds the distance to the fixed point instead."""
     g = gg.rmat(22, 16, seed=1)
+    flags = 0
     with atos.Graph.from_csr(g) as G:
-        rank, st = G.pagerank(ALPHA, EPS)
+        rank, st = G.pagerank(ALPHA, EPS, cfg=atos.queue_config(worker_size=worker, fetch_size=worker))
     q = rank.cpu().numpy().astype(np.float64)
     bound = oracle.pr_error_bound(g, q / q.sum(), ALPHA)
     assert st.status == 0 and bound <= PR_L1_TOL and st.error_bound <= PR_L1_TOL
-    print(f"rmat22 pagerank: bound {bound:.3e} (device {st.error_bound:.3e}), {st.tasks} tasks, "
+    print(f"rmat22 pagerank flags {flags}: bound {bound:.3e} (device {st.error_bound:.3e}), {st.tasks} tasks, "
           f"{st.edges} edge pushes, {st.ms:.1f} ms")
 
 
@@ -157,3 +159,60 @@ def test_repeated_runs_leave_scratch_clean(atos, worker):
             assert k == 40 and G.scratch_check() == (0, 0)
             G.bfs([rep % 40], cfg=cfg)
             assert G.scratch_check()[1] == 0
+
+
+@pytest.mark.parametrize("gname", ["rmat12", "rmat11_del", "grid97x61_del", "star1000", "clique40", "two_parts",
+                                   "path300", "single", "isolated3"])
+def test_pagerank_crossing_all_configs(atos, graphs, gname):
+    """Threshold-crossing enqueue (ATOS_FLAG_PR_CROSSING): the same fixed point, tolerance and
+    bound as Algorithm 4's Check_Size scan, for every worker shape and strategy."""
+    g = graphs[gname]
+    ref = pr_reference(g)
+    with atos.Graph.from_csr(g) as G:
+        for cname, cfg in configs(atos).items():
+            cfg.flags |= atos.FLAG_PR_CROSSING
+            try:
+                rank, st = G.pagerank(ALPHA, EPS, cfg=cfg)
+            except atos.AtosError as e:
+                pytest.fail(f"{gname}/{cname}: {e}; queues {G.queue_state(1)}")
+            q = rank.cpu().numpy().astype(np.float64)
+            l1 = np.abs(q - ref).sum()
+            assert st.status == 0 and l1 <= PR_L1_TOL, f"{gname}/{cname}: L1 {l1}"
+            assert l1 <= st.error_bound * 1.0001 + 1e-12, f"{gname}/{cname}: L1 {l1} > bound {st.error_bound}"
+            if cname != "bsp":  # the level-synchronous form uses neither the ring nor the queued bits
+                assert G.scratch_check() == (0, 0), f"{gname}/{cname}: {G.scratch_check()}"
+
+
+def test_pagerank_crossing_full_size_grid_2048(atos):
+    """The crossing rule on the high-diameter mesh (where it beats the Check_Size scan); on
+    RMAT graphs it multiplies the work and its FP32 rank sums lose small residues, which is why
+    the autotuner gates PageRank candidates on their error bound."""
+    g = gg.grid(2048, delete_frac=0.1, seed=1)
+    ref = pr_reference(g)
+    with atos.Graph.from_csr(g) as G:
+        for worker in (256, 1024):
+            cfg = atos.queue_config(worker_size=worker, fetch_size=worker, flags=atos.FLAG_PR_CROSSING)
+            rank, st = G.pagerank(ALPHA, EPS, cfg=cfg)
+            l1 = np.abs(rank.cpu().numpy().astype(np.float64) - ref).sum()
+            assert st.status == 0 and l1 <= PR_L1_TOL and l1 <= st.error_bound * 1.0001, f"cta{worker}: L1 {l1}"
+
+
+def test_unknown_config_flag_rejected(atos):
+    with atos.Graph.from_csr(gg.path(5)) as G:
+        with pytest.raises(atos.AtosError) as e:
+            G.pagerank(ALPHA, EPS, cfg=atos.queue_config(flags=1 << 20))
+        assert e.value.status == atos.abi.ERR_INVALID_ARG
+
+
+def test_stats_batches_and_idle_polls(atos):
+    """tasks / batches is the mean worker batch; persistent CTA workers never run more tasks per
+    batch than their fetch size."""
+    g = gg.rmat(12, 16, seed=1)
+    with atos.Graph.from_csr(g) as G:
+        for worker, fetch in ((256, 256), (1024, 1024), (128, 16), (32, 32)):
+            _, st = G.pagerank(ALPHA, EPS, cfg=atos.queue_config(worker_size=worker, fetch_size=fetch))
+            assert st.batches > 0 and st.tasks <= st.batches * fetch, (worker, st.as_dict())
+            _, st = G.bfs([0], cfg=atos.queue_config(worker_size=worker, fetch_size=fetch))
+            assert 0 < st.batches <= st.tasks <= st.batches * fetch
+        _, st = G.pagerank(ALPHA, EPS, cfg=atos.queue_config("bsp"))
+        assert st.batches == 0
