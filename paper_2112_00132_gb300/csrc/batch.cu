@@ -292,7 +292,7 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
     ring_off[i] = ring_total;
     ring_total += cap;
     res_off[i] = res_total;
-    if (inst[i].app == ATOS_APP_PAGERANK) res_total += (uint64_t)n;
+    if (inst[i].app == ATOS_APP_PAGERANK) res_total += ((uint64_t)n + 63) & ~(uint64_t)63;  // 256-byte aligned rows
     bits_off[i] = bits_total;
     if (inst[i].app != ATOS_APP_BFS) bits_total += (uint64_t)(n + 31) / 32;
     b->max_n = std::max(b->max_n, n);

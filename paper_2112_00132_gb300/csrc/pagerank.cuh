@@ -91,6 +91,59 @@ __device__ __forceinline__ bool pr_record_clean(const Instance& I, unsigned T, u
   return false;
 }
 
+// The Check_Size scan reads residues in groups of 4 consecutive vertices (group g = vertices
+// 4g .. 4g+3): one 16-byte load per group (res rows are 16-byte aligned), and the queued bits of
+// a group sit in one bitmap word, so one atomicOr claims all of its vertices at once.
+__device__ __forceinline__ float4 pr_load_group(const Instance& I, unsigned g) {
+  const int v = (int)(g << 2);
+  if (v + 3 < I.n) return __ldcg(reinterpret_cast<const float4*>(I.res) + g);
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (v < I.n) r.x = __ldcg(I.res + v);
+  if (v + 1 < I.n) r.y = __ldcg(I.res + v + 1);
+  if (v + 2 < I.n) r.z = __ldcg(I.res + v + 2);
+  return r;
+}
+
+// Claims the group's vertices whose residue is above eps and whose queued bit was clear; returns
+// them as a 4-bit mask (bit b = vertex 4g + b).
+__device__ __forceinline__ unsigned pr_claim_group(const Instance& I, unsigned g, float4 r) {
+  const float e = I.eps;
+  const unsigned m = (r.x > e ? 1u : 0u) | (r.y > e ? 2u : 0u) | (r.z > e ? 4u : 0u) | (r.w > e ? 8u : 0u);
+  if (!m) return 0u;
+  const unsigned sh = (g & 7u) * 4u;
+  const unsigned old = atomicOr(I.qbits + (g >> 3), m << sh);
+  return m & ~(old >> sh) & 0xfu;
+}
+
+// Appends to the CTA push buffer the vertices of each thread's claimed groups: bit 4j + b of
+// `claimed` is vertex 4 grp[j] + b.  One block scan places every thread's items; the buffer is
+// flushed first when they do not fit (several times if they exceed it).  Whole block.
+template <int BLOCK, int G, class S>
+__device__ __forceinline__ void cta_push_claimed(S& sm, unsigned claimed, const unsigned (&grp)[G], const Launch& L,
+                                                 unsigned long long* st) {
+  int total;
+  const int off = block_exclusive_scan<BLOCK>(__popc(claimed), sm.tmp, total);  // ends with a barrier
+  for (int w = 0; w < total; w += S::kPushCap) {
+    const int need = min(S::kPushCap, total - w);
+    if (sm.npush + need > S::kPushCap) cta_flush<BLOCK>(sm, sm.I, 0, L, st);
+    const int at = sm.npush - w;
+    int idx = off;
+#pragma unroll
+    for (int j = 0; j < G; ++j) {  // static indices: grp stays in registers
+      unsigned c = (claimed >> (4 * j)) & 0xfu;
+      while (c) {
+        const int b = __ffs(c) - 1;
+        c &= c - 1;
+        if (idx >= w && idx < w + need) sm.push[at + idx] = (int)(grp[j] << 2) + b;
+        ++idx;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sm.npush += need;
+    __syncthreads();
+  }
+}
+
 // Threshold-crossing scatter: adds s to u's residue; true if this add lifted it from <= eps to
 // above eps and claimed u's queued bit (the caller then enqueues u).
 __device__ __forceinline__ bool pr_add_crossing(const Instance& I, int u, float s) {
@@ -103,23 +156,31 @@ __device__ __forceinline__ bool pr_add_crossing(const Instance& I, int u, float 
 struct PrBody {
   using Extra = NoExtra;
 
+  // Algorithm 4's Check_Size scan of `nchk` vertex ids (rounded up to whole groups of 4) from
+  // the round-robin cursor, which counts groups.  Each thread issues its G group loads, then its
+  // G claims, before using any result: two round trips per round instead of one per id.
   template <int BLOCK, class S>
   __device__ static void check_scan(S& sm, int nchk, const Launch& L, unsigned long long* st) {
     const Instance& I = sm.I;
-    if (threadIdx.x == 0) sm.base = atomicAdd(&I.ctl->check, (unsigned)nchk);
+    constexpr int G = BLOCK >= 1024 ? 4 : 2;  // smaller CTAs run under a 40-register cap
+    const unsigned ngroups = ((unsigned)I.n + 3u) >> 2;
+    const int ng = (nchk + 3) >> 2;
+    if (threadIdx.x == 0) sm.base = atomicAdd(&I.ctl->check, (unsigned)ng);
     __syncthreads();
-    const unsigned base = sm.base;
-    int rounds = 0;
-    for (int r = 0; r < nchk; r += BLOCK) {
-      const int k = r + threadIdx.x;
-      int u = 0;
-      bool want = false;
-      if (k < nchk) {
-        u = (int)((base + (unsigned)k) % (unsigned)I.n);
-        want = pr_try_enqueue(I, u);
+    const unsigned gbase = sm.base;
+    for (int r = 0; r < ng; r += BLOCK * G) {
+      unsigned grp[G];
+      float4 v[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        const int k = r + j * BLOCK + (int)threadIdx.x;
+        grp[j] = (gbase + (unsigned)k) % ngroups;
+        v[j] = k < ng ? pr_load_group(I, grp[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      cta_push(sm, want, u);
-      if (r + BLOCK < nchk && flush_round<S>(rounds)) cta_maybe_flush<BLOCK>(sm, I, L, st);
+      unsigned claimed = 0;
+#pragma unroll
+      for (int j = 0; j < G; ++j) claimed |= pr_claim_group(I, grp[j], v[j]) << (4 * j);
+      cta_push_claimed<BLOCK, G>(sm, claimed, grp, L, st);
     }
   }
 
@@ -256,19 +317,27 @@ struct PrBody {
       return;
     }
     for (int k = s + lane; k < e; k += 32) red_add_f32(I.res + ldg(I.col + k), share);
+    warp_check_scan(ws, I, I.check_size, L, st);
+  }
+
+  // The Check_Size scan for a warp: lane k takes group k of the range (see check_scan).
+  __device__ static void warp_check_scan(WarpSmem& ws, const Instance& I, unsigned nchk, const Launch& L,
+                                         unsigned long long* st) {
+    const int lane = threadIdx.x & 31;
+    const unsigned ngroups = ((unsigned)I.n + 3u) >> 2;
+    const unsigned ng = (nchk + 3u) >> 2;
     unsigned base = 0;
-    if (lane == 0) base = atomicAdd(&I.ctl->check, I.check_size);
+    if (lane == 0) base = atomicAdd(&I.ctl->check, ng);
     base = __shfl_sync(0xffffffffu, base, 0);
-    for (unsigned r = 0; r < I.check_size; r += 32) {
+    for (unsigned r = 0; r < ng; r += 32) {
       const unsigned k = r + lane;
-      int u = 0;
-      bool want = false;
-      if (k < I.check_size) {
-        u = (int)((base + k) % (unsigned)I.n);
-        want = pr_try_enqueue(I, u);
+      const unsigned g = (base + k) % ngroups;
+      const unsigned claimed = k < ng ? pr_claim_group(I, g, pr_load_group(I, g)) : 0u;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        warp_push(ws, (claimed >> b) & 1u, (int)(g << 2) + b);
+        warp_maybe_flush(ws, I, L, st);
       }
-      warp_push(ws, want, u);
-      warp_maybe_flush(ws, I, L, st);
     }
   }
 
@@ -284,11 +353,7 @@ struct PrBody {
     if (k == -1) return 0;
     if (k == -2) {
       if (I.pr_crossing) return 0;
-      unsigned base = 0;
-      if (lane == 0) base = atomicAdd(&I.ctl->check, 32u);
-      base = __shfl_sync(0xffffffffu, base, 0);
-      const int u = (int)((base + lane) % (unsigned)I.n);
-      warp_push(ws, pr_try_enqueue(I, u), u);
+      warp_check_scan(ws, I, 128u, L, st);
       warp_flush(ws, I, 0, L, st);
       return 0;
     }
