@@ -430,12 +430,19 @@ def run_batched(args, rank: int, world: int):
     graphs, specs = batched_workload()
     stream = torch.cuda.current_stream()
     Gs = [atos.Graph.from_csr(g) for g in graphs]
-    cfg = atos.queue_config()
+    # the batch's configuration: the autotuner's choice (worker, fetch, window, persistent vs
+    # discrete, PageRank enqueue rule; an untimed sweep), unless fixed
+    if args.no_tune:
+        cfg, tune_ms = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch), None
+    else:
+        cfg, tune_ms = atos.batch_autotune(Gs, specs, repeats=1, stream=stream)
+    use_graph = cfg.strategy == atos.PERSISTENT  # discrete generations are driven by the host
     B = atos.Batch(Gs, specs, cfg)
 
-    # warm-up through the captured graph; the last one with statistics counts the work
+    # warm-up (through the captured graph when persistent); the last one with statistics counts
+    # the work
     for _ in range(max(args.warmup, 3)):
-        B.run(stream=stream, graph=True)
+        B.run(stream=stream, graph=use_graph)
     _, per = B.stats(stream=stream)
     bfs_edges = pr_edges = pr_tasks = 0
     bfs_bytes = 0.0
@@ -461,7 +468,7 @@ def run_batched(args, rank: int, world: int):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         evs[0].record(stream)
         for k in range(args.steps):
-            B.run(stream=stream, graph=True)
+            B.run(stream=stream, graph=use_graph)
             evs[k + 1].record(stream)
         torch.cuda.synchronize()
     launches = atos.kernel_launches() - l0
@@ -482,7 +489,8 @@ def run_batched(args, rank: int, world: int):
             b.record(stream)
             torch.cuda.synchronize()
             return a.elapsed_time(b)
-        comparisons["batched_no_graph_ms"] = round(timed(lambda: B.run(stream=stream)), 3)
+        if use_graph:
+            comparisons["batched_no_graph_ms"] = round(timed(lambda: B.run(stream=stream)), 3)
         outs = [(torch.empty((BATCH_BFS, g.n), dtype=torch.int32, device="cuda"),
                  torch.empty(g.n, dtype=torch.float32, device="cuda")) for g in graphs]
         srcs = [[sp[2] for sp in specs if sp[0] == "bfs" and sp[1] == gi] for gi in range(len(graphs))]
@@ -493,7 +501,7 @@ def run_batched(args, rank: int, world: int):
                 G.pagerank(ALPHA, EPS, outs[gi][1], cfg=cfg, stream=stream, stats=False)
         comparisons["per_graph_calls_ms"] = round(timed(unbatched), 3)
         del outs
-        comparisons["batched_graph_replay_ms"] = round(statistics.mean(step_ms), 3)
+        comparisons["batched_ms"] = round(statistics.mean(step_ms), 3)
 
     peaks = {}
     try:
@@ -513,7 +521,10 @@ def run_batched(args, rank: int, world: int):
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32 (BFS) + f32 (PageRank)", "data": "synthetic",
         "config": batched_config(graphs, specs, {"window": B.window, "grid": B.grid, "worker": cfg.worker_size,
-                                                 "fetch": cfg.fetch_size, "cuda_graph": True,
+                                                 "fetch": cfg.fetch_size, "fetch_policy": cfg.fetch_policy,
+                                                 "strategy": {0: "persistent", 1: "discrete"}.get(cfg.strategy),
+                                                 "flags": cfg.flags, "cuda_graph": use_graph,
+                                                 "autotuned": not args.no_tune, "autotune_best_ms": tune_ms,
                                                  "parallelism": f"replicas x{world}"}),
         "comparisons": comparisons, "roofline": roofline, "gpu_launches": launches,
         "breakdown": {"p50_ms": round(float(np.percentile(step_ms, 50)), 3),

@@ -202,19 +202,22 @@ typedef struct atos_batch_s* atos_batch_t;
  * to one worklist per instance; Section 3's scheduler, several problems at once).  Everything a
  * run needs (instance table, rings, control blocks, PageRank and colouring scratch) is
  * allocated here; the graphs and output buffers must stay alive until atos_batch_destroy.
- * cfg: persistent strategy only (ATOS_ERR_UNSUPPORTED otherwise); cfg->window instances are
- * active at a time (0 = as many as fit in about half of L2).  Errors: ATOS_ERR_INVALID_ARG for
+ * cfg: persistent or discrete strategy (ATOS_ERR_UNSUPPORTED for BSP); with the persistent one
+ * cfg->window instances are active at a time (0 = as many as fit in about half of L2); the
+ * discrete one launches each queue generation of every instance at once.  Errors: ATOS_ERR_INVALID_ARG for
  * NULL pointers, ninst outside [1, 65535], a bad graph index, source, alpha or eps. */
 int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_instance* inst, int32_t ninst,
                       const atos_config* cfg, atos_batch_t* out);
 
-/* Enqueues one run of every instance on `stream` (stream-ordered kernel launches and memsets
- * only: no host synchronisation, no allocation, so the call can be captured in a CUDA graph).
+/* Enqueues one run of every instance on `stream`.  Persistent strategy: stream-ordered kernel
+ * launches and memsets only (no host synchronisation, no allocation), so the call can be captured
+ * in a CUDA graph.  Discrete strategy: the host loop synchronises `stream` after every generation.
  * Calls on one batch must not overlap on the device. */
 int atos_batch_run(atos_batch_t b, void* stream);
 
 /* Same as atos_batch_run, but the first call captures the run into a CUDA graph (on a private
- * stream) and every call replays it with one graph launch on `stream`. */
+ * stream) and every call replays it with one graph launch on `stream`.  Persistent strategy only
+ * (ATOS_ERR_UNSUPPORTED for a discrete batch, whose generations the host drives). */
 int atos_batch_run_graph(atos_batch_t b, void* stream);
 
 /* Synchronises `stream` and reports the last run: *total sums the instances' counters (ms = the
@@ -296,6 +299,16 @@ int atos_server_destroy(atos_server_t s);
  * log2 average degree, log2 max/average degree).  Synchronises `stream`. */
 int atos_autotune(atos_graph_t g, int32_t app, const int32_t* sources, int32_t nsrc, void* scratch_out,
                   int32_t repeats, atos_config* best, double* best_ms, void* stream);
+
+/* Autotuner for a batch: creates the batch under each candidate configuration -- CTA workers of
+ * 128..1024 threads and warp workers, fetch policies, instance windows, the persistent strategy
+ * (replayed as a CUDA graph) and the discrete one, and PageRank's threshold-crossing enqueue --
+ * runs it repeats + 1 times (the first warms up) and returns the fastest in *best (device time of
+ * one run in *best_ms).  Candidates that fail, or whose largest PageRank error bound exceeds
+ * ATOS_TUNE_PR_MAX_ERROR, are skipped.  Arguments as for atos_batch_create; outputs are written
+ * by the runs.  Synchronises `stream`. */
+int atos_batch_autotune(const atos_graph_t* graphs, int32_t ngraphs, const atos_instance* inst, int32_t ninst,
+                        int32_t repeats, atos_config* best, double* best_ms, void* stream);
 
 /* The configuration cached by atos_autotune for g's graph class and `app`: ATOS_OK, or
  * ATOS_ERR_UNSUPPORTED (and the defaults in *cfg) when that class has not been tuned. */

@@ -8,7 +8,7 @@ Python binding.
 """
 from ._binding import (  # noqa: F401
     BSP, DISCRETE, FETCH_FIXED, FETCH_GREEDY, FETCH_SPREAD, FLAG_PHANTOM_TASK, FLAG_PR_CROSSING, PERSISTENT, UNREACHED, WORKER_WARP,
-    AtosError, Batch, Completion, Config, Graph, Instance, Server, Stats, csr_validate, header_functions, kernel_launches, lib, queue_config, status_string,
+    AtosError, Batch, Completion, batch_autotune, Config, Graph, Instance, Server, Stats, csr_validate, header_functions, kernel_launches, lib, queue_config, status_string,
     version,
 )
 from . import _binding as abi  # noqa: F401

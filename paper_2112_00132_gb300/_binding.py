@@ -158,6 +158,8 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).restype = ctypes.c_int
         L.atos_autotune.argtypes = [vp, i32, vp, i32, vp, i32, P(Config), P(ctypes.c_double), vp]
         L.atos_autotune.restype = ctypes.c_int
+        L.atos_batch_autotune.argtypes = [vp, i32, P(Instance), i32, i32, P(Config), P(ctypes.c_double), vp]
+        L.atos_batch_autotune.restype = ctypes.c_int
         L.atos_tuned_config.argtypes = [vp, i32, P(Config)]
         L.atos_tuned_config.restype = ctypes.c_int
         L.atos_bfs_noalloc.argtypes = [vp, vp, i32, i64, i32, vp, vp]
@@ -367,6 +369,47 @@ class Graph:
         return colors, (k.value if stats else None), st
 
 
+def _instance_table(graphs, specs):
+    """(atos_instance array, output tensors) for batch specs (see Batch)."""
+    import torch
+    arr = (Instance * len(specs))()
+    outputs = []
+    for i, spec in enumerate(specs):
+        kind, gi = spec[0], int(spec[1])
+        n = graphs[gi].n if 0 <= gi < len(graphs) else 1  # a bad index is the C ABI's to reject
+        q = arr[i]
+        q.graph = gi
+        if kind == "bfs":
+            q.app, q.source = APP_BFS, int(spec[2])
+            out = torch.empty(n, dtype=torch.int32, device="cuda")
+        elif kind == "pagerank":
+            q.app = APP_PAGERANK
+            q.alpha = float(spec[2]) if len(spec) > 2 else 0.85
+            q.eps = float(spec[3]) if len(spec) > 3 else 1e-9
+            out = torch.empty(n, dtype=torch.float32, device="cuda")
+        elif kind == "color":
+            q.app = APP_COLOR
+            out = torch.empty(n, dtype=torch.int32, device="cuda")
+        else:
+            raise ValueError(kind)
+        q.out = out.data_ptr()
+        outputs.append(out)
+    return arr, outputs
+
+
+def batch_autotune(graphs, specs, repeats: int = 1, stream=None):
+    """Times candidate configurations (worker, fetch, window, persistent vs discrete, PageRank
+    enqueue rule) of a batch of ``specs`` over ``graphs``; returns (best Config, device ms)."""
+    graphs = list(graphs)
+    arr, outputs = _instance_table(graphs, list(specs))
+    handles = (ctypes.c_void_p * len(graphs))(*[g._h.value for g in graphs])
+    best, ms = Config(), ctypes.c_double(0)
+    _check(lib().atos_batch_autotune(handles, len(graphs), arr, len(specs), repeats, ctypes.byref(best),
+                                     ctypes.byref(ms), _stream_handle(stream)), "atos_batch_autotune")
+    del outputs
+    return best, ms.value
+
+
 class Batch:
     """Many instances over several graphs in one persistent launch (wraps an atos_batch_t).
 
@@ -375,32 +418,10 @@ class Batch:
     The graphs must stay open while the batch lives."""
 
     def __init__(self, graphs, specs, cfg: Config | None = None):
-        import torch
         self._h = ctypes.c_void_p()
         self.graphs = list(graphs)
         self.specs = list(specs)
-        arr = (Instance * len(self.specs))()
-        self.outputs = []
-        for i, spec in enumerate(self.specs):
-            kind, gi = spec[0], int(spec[1])
-            n = self.graphs[gi].n if 0 <= gi < len(self.graphs) else 1  # a bad index is the C ABI's to reject
-            q = arr[i]
-            q.graph = gi
-            if kind == "bfs":
-                q.app, q.source = APP_BFS, int(spec[2])
-                out = torch.empty(n, dtype=torch.int32, device="cuda")
-            elif kind == "pagerank":
-                q.app = APP_PAGERANK
-                q.alpha = float(spec[2]) if len(spec) > 2 else 0.85
-                q.eps = float(spec[3]) if len(spec) > 3 else 1e-9
-                out = torch.empty(n, dtype=torch.float32, device="cuda")
-            elif kind == "color":
-                q.app = APP_COLOR
-                out = torch.empty(n, dtype=torch.int32, device="cuda")
-            else:
-                raise ValueError(kind)
-            q.out = out.data_ptr()
-            self.outputs.append(out)
+        arr, self.outputs = _instance_table(self.graphs, self.specs)
         handles = (ctypes.c_void_p * len(self.graphs))(*[g._h.value for g in self.graphs])
         _check(lib().atos_batch_create(handles, len(self.graphs), arr, len(self.specs),
                                        ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(self._h)),

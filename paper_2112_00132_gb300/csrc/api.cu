@@ -257,30 +257,9 @@ int run_instances(atos_graph_s* g, int ninst, int max_n, const atos_config& cfg,
     const int per_block = worker == 32 ? std::min(cfg.fetch_size, 32) * (kWarpBlock / 32) : cfg.fetch_size;
     unsigned gen = 0;
     for (int i = 0; i < ninst; ++i) gen = std::max(gen, s.h_insts[i].prefix_len);
-    for (;;) {
-      if (iters > (1 << 24)) return ATOS_ERR_TIMEOUT;
-      if (gen == 0) {
-        if (app != kAppPr) break;
-        // PageRank: the queue drained; sweep every residue once (Algorithm 4's scan over all
-        // ids) and stop only if nothing exceeds epsilon.
-        ATOS_TRY(pr_verify_sweep(s.d_insts, ninst, max_n, s.d_ctl, st));
-        ATOS_TRY(launch_next_generation(s.d_insts, ninst, s.d_ctl, st));
-        ATOS_TRY(cudaMemcpyAsync(s.h_ctl, s.d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
-        ATOS_TRY(cudaStreamSynchronize(st));
-        if (s.h_ctl->status) break;
-        gen = s.h_ctl->maxgen;
-        if (gen == 0) break;
-      }
-      unsigned gx = (gen + per_block - 1) / per_block;
-      L.nworkers = (int)gx;
-      ATOS_TRY(launch_kernel(fn, dim3(gx, ninst), threads, L, st));
-      ATOS_TRY(launch_next_generation(s.d_insts, ninst, s.d_ctl, st));
-      ATOS_TRY(cudaMemcpyAsync(s.h_ctl, s.d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
-      ATOS_TRY(cudaStreamSynchronize(st));
-      iters++;
-      if (s.h_ctl->status) break;
-      gen = s.h_ctl->maxgen;
-    }
+    ATOS_TRY(discrete_loop(fn, threads, per_block, L, s.d_insts, ninst, max_n, gen, app == kAppPr, s.d_ctl, s.h_ctl,
+                           st, &iters));
+    if (iters > (1 << 24)) return ATOS_ERR_TIMEOUT;
   }
   ATOS_TRY(launch_finalize(s.d_insts, ninst, s.d_ctl, st));
   if (iterations) *iterations = iters;

@@ -71,9 +71,11 @@ struct InstResult {
   int pad;
 };
 
-__global__ void batch_reduce_kernel(const Instance* insts, InstResult* out) {
+// only_finished: skip instances whose worklist has not terminated (serving epochs).
+__global__ void batch_reduce_kernel(const Instance* insts, InstResult* out, int only_finished) {
   const Instance I = insts[blockIdx.y];
   if (I.app == kAppBfs) return;
+  if (only_finished && !ld_relaxed(&I.ctl->finished)) return;
   double a = 0.0, b = 0.0;
   int m = -1;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < I.n; v += gridDim.x * blockDim.x) {
@@ -101,24 +103,27 @@ __global__ void batch_reduce_kernel(const Instance* insts, InstResult* out) {
   }
 }
 
-__global__ void batch_normalise_kernel(const Instance* insts, const InstResult* res) {
+__global__ void batch_normalise_kernel(const Instance* insts, const InstResult* res, int only_finished) {
   const Instance I = insts[blockIdx.y];
   if (I.app != kAppPr) return;
+  if (only_finished && !ld_relaxed(&I.ctl->finished)) return;
   const double inv = 1.0 / res[blockIdx.y].sum_rank;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < I.n; v += gridDim.x * blockDim.x)
     I.rank[v] = (float)((double)I.rank[v] * inv);
 }
 
 const void* mixed_persistent_kernel(int worker) { return persistent_kernel_ptr<MixedBody>(worker); }
+const void* mixed_discrete_kernel(int worker) { return discrete_kernel_ptr<MixedBody>(worker); }
 
-// Finish one instance (PageRank normalisation, colour count) into *d_result (an InstResult).
-cudaError_t batch_finish(Instance* d_inst, int max_n, void* d_result, cudaStream_t s) {
-  cudaMemsetAsync(d_result, 0, sizeof(InstResult), s);
+// Finishes the terminated instances among d_insts[0, ninst) (PageRank normalisation, colour
+// count) into d_results[k] (InstResult each); instances still running are left alone.
+cudaError_t batch_finish_terminated(const Instance* d_insts, int ninst, int max_n, void* d_results, cudaStream_t s) {
+  cudaMemsetAsync(d_results, 0, sizeof(InstResult) * ninst, s);
   int gx = (max_n + 255) / 256;
   gx = gx < 1 ? 1 : (gx > 256 ? 256 : gx);
   count_launches(2);
-  batch_reduce_kernel<<<dim3(gx, 1), 256, 0, s>>>(d_inst, (InstResult*)d_result);
-  batch_normalise_kernel<<<dim3(gx, 1), 256, 0, s>>>(d_inst, (const InstResult*)d_result);
+  batch_reduce_kernel<<<dim3(gx, ninst), 256, 0, s>>>(d_insts, (InstResult*)d_results, 1);
+  batch_normalise_kernel<<<dim3(gx, ninst), 256, 0, s>>>(d_insts, (const InstResult*)d_results, 1);
   return cudaGetLastError();
 }
 
@@ -174,6 +179,8 @@ struct atos_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned graph_kernels = 0;  // library kernels one replay of the captured graph launches
+  const void* fn_discrete = nullptr;
+  unsigned first_gen = 0;      // discrete strategy: the largest virtual prefix (first generation)
 
   ~atos_batch_s() {
     cudaDeviceSynchronize();
@@ -201,7 +208,8 @@ int cuda_rc(cudaError_t e) {
     if (_rc != ATOS_OK) return _rc;    \
   } while (0)
 
-// The stream-ordered sequence of one batch run (no host synchronisation, no allocation).
+// The stream-ordered sequence of one batch run: no allocation, and no host synchronisation with
+// the persistent strategy (the discrete one reads each generation's size back).
 int enqueue_run(atos_batch_s* b, cudaStream_t st) {
   Launch L;
   memset(&L, 0, sizeof(L));
@@ -218,16 +226,27 @@ int enqueue_run(atos_batch_s* b, cudaStream_t st) {
   L.lifetime_ns = L.spin_limit_ns * 16;
   const int workers_per_block = b->cfg.worker_size == 32 ? kWarpBlock / 32 : 1;
   L.nworkers = std::max(1, b->nb * workers_per_block / b->window);
-  BATCH_TRY(launch_prepare(b->d_insts, b->ninst, b->max_n, b->d_ctl, b->cfg.flags, (unsigned)b->window, st));
+  const bool discrete = b->cfg.strategy == ATOS_DISCRETE;
+  BATCH_TRY(launch_prepare(b->d_insts, b->ninst, b->max_n, b->d_ctl, b->cfg.flags,
+                           discrete ? (unsigned)b->ninst : (unsigned)b->window, st));
   if (b->has_pr) BATCH_TRY(launch_pr_init(b->d_insts, b->ninst, b->max_nnz, st));
-  BATCH_TRY(launch_kernel(b->fn, dim3(b->nb), b->threads, L, st));
+  if (discrete) {
+    // one launch per generation over every instance, the generation size read back each time
+    L.window = b->ninst;
+    const int per_block = b->cfg.worker_size == 32 ? std::min(b->cfg.fetch_size, 32) * (kWarpBlock / 32)
+                                                   : b->cfg.fetch_size;
+    BATCH_TRY(discrete_loop(b->fn_discrete, b->threads, per_block, L, b->d_insts, b->ninst, b->max_n, b->first_gen,
+                            b->has_pr, b->d_ctl, b->h_ctl, st, nullptr));
+  } else {
+    BATCH_TRY(launch_kernel(b->fn, dim3(b->nb), b->threads, L, st));
+  }
   BATCH_TRY(launch_finalize(b->d_insts, b->ninst, b->d_ctl, st));
   BATCH_TRY(cudaMemsetAsync(b->d_results, 0, sizeof(InstResult) * b->ninst, st));
   int gx = (b->max_n + 255) / 256;
   gx = std::max(1, std::min(gx, 256));
   count_launches(2);
-  batch_reduce_kernel<<<dim3(gx, b->ninst), 256, 0, st>>>(b->d_insts, b->d_results);
-  batch_normalise_kernel<<<dim3(gx, b->ninst), 256, 0, st>>>(b->d_insts, b->d_results);
+  batch_reduce_kernel<<<dim3(gx, b->ninst), 256, 0, st>>>(b->d_insts, b->d_results, 0);
+  batch_normalise_kernel<<<dim3(gx, b->ninst), 256, 0, st>>>(b->d_insts, b->d_results, 0);
   return cuda_rc(cudaGetLastError());
 }
 
@@ -250,7 +269,7 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
   if (cfg_in) cfg = *cfg_in;
   else atos_queue_config(&cfg, nullptr);
   if (!worker_supported(cfg.worker_size)) return ATOS_ERR_UNSUPPORTED;
-  if (cfg.strategy != ATOS_PERSISTENT) return ATOS_ERR_UNSUPPORTED;
+  if (cfg.strategy != ATOS_PERSISTENT && cfg.strategy != ATOS_DISCRETE) return ATOS_ERR_UNSUPPORTED;
   if (cfg.fetch_size < 1 || cfg.fetch_size > 1024 || (cfg.worker_size != 32 && cfg.fetch_size > cfg.worker_size))
     return ATOS_ERR_INVALID_ARG;
   // validate every instance before allocating anything
@@ -273,6 +292,7 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
   b->ninst = ninst;
   b->threads = block_threads(cfg.worker_size);
   b->fn = mixed_persistent_kernel(cfg.worker_size);
+  b->fn_discrete = mixed_discrete_kernel(cfg.worker_size);
   int rc = ATOS_OK;
   // sizes: one ring per instance, PageRank residues and queued bits, colouring bits
   std::vector<uint64_t> ring_off(ninst), res_off(ninst), bits_off(ninst);
@@ -361,6 +381,7 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
       I.qbits = b->d_qbits + bits_off[i];
     }
     b->h_insts[i] = I;
+    b->first_gen = std::max(b->first_gen, I.prefix_len);
   }
   rc = cuda_rc(cudaMemcpy(b->d_insts, b->h_insts.data(), sizeof(Instance) * ninst, cudaMemcpyHostToDevice));
   DevCtl init;
@@ -399,6 +420,7 @@ int atos_batch_run(atos_batch_t b, void* stream) {
 
 int atos_batch_run_graph(atos_batch_t b, void* stream) {
   if (!b) return ATOS_ERR_INVALID_ARG;
+  if (b->cfg.strategy != ATOS_PERSISTENT) return ATOS_ERR_UNSUPPORTED;  // host-driven generations
   cudaStream_t st = (cudaStream_t)stream;
   if (!b->exec) {
     // capture the run once on a private stream (the legacy default stream cannot be captured)

@@ -33,6 +33,7 @@ const void* pr_discrete_kernel(int worker) { return discrete_kernel_ptr<PrBody>(
 // whose residue still exceeds epsilon (they form the next generation).
 __global__ void pr_sweep_kernel(Instance* insts, int* status) {
   const Instance I = insts[blockIdx.y];
+  if (I.app != kAppPr) return;  // batches mix applications
   const int lane = threadIdx.x & 31;
   const int stride = gridDim.x * blockDim.x;
   for (int r = blockIdx.x * blockDim.x; r < I.n; r += stride) {

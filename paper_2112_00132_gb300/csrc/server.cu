@@ -29,7 +29,7 @@
 namespace atos {
 const void* mixed_persistent_kernel(int worker);
 int graph_device_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, int32_t* n_isolated);
-cudaError_t batch_finish(Instance* d_inst, int max_n, void* d_result, cudaStream_t s);
+cudaError_t batch_finish_terminated(const Instance* d_insts, int ninst, int max_n, void* d_results, cudaStream_t s);
 size_t batch_result_bytes();
 void batch_result_read(const void* h_result, double* sum_rank, double* sum_res, int* num_colors);
 
@@ -163,6 +163,7 @@ struct atos_server_s {
   char* d_arena = nullptr;
   std::vector<Slot> slots;
   Instance* d_slots = nullptr;   // descriptor of every slot
+  Instance* h_slots = nullptr;   // pinned staging of the descriptors (submit copies from it)
   Instance* d_active = nullptr;  // the active slots of the current epoch, compacted
   Instance* h_active = nullptr;  // pinned
   std::vector<int> active_idx;
@@ -180,7 +181,8 @@ struct atos_server_s {
 
   ~atos_server_s() {
     cudaDeviceSynchronize();
-    cudaFree(d_arena), cudaFree(d_slots), cudaFree(d_active), cudaFreeHost(h_active), cudaFree(d_qctl);
+    cudaFree(d_arena), cudaFree(d_slots), cudaFreeHost(h_slots), cudaFree(d_active), cudaFreeHost(h_active);
+    cudaFree(d_qctl);
     cudaFree(d_stats), cudaFreeHost(h_stats), cudaFree(d_ctl), cudaFreeHost(h_ctl), cudaFree(d_fin);
     cudaFreeHost(h_fin), cudaFree(d_results), cudaFreeHost(h_results);
     if (stream) cudaStreamDestroy(stream);
@@ -256,6 +258,7 @@ int atos_server_create(const atos_graph_t* graphs, int32_t ngraphs, int32_t max_
   if (!rc) rc = rc_of(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
   if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_arena, (size_t)budget_bytes));
   if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_slots, sizeof(Instance) * max_slots));
+  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_slots, sizeof(Instance) * max_slots));
   if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_active, sizeof(Instance) * max_slots));
   if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_active, sizeof(Instance) * max_slots));
   if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_qctl, sizeof(QueueCtl) * max_slots));
@@ -265,7 +268,7 @@ int atos_server_create(const atos_graph_t* graphs, int32_t ngraphs, int32_t max_
   if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_ctl, sizeof(DevCtl)));
   if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_fin, sizeof(int) * max_slots));
   if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_fin, sizeof(int) * max_slots));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_results, batch_result_bytes() * max_slots));
+  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_results, batch_result_bytes() * max_slots));  // by active index
   if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_results, batch_result_bytes() * max_slots));
   if (!rc) rc = rc_of(cudaMemsetAsync(s->d_ctl, 0, sizeof(DevCtl), s->stream));
   if (rc) {
@@ -354,12 +357,16 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
   sl.off = off;
   sl.bytes = bytes;
   sl.inst = I;
-  // initialise on the server stream: descriptor, free ring, state (prepare), PageRank residues
-  int rc = rc_of(cudaMemcpyAsync(s->d_slots + slot, &sl.inst, sizeof(Instance), cudaMemcpyHostToDevice, s->stream));
+  // initialise on the server stream: descriptor, free ring, state (prepare), PageRank residues.
+  // Nothing waits here: the descriptor is copied from pinned staging that this slot alone uses
+  // (the slot is not reused before a later step has synchronised the stream), and the next
+  // epoch is ordered after these operations on the same stream.
+  s->h_slots[slot] = I;
+  int rc = rc_of(cudaMemcpyAsync(s->d_slots + slot, s->h_slots + slot, sizeof(Instance), cudaMemcpyHostToDevice,
+                                 s->stream));
   if (!rc) rc = rc_of(cudaMemsetAsync(I.ring, 0xff, (size_t)cap * 8, s->stream));
   if (!rc) rc = rc_of(launch_prepare(s->d_slots + slot, 1, n, s->d_ctl, 0u, 1u, s->stream));
   if (!rc && I.app == kAppPr) rc = rc_of(launch_pr_init(s->d_slots + slot, 1, s->gnnz[q->graph], s->stream));
-  if (!rc) rc = rc_of(cudaStreamSynchronize(s->stream));  // &sl.inst is pageable: the copy must finish
   if (rc) {
     release_slot(s, slot);
     return rc;
@@ -404,31 +411,29 @@ int atos_server_step(atos_server_t s, int64_t slice_ns, int32_t* active_left) {
   L.slice_ns = slice_ns > 0 ? slice_ns : 1000000;
   L.epoch = s->epoch;
   SRV_TRY(launch_kernel(s->fn, dim3(s->nb), s->threads, L, st));
+  // finish the requests that terminated in this epoch on the device (PageRank normalised, colours
+  // counted), then read flags, statistics and results back: one synchronisation per epoch
   count_launches(1);
   server_gather_finished<<<(na + 255) / 256, 256, 0, st>>>(s->d_active, na, s->d_fin);
+  int max_n = 1;
+  for (int k = 0; k < na; ++k) max_n = std::max(max_n, (int)s->h_active[k].n);
+  SRV_TRY(batch_finish_terminated(s->d_active, na, max_n, s->d_results, st));
+  const size_t rb = batch_result_bytes();
   SRV_TRY(cudaMemcpyAsync(s->h_fin, s->d_fin, sizeof(int) * na, cudaMemcpyDeviceToHost, st));
   SRV_TRY(cudaMemcpyAsync(s->h_ctl, s->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+  SRV_TRY(cudaMemcpyAsync(s->h_stats, s->d_stats, sizeof(unsigned long long) * kNumStats * s->max_slots,
+                          cudaMemcpyDeviceToHost, st));
+  SRV_TRY(cudaMemcpyAsync(s->h_results, s->d_results, rb * na, cudaMemcpyDeviceToHost, st));
   SRV_TRY(cudaStreamSynchronize(st));
   s->epoch++;
   s->epochs++;
   const int status = s->h_ctl->status;
-  // finish the terminated requests (or fail every active one if the epoch failed)
-  std::vector<int> finished;
+  // complete the terminated requests (or fail every active one if the epoch failed)
+  std::vector<int> finished, finished_k;
   for (int k = 0; k < na; ++k)
-    if (status != 0 || s->h_fin[k]) finished.push_back(s->active_idx[k]);
-  const size_t rb = batch_result_bytes();
-  for (int i : finished) {
-    Slot& sl = s->slots[i];
-    if (status == 0 && sl.app != ATOS_APP_BFS)
-      SRV_TRY(batch_finish(s->d_slots + i, sl.inst.n, s->d_results + rb * i, st));
-  }
-  if (!finished.empty()) {
-    SRV_TRY(cudaMemcpyAsync(s->h_stats, s->d_stats, sizeof(unsigned long long) * kNumStats * s->max_slots,
-                            cudaMemcpyDeviceToHost, st));
-    SRV_TRY(cudaMemcpyAsync(s->h_results, s->d_results, rb * s->max_slots, cudaMemcpyDeviceToHost, st));
-    SRV_TRY(cudaStreamSynchronize(st));
-  }
-  for (int i : finished) {
+    if (status != 0 || s->h_fin[k]) finished.push_back(s->active_idx[k]), finished_k.push_back(k);
+  for (size_t f = 0; f < finished.size(); ++f) {
+    const int i = finished[f];
     Slot& sl = s->slots[i];
     atos_completion c;
     memset(&c, 0, sizeof(c));
@@ -441,7 +446,7 @@ int atos_server_step(atos_server_t s, int64_t slice_ns, int32_t* active_left) {
     c.epochs = s->epochs;
     double sum_rank = 0, sum_res = 0;
     int ncol = 0;
-    batch_result_read(s->h_results + rb * i, &sum_rank, &sum_res, &ncol);
+    batch_result_read(s->h_results + rb * finished_k[f], &sum_rank, &sum_res, &ncol);
     if (sl.app == ATOS_APP_PAGERANK)
       c.error_bound = 2.0 * sum_res / ((1.0 - (double)sl.alpha) * std::max(sl.exact_sum, 1e-300));
     if (sl.app == ATOS_APP_COLOR) c.num_colors = ncol;

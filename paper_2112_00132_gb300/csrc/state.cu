@@ -188,4 +188,48 @@ cudaError_t launch_finalize(const Instance* d_insts, int ninst, DevCtl* d_ctl, c
   return cudaGetLastError();
 }
 
+cudaError_t pr_verify_sweep(Instance* d_insts, int ninst, int max_n, DevCtl* d_ctl, cudaStream_t s);
+
+cudaError_t discrete_loop(const void* fn, int threads, int per_block, Launch L, Instance* d_insts, int ninst,
+                          int max_n, unsigned first_gen, bool has_pr, DevCtl* d_ctl, DevCtl* h_ctl, cudaStream_t st,
+                          int64_t* iterations) {
+#define DL_TRY(expr)                     \
+  do {                                   \
+    cudaError_t _e = (expr);             \
+    if (_e != cudaSuccess) return _e;    \
+  } while (0)
+  int64_t iters = 0;
+  unsigned gen = first_gen;
+  for (;;) {
+    if (iters > (1 << 24)) break;  // the caller sees the unbalanced queues as a failed run
+    if (gen == 0) {
+      if (!has_pr) break;
+      // PageRank: the queues drained; sweep every residue once (Algorithm 4's scan over all ids)
+      // and stop only if nothing exceeds epsilon
+      DL_TRY(pr_verify_sweep(d_insts, ninst, max_n, d_ctl, st));
+      DL_TRY(launch_next_generation(d_insts, ninst, d_ctl, st));
+      DL_TRY(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+      DL_TRY(cudaStreamSynchronize(st));
+      if (h_ctl->status) break;
+      gen = h_ctl->maxgen;
+      if (gen == 0) break;
+    }
+    const unsigned gx = (gen + per_block - 1) / per_block;
+    L.nworkers = (int)gx;
+    Launch copy = L;
+    void* args[] = {&copy};
+    count_launches(1);
+    DL_TRY(cudaLaunchKernel(fn, dim3(gx, ninst), dim3(threads), args, 0, st));
+    DL_TRY(launch_next_generation(d_insts, ninst, d_ctl, st));
+    DL_TRY(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+    DL_TRY(cudaStreamSynchronize(st));
+    iters++;
+    if (h_ctl->status) break;
+    gen = h_ctl->maxgen;
+  }
+#undef DL_TRY
+  if (iterations) *iterations = iters;
+  return cudaSuccess;
+}
+
 }  // namespace atos

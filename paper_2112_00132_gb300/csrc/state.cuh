@@ -29,6 +29,15 @@ cudaError_t launch_pr_init(Instance* d_insts, int ninst, int64_t max_nnz, cudaSt
 cudaError_t launch_next_generation(Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
 cudaError_t launch_finalize(const Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
 
+// Host loop of the discrete strategy (Section 3.4) over d_insts[0, ninst), after prepare: one
+// launch of `fn` per queue generation (grid: generation slices x instances), until every queue is
+// empty; PageRank instances (has_pr) also need a verification sweep that enqueues nothing.  Reads
+// the generation size back after every launch (h_ctl: pinned mirror of d_ctl).  Returns a
+// cudaError_t; *iterations receives the launches of `fn`.
+cudaError_t discrete_loop(const void* fn, int threads, int per_block, Launch L, Instance* d_insts, int ninst,
+                          int max_n, unsigned first_gen, bool has_pr, DevCtl* d_ctl, DevCtl* h_ctl, cudaStream_t st,
+                          int64_t* iterations);
+
 const void* bfs_persistent_kernel(int worker);
 const void* bfs_discrete_kernel(int worker);
 

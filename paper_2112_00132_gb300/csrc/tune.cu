@@ -57,11 +57,12 @@ std::vector<atos_config> candidates(int app, int nsrc) {
   out.push_back(make("discrete-cta", 0, 0, -1));
   out.push_back(make("bsp", 0, 0, -1));
   if (app == ATOS_APP_PAGERANK) {
-    for (int cs : {8, 128}) {
-      atos_config c = make(nullptr, 512, 512, ATOS_FETCH_SPREAD);
-      c.check_size = cs;
-      out.push_back(c);
-    }
+    for (int w : {512, 1024})
+      for (int cs : {8, 16, 64}) {
+        atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
+        c.check_size = cs;
+        out.push_back(c);
+      }
     for (int w : {256, 512, 1024}) {  // threshold-crossing enqueue instead of the Check_Size scan
       atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
       c.flags |= ATOS_FLAG_PR_CROSSING;
@@ -118,6 +119,67 @@ int atos_autotune(atos_graph_t g, int32_t app, const int32_t* sources, int32_t n
   if (best_ms) *best_ms = best_t;
   std::lock_guard<std::mutex> lock(g_cache_mu);
   g_cache[class_of(g, app)] = std::make_pair(best_c, best_t);
+  return ATOS_OK;
+}
+
+int atos_batch_autotune(const atos_graph_t* graphs, int32_t ngraphs, const atos_instance* inst, int32_t ninst,
+                        int32_t repeats, atos_config* best, double* best_ms, void* stream) {
+  if (!graphs || ngraphs < 1 || !inst || ninst < 1 || !best || repeats < 1) return ATOS_ERR_INVALID_ARG;
+  bool has_pr = false;
+  for (int i = 0; i < ninst; ++i) has_pr |= inst[i].app == ATOS_APP_PAGERANK;
+  std::vector<atos_config> cands;
+  for (int w : {128, 256, 512, 1024}) cands.push_back(make(nullptr, w, w, ATOS_FETCH_SPREAD));
+  cands.push_back(make(nullptr, 256, 64, ATOS_FETCH_GREEDY));
+  cands.push_back(make(nullptr, 32, 32, ATOS_FETCH_SPREAD));
+  for (int win : {8, 64, 512}) {
+    if (win >= ninst) break;
+    atos_config c = make(nullptr, 256, 256, ATOS_FETCH_SPREAD);
+    c.window = win;
+    cands.push_back(c);
+  }
+  cands.push_back(make("discrete-cta", 0, 0, -1));
+  if (has_pr)
+    for (int w : {256, 512}) {
+      atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
+      c.flags |= ATOS_FLAG_PR_CROSSING;
+      cands.push_back(c);
+    }
+  std::vector<atos_stats> per((size_t)ninst);
+  double best_t = INFINITY;
+  atos_config best_c;
+  atos_queue_config(&best_c, nullptr);
+  int tried = 0;
+  for (const atos_config& c : cands) {
+    atos_batch_t b = nullptr;
+    if (atos_batch_create(graphs, ngraphs, inst, ninst, &c, &b) != ATOS_OK) continue;
+    const bool graph = c.strategy == ATOS_PERSISTENT;
+    double t = INFINITY;
+    bool ok = true;
+    for (int r = 0; r <= repeats && ok; ++r) {  // run 0 warms up (and captures the graph)
+      atos_stats total;
+      int rc = graph ? atos_batch_run_graph(b, stream) : atos_batch_run(b, stream);
+      if (rc == ATOS_OK) rc = atos_batch_stats(b, &total, per.data(), stream);
+      if (rc != ATOS_OK) {
+        ok = false;
+        break;
+      }
+      for (int i = 0; i < ninst && ok; ++i)
+        if (inst[i].app == ATOS_APP_PAGERANK && !(per[i].error_bound <= ATOS_TUNE_PR_MAX_ERROR)) ok = false;
+      if (!ok) break;
+      if (r > 0) t = std::min(t, total.ms);
+      else if (total.ms > 4.0 * best_t) ok = false;  // the warm-up alone is far slower: not a contender
+    }
+    atos_batch_destroy(b);
+    if (!ok) continue;
+    tried++;
+    if (t < best_t) {
+      best_t = t;
+      best_c = c;
+    }
+  }
+  if (!tried) return ATOS_ERR_CUDA;
+  *best = best_c;
+  if (best_ms) *best_ms = best_t;
   return ATOS_OK;
 }
 

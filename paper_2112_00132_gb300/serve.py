@@ -10,7 +10,8 @@ the warm-up are served but not counted.
 
 Usage: python -m paper_2112_00132_gb300.serve [--rate 2000] [--duration 10] [--warmup 1]
        [--graphs small|config]   (``config``: 64 graphs of the batched mix plus RMAT 23)
-Prints one JSON line with p50 / p99 latency, achieved rate and throughput.
+       [--rates 100,200,400]     (a sweep: one JSON line per offered rate, graphs uploaded once)
+Prints one JSON line per rate with p50 / p99 latency, achieved rate and throughput.
 """
 from __future__ import annotations
 
@@ -53,11 +54,14 @@ def make_arrivals(rate: float, duration: float, mix, ngraphs: int, seed: int = 1
 
 
 def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), slice_ns=1_000_000, max_slots=256,
-          budget_bytes=None, alpha=0.85, eps=1e-9, seed=1, drain_s=30.0, keep=0, cfg=None):
+          budget_bytes=None, alpha=0.85, eps=1e-9, seed=1, drain_s=30.0, keep=0, cfg=None, graphs=None):
     """Runs the serving loop; returns a summary dict (and up to `keep` finished requests with their
-    outputs under "kept", for checking)."""
+    outputs under "kept", for checking).  `graphs`: resident abi.Graph objects of `csrs` to reuse
+    (created here, and closed at the end, when None)."""
     import torch
-    graphs = [abi.Graph.from_csr(g) for g in csrs]
+    own_graphs = graphs is None
+    if own_graphs:
+        graphs = [abi.Graph.from_csr(g) for g in csrs]
     sources = [gg.sources(g, 4096, seed=seed + 11 * k) if g.nnz else np.zeros(1, np.int32)
                for k, g in enumerate(csrs)]
     if budget_bytes is None:
@@ -116,8 +120,9 @@ def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), sli
     lat_ms = np.array(lat) * 1e3
     info = server.info()
     server.close()
-    for g in graphs:
-        g.close()
+    if own_graphs:
+        for g in graphs:
+            g.close()
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None  # noqa: E731
     achieved = len(lat) / window
     offered = len(measured) / max(1e-9, duration - warmup)
@@ -162,16 +167,23 @@ def main():
     ap.add_argument("--slice-ms", type=float, default=1.0)
     ap.add_argument("--graphs", default="config", choices=["config", "small"])
     ap.add_argument("--max-slots", type=int, default=256)
+    ap.add_argument("--drain", type=float, default=30.0, help="seconds allowed after the last arrival")
+    ap.add_argument("--rates", default="", help="comma-separated offered rates (a sweep); overrides --rate")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
     abi.lib()
     csrs = config_graphs() if args.graphs == "config" else small_graphs()
-    res = serve(csrs, rate=args.rate, duration=args.duration, warmup=args.warmup,
-                slice_ns=int(args.slice_ms * 1e6), max_slots=args.max_slots)
-    res["workload"] = ("64 graphs of the batched mix + RMAT 23" if args.graphs == "config" else "4 small graphs")
-    res["mix"] = "BFS 60% / PageRank 30% / colouring 10%"
-    print(json.dumps(res), flush=True)
+    graphs = [abi.Graph.from_csr(g) for g in csrs]
+    rates = [float(r) for r in args.rates.split(",") if r] or [args.rate]
+    for rate in rates:
+        res = serve(csrs, rate=rate, duration=args.duration, warmup=args.warmup, slice_ns=int(args.slice_ms * 1e6),
+                    max_slots=args.max_slots, drain_s=args.drain, graphs=graphs)
+        res["workload"] = ("64 graphs of the batched mix + RMAT 23" if args.graphs == "config" else "4 small graphs")
+        res["mix"] = "BFS 60% / PageRank 30% / colouring 10%"
+        print(json.dumps(res), flush=True)
+    for g in graphs:
+        g.close()
 
 
 if __name__ == "__main__":

@@ -117,8 +117,12 @@ def test_batch_invalid(atos, graphs):
             atos.Batch([G], bad)
         assert e.value.status == atos.abi.ERR_INVALID_ARG
     with pytest.raises(atos.AtosError) as e:
-        atos.Batch([G], [("bfs", 0, 0)], atos.queue_config("discrete-cta"))
+        atos.Batch([G], [("bfs", 0, 0)], atos.queue_config("bsp"))
     assert e.value.status == atos.abi.ERR_UNSUPPORTED
+    with atos.Batch([G], [("bfs", 0, 0)], atos.queue_config("discrete-cta")) as B:
+        with pytest.raises(atos.AtosError) as e:  # host-driven generations cannot be captured
+            B.run(graph=True)
+        assert e.value.status == atos.abi.ERR_UNSUPPORTED
     G.close()
 
 
@@ -133,6 +137,34 @@ def test_mixed_batch_pagerank_crossing(atos, graphs, worker):
         B.run(graph=True)
         total, per = B.stats()
         assert total.status == 0
+        check_results(graphs, specs, B.outputs, per)
+    for G in Gs:
+        G.close()
+
+
+@pytest.mark.parametrize("preset,worker", [("discrete-cta", 256), ("discrete-cta", 64), ("discrete-warp", 32)])
+def test_discrete_batch_matches_oracle(atos, graphs, preset, worker):
+    """The discrete strategy over a mixed batch: one launch per generation of every instance."""
+    Gs = [atos.Graph.from_csr(g) for g in graphs]
+    specs = mixed_specs(graphs, per_graph_bfs=2)
+    cfg = atos.queue_config(preset, worker_size=worker, fetch_size=min(worker, 32) if worker <= 64 else worker)
+    with atos.Batch(Gs, specs, cfg) as B:
+        B.run()
+        total, per = B.stats()
+        assert total.status == 0
+        check_results(graphs, specs, B.outputs, per)
+    for G in Gs:
+        G.close()
+
+
+def test_batch_autotune(atos, graphs):
+    Gs = [atos.Graph.from_csr(g) for g in graphs]
+    specs = mixed_specs(graphs, per_graph_bfs=2)
+    cfg, ms = atos.batch_autotune(Gs, specs, repeats=1)
+    assert ms > 0 and cfg.worker_size in (32, 64, 128, 256, 512, 1024)
+    with atos.Batch(Gs, specs, cfg) as B:
+        B.run(graph=cfg.strategy == atos.PERSISTENT)
+        total, per = B.stats()
         check_results(graphs, specs, B.outputs, per)
     for G in Gs:
         G.close()
