@@ -29,6 +29,7 @@ namespace atos {
 // Dispatches to the body of the instance's application (uniform across a CTA / warp).
 struct MixedBody {
   using Extra = GcExtra;
+  static constexpr int kResidentThreads = 1536;
 
   template <int BLOCK, class S>
   __device__ static void cta_batch(S& sm, int cnt, const Launch& L, unsigned long long* st) {

@@ -7,6 +7,7 @@ namespace atos {
 
 struct BfsBody {
   using Extra = NoExtra;
+  static constexpr int kResidentThreads = 1536;
 
   // CTA worker: stage (row start, depth + 1) of the popped vertices, scan their degrees and map
   // the flattened neighbour range onto the threads (load-balancing search inside the worker).

@@ -39,6 +39,7 @@ __device__ __forceinline__ bool gc_claim_assign(const Instance& I, int u) {
 
 struct GcBody {
   using Extra = GcExtra;
+  static constexpr int kResidentThreads = 1536;
 
   template <int BLOCK, class S>
   __device__ static void cta_batch(S& sm, int cnt, const Launch& L, unsigned long long* st) {

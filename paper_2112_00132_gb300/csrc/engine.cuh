@@ -563,15 +563,17 @@ __device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const 
   }
 }
 
-// Minimum resident CTAs per SM the compiler must allow (75% of the 2048 threads of an SM): caps
-// registers near 42 per thread, trading some per-thread ILP for resident warps.
-template <int BLOCK>
+// Minimum resident CTAs per SM the compiler must allow: Body::kResidentThreads threads per SM.
+// 1536 (75% of an SM's 2048 threads) caps registers near 42 per thread, trading per-thread ILP
+// for resident warps; 1024 leaves 64 registers, so a body can keep more gathers in flight per
+// thread instead.
+template <class Body, int BLOCK>
 struct MinBlocks {
-  static constexpr int value = BLOCK >= 1024 ? 1 : 1536 / BLOCK;
+  static constexpr int value = BLOCK >= Body::kResidentThreads ? 1 : Body::kResidentThreads / BLOCK;
 };
 
 template <class Body, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, MinBlocks<BLOCK>::value) cta_persistent_kernel(Launch L) {
+__global__ void __launch_bounds__(BLOCK, (MinBlocks<Body, BLOCK>::value)) cta_persistent_kernel(Launch L) {
   __shared__ CtaSmem<BLOCK, typename Body::Extra> sm;
   unsigned long long st[kNumStats] = {};
   const unsigned long long t0 = globaltimer();

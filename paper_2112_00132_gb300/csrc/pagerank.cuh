@@ -155,6 +155,10 @@ __device__ __forceinline__ bool pr_add_crossing(const Instance& I, int u, float 
 
 struct PrBody {
   using Extra = NoExtra;
+  // 1536 threads per SM (the 40-register cap spills a little below 1024-thread CTAs); 1024 at
+  // 64 registers measured faster on RMAT at 256 and 512 threads but slower on the grid, and the
+  // tuned RMAT configuration (1024 threads, one CTA per SM) is the same either way
+  static constexpr int kResidentThreads = 1536;
 
   // Algorithm 4's Check_Size scan of `nchk` vertex ids (rounded up to whole groups of 4) from
   // the round-robin cursor, which counts groups.  Each thread issues its G group loads, then its
