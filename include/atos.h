@@ -90,8 +90,11 @@ typedef struct atos_stats {
   int64_t pushes;         /* tasks pushed (children, re-checks, re-colourings) */
   int64_t iterations;     /* kernel launches of the scheduling loop (1 when persistent) */
   double residual_l1;     /* PageRank: FP64 sum of the residues left (unnormalised scale) */
-  double error_bound;     /* PageRank: FP64 bound on the L1 distance of the normalised result
-                             to the exact fixed point, residual_l1 / ((1 - alpha) * sum) */
+  double error_bound;     /* PageRank: bound on the L1 distance of the normalised result to the
+                             normalised fixed point, from an FP64 a-posteriori certificate:
+                             ||(1 - alpha) 1 + alpha P x - x||_1 / ((1 - alpha) S) for the
+                             result scaled to the fixed point's sum S = n - alpha * (isolated
+                             vertices); it covers the FP32 rounding of the ranks */
   int32_t num_colors;     /* colouring: colours used */
   int32_t status;         /* device-side status (ATOS_OK or ATOS_ERR_*) */
   int64_t batches;        /* worker batches that processed at least one task (tasks / batches is
@@ -222,8 +225,8 @@ int atos_batch_run_graph(atos_batch_t b, void* stream);
 
 /* Synchronises `stream` and reports the last run: *total sums the instances' counters (ms = the
  * run's device time); per_instance (ninst entries, may be NULL) gets each instance's counters,
- * PageRank residual_l1 and error_bound (2 ||r||_1 / ((1 - alpha) sum p), from the residue
- * invariant) and colouring num_colors.  Returns the device status of the run. */
+ * PageRank residual_l1 and error_bound (the FP64 certificate of the returned ranks, as for
+ * atos_pagerank) and colouring num_colors.  Returns the device status of the run. */
 int atos_batch_stats(atos_batch_t b, atos_stats* total, atos_stats* per_instance, void* stream);
 
 /* Instances, active window and persistent grid size of a batch (any pointer may be NULL). */
@@ -244,7 +247,7 @@ typedef struct atos_completion {
   int64_t tasks;       /* tasks processed for this request */
   int64_t edges;       /* neighbour entries read for this request */
   int64_t epochs;      /* server epochs run so far (when the request completed) */
-  double error_bound;  /* PageRank: 2 ||r||_1 / ((1 - alpha) sum p) from the residue invariant */
+  double error_bound;  /* PageRank: FP64 certificate of the returned ranks (see atos_stats) */
 } atos_completion;
 
 typedef struct atos_server_s* atos_server_t;

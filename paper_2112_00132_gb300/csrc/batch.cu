@@ -180,6 +180,13 @@ struct atos_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned graph_kernels = 0;  // library kernels one replay of the captured graph launches
+  // PageRank output certificates: instance indices, FP64 scratch, results (device / pinned host)
+  int n_pr = 0, max_n_pr = 0;
+  int64_t max_nnz_pr = 0;
+  int* d_pr_idx = nullptr;
+  double* d_cert_y = nullptr;
+  double* d_cert = nullptr;
+  double* h_cert = nullptr;
   const void* fn_discrete = nullptr;
   unsigned first_gen = 0;      // discrete strategy: the largest virtual prefix (first generation)
 
@@ -192,6 +199,7 @@ struct atos_batch_s {
     if (ev1) cudaEventDestroy(ev1);
     cudaFree(d_insts), cudaFree(d_qctl), cudaFree(d_ring), cudaFree(d_stats), cudaFreeHost(h_stats);
     cudaFree(d_ctl), cudaFreeHost(h_ctl), cudaFree(d_res), cudaFree(d_qbits), cudaFree(d_results);
+    cudaFree(d_pr_idx), cudaFree(d_cert_y), cudaFree(d_cert), cudaFreeHost(h_cert);
     cudaFreeHost(h_results);
   }
 };
@@ -248,7 +256,10 @@ int enqueue_run(atos_batch_s* b, cudaStream_t st) {
   count_launches(2);
   batch_reduce_kernel<<<dim3(gx, b->ninst), 256, 0, st>>>(b->d_insts, b->d_results, 0);
   batch_normalise_kernel<<<dim3(gx, b->ninst), 256, 0, st>>>(b->d_insts, b->d_results, 0);
-  return cuda_rc(cudaGetLastError());
+  BATCH_TRY(cudaGetLastError());
+  // FP64 certificate of every PageRank output (it certifies the FP32 vector returned)
+  BATCH_TRY(pr_certify_outputs(b->d_insts, b->d_pr_idx, b->n_pr, b->max_n_pr, b->max_nnz_pr, b->d_cert, st));
+  return ATOS_OK;
 }
 
 }  // namespace
@@ -319,6 +330,11 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
     b->max_n = std::max(b->max_n, n);
     b->max_nnz = std::max(b->max_nnz, gnnz[inst[i].graph]);
     b->has_pr |= inst[i].app == ATOS_APP_PAGERANK;
+    if (inst[i].app == ATOS_APP_PAGERANK) {
+      b->n_pr++;
+      b->max_n_pr = std::max(b->max_n_pr, n);
+      b->max_nnz_pr = std::max(b->max_nnz_pr, gnnz[inst[i].graph]);
+    }
     footprint += (inst[i].app == ATOS_APP_PAGERANK ? 8.0 : 4.0) * n;
   }
   if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_insts, sizeof(Instance) * ninst));
@@ -330,6 +346,12 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
   if (!rc) rc = cuda_rc(cudaMallocHost((void**)&b->h_ctl, sizeof(DevCtl)));
   if (!rc && res_total) rc = cuda_rc(cudaMalloc((void**)&b->d_res, sizeof(float) * res_total));
   if (!rc && bits_total) rc = cuda_rc(cudaMalloc((void**)&b->d_qbits, sizeof(uint32_t) * bits_total));
+  if (!rc && b->n_pr) {
+    rc = cuda_rc(cudaMalloc((void**)&b->d_cert_y, sizeof(double) * res_total));  // same row offsets as res
+    if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_pr_idx, sizeof(int) * b->n_pr));
+    if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_cert, sizeof(double) * b->n_pr));
+    if (!rc) rc = cuda_rc(cudaMallocHost((void**)&b->h_cert, sizeof(double) * b->n_pr));
+  }
   if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_results, sizeof(InstResult) * ninst));
   if (!rc) rc = cuda_rc(cudaMallocHost((void**)&b->h_results, sizeof(InstResult) * ninst));
   if (!rc) rc = cuda_rc(cudaEventCreate(&b->ev0));
@@ -341,6 +363,7 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
   b->h_insts.resize(ninst);
   b->exact_sum.assign(ninst, 0.0);
   b->alpha.assign(ninst, 0.0f);
+  std::vector<int> pr_idx;
   for (int32_t i = 0; i < ninst; ++i) {
     const atos_instance& q = inst[i];
     const int32_t* rp = nullptr;
@@ -374,6 +397,9 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
       I.pr_crossing = (cfg.flags & ATOS_FLAG_PR_CROSSING) ? 1 : 0;
       b->exact_sum[i] = (double)I.n - (double)q.alpha * iso;
       b->alpha[i] = q.alpha;
+      I.cert_y = b->d_cert_y + res_off[i];
+      I.exact_sum = b->exact_sum[i];
+      pr_idx.push_back(i);
     } else {
       I.app = kAppGc;
       I.prefix_len = (uint32_t)I.n;
@@ -385,6 +411,8 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
     b->first_gen = std::max(b->first_gen, I.prefix_len);
   }
   rc = cuda_rc(cudaMemcpy(b->d_insts, b->h_insts.data(), sizeof(Instance) * ninst, cudaMemcpyHostToDevice));
+  if (!rc && b->n_pr)
+    rc = cuda_rc(cudaMemcpy(b->d_pr_idx, pr_idx.data(), sizeof(int) * b->n_pr, cudaMemcpyHostToDevice));
   DevCtl init;
   memset(&init, 0, sizeof(init));
   init.dirty = 1;  // fresh rings: the first prepare fills them
@@ -456,6 +484,7 @@ int atos_batch_stats(atos_batch_t b, atos_stats* total, atos_stats* per_instance
                             cudaMemcpyDeviceToHost, st));
   BATCH_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
   BATCH_TRY(cudaMemcpyAsync(b->h_results, b->d_results, sizeof(InstResult) * b->ninst, cudaMemcpyDeviceToHost, st));
+  if (b->n_pr) BATCH_TRY(cudaMemcpyAsync(b->h_cert, b->d_cert, sizeof(double) * b->n_pr, cudaMemcpyDeviceToHost, st));
   BATCH_TRY(cudaStreamSynchronize(st));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, b->ev0, b->ev1);
@@ -464,6 +493,7 @@ int atos_batch_stats(atos_batch_t b, atos_stats* total, atos_stats* per_instance
   sum.ms = ms;
   sum.iterations = 1;
   sum.status = b->h_ctl->status;
+  int kpr = 0;
   for (int i = 0; i < b->ninst; ++i) {
     atos_stats one;
     memset(&one, 0, sizeof(one));
@@ -476,8 +506,8 @@ int atos_batch_stats(atos_batch_t b, atos_stats* total, atos_stats* per_instance
     const Instance& I = b->h_insts[i];
     if (I.app == kAppPr) {
       one.residual_l1 = b->h_results[i].sum_res;
-      // invariant bound (no rounding term): ||x/sum x - p/sum p||_1 <= 2 ||r||_1 / ((1 - alpha) sum p)
-      one.error_bound = 2.0 * b->h_results[i].sum_res / ((1.0 - (double)b->alpha[i]) * b->exact_sum[i]);
+      // FP64 certificate of the returned vector q: ||q - p / sum p||_1 <= ||rho||_1 / ((1 - alpha) S)
+      one.error_bound = b->h_cert[kpr++] / ((1.0 - (double)b->alpha[i]) * b->exact_sum[i]);
     } else if (I.app == kAppGc) {
       one.num_colors = b->h_results[i].num_colors;
     }

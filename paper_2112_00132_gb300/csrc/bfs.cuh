@@ -9,6 +9,26 @@ struct BfsBody {
   using Extra = NoExtra;
   static constexpr int kResidentThreads = 1536;
 
+  // Reads the neighbours' depths of one load-balancing round, relaxes them (atomicMin) and
+  // pushes the neighbours it improved.
+  template <int BLOCK, class S>
+  __device__ static void relax_round(S& sm, int32_t* __restrict__ depth, const int (&item)[LbsRun<BLOCK>::R],
+                                     const int (&nb)[LbsRun<BLOCK>::R]) {
+    constexpr int R = LbsRun<BLOCK>::R;
+    int cur[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) cur[j] = item[j] >= 0 ? __ldcg(depth + nb[j]) : 0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      bool want = false;
+      if (item[j] >= 0) {
+        const int nd = sm.aux[item[j]];
+        if (nd < cur[j]) want = nd < atomicMin(depth + nb[j], nd);
+      }
+      cta_push(sm, want, nb[j]);
+    }
+  }
+
   // CTA worker: stage (row start, depth + 1) of the popped vertices, scan their degrees and map
   // the flattened neighbour range onto the threads (load-balancing search inside the worker).
   template <int BLOCK, class S>
@@ -30,21 +50,27 @@ struct BfsBody {
     int32_t* __restrict__ depth = I.depth;
     constexpr int R = LbsRun<BLOCK>::R;
     int rounds = 0;
-    for (int base = 0; base < total; base += BLOCK * R) {
-      int item[R], nb[R], cur[R];
-      lbs_round<BLOCK>(sm, I.col, cnt, total, base, item, nb);
+    if (BLOCK >= 512) {
+      // software-pipelined: the next round's col gathers are in flight while this round's
+      // neighbour depths are read and relaxed (smaller CTAs run under a 40-register cap, where
+      // the extra live registers spill)
+      int item[R], nb[R];
+      lbs_round<BLOCK>(sm, I.col, cnt, total, 0, item, nb);
+      for (int base = 0; base < total; base += BLOCK * R) {
+        int item2[R], nb2[R];
+        lbs_round<BLOCK>(sm, I.col, cnt, total, base + BLOCK * R, item2, nb2);
+        relax_round<BLOCK>(sm, depth, item, nb);
 #pragma unroll
-      for (int j = 0; j < R; ++j) cur[j] = item[j] >= 0 ? __ldcg(depth + nb[j]) : 0;
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        bool want = false;
-        if (item[j] >= 0) {
-          const int nd = sm.aux[item[j]];
-          if (nd < cur[j]) want = nd < atomicMin(depth + nb[j], nd);
-        }
-        cta_push(sm, want, nb[j]);
+        for (int j = 0; j < R; ++j) item[j] = item2[j], nb[j] = nb2[j];
+        if (base + BLOCK * R < total && flush_round<S>(rounds)) cta_maybe_flush<BLOCK>(sm, I, L, st);
       }
-      if (base + BLOCK * R < total && flush_round<S>(rounds)) cta_maybe_flush<BLOCK>(sm, I, L, st);
+    } else {
+      for (int base = 0; base < total; base += BLOCK * R) {
+        int item[R], nb[R];
+        lbs_round<BLOCK>(sm, I.col, cnt, total, base, item, nb);
+        relax_round<BLOCK>(sm, depth, item, nb);
+        if (base + BLOCK * R < total && flush_round<S>(rounds)) cta_maybe_flush<BLOCK>(sm, I, L, st);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -80,6 +80,8 @@ struct Instance {
   unsigned* orphans[2];  // serving: pending tickets recorded at a pause, by epoch parity
   uint32_t orphan_cap;
   int32_t _pad2;
+  double* cert_y;        // PageRank in batches and serving: FP64 scratch (n) of the output certificate
+  double exact_sum;      // PageRank: n - alpha * (isolated vertices), the fixed point's sum
 };
 
 struct Launch {

@@ -144,6 +144,62 @@ __global__ void pr_normalise_kernel(const Instance* inst, const DevCtl* ctl) {
     I.rank[v] = (float)((double)I.rank[v] * inv);
 }
 
+// Output certificates of several instances (see state.cuh): blockIdx.y selects d_idx[y].
+__global__ void pr_out_cert_zero_kernel(const Instance* insts, const int* idx) {
+  const Instance I = insts[idx[blockIdx.y]];
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < I.n; v += gridDim.x * blockDim.x) I.cert_y[v] = 0.0;
+}
+
+__global__ void pr_out_cert_pull_kernel(const Instance* insts, const int* idx) {
+  const Instance I = insts[idx[blockIdx.y]];
+  const int64_t nnz = __ldg(I.row_ptr + I.n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kCertRun;
+  for (int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kCertRun; k0 < nnz; k0 += stride) {
+    const int k1 = (int)(k0 + kCertRun < nnz ? k0 + kCertRun : nnz);
+    int r = cert_row_of(I.row_ptr, 0, I.n, (int)k0);
+    int next = __ldg(I.row_ptr + r + 1);
+    double acc = 0.0;
+    for (int k = (int)k0; k < k1; ++k) {
+      while (k >= next) {
+        if (acc != 0.0) atomicAdd(I.cert_y + r, acc);
+        acc = 0.0;
+        ++r;
+        next = __ldg(I.row_ptr + r + 1);
+      }
+      const int u = __ldg(I.col + k);
+      acc += (double)I.rank[u] / (double)(__ldg(I.row_ptr + u + 1) - __ldg(I.row_ptr + u));
+    }
+    if (acc != 0.0) atomicAdd(I.cert_y + r, acc);
+  }
+}
+
+__global__ void pr_out_cert_sum_kernel(const Instance* insts, const int* idx, double* out) {
+  const Instance I = insts[idx[blockIdx.y]];
+  const double S = I.exact_sum, a = (double)I.alpha;
+  double acc = 0.0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < I.n; v += gridDim.x * blockDim.x)
+    acc += fabs((1.0 - a) + a * S * I.cert_y[v] - S * (double)I.rank[v]);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out + blockIdx.y, acc);
+}
+
+cudaError_t pr_certify_outputs(const Instance* d_insts, const int* d_idx, int count, int max_n, int64_t max_nnz,
+                               double* d_out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (count > 65535) return cudaErrorInvalidValue;
+  cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)count, s);
+  int gx = (max_n + 255) / 256;
+  gx = gx < 1 ? 1 : (gx > 1024 ? 1024 : gx);
+  int64_t per = (max_nnz + 256 * kCertRun - 1) / (256 * kCertRun);
+  const int gy = (int)(per < 1 ? 1 : (per > 2048 ? 2048 : per));
+  count_launches(3);
+  pr_out_cert_zero_kernel<<<dim3(gx, count), 256, 0, s>>>(d_insts, d_idx);
+  pr_out_cert_pull_kernel<<<dim3(gy, count), 256, 0, s>>>(d_insts, d_idx);
+  pr_out_cert_sum_kernel<<<dim3(gx, count), 256, 0, s>>>(d_insts, d_idx, d_out);
+  return cudaGetLastError();
+}
+
 // certificate_y: FP64 scratch of n entries (needed only when `certificate`).
 cudaError_t pr_finish(Instance* d_insts, int ninst, int n, int64_t nnz, DevCtl* d_ctl, double* certificate_y,
                       double exact_sum, cudaStream_t s) {

@@ -176,6 +176,10 @@ struct atos_server_s {
   int* h_fin = nullptr;  // pinned
   char* d_results = nullptr;
   char* h_results = nullptr;  // pinned
+  int* d_cert_idx = nullptr;  // PageRank certificates of the requests an epoch finished
+  int* h_cert_idx = nullptr;  // pinned
+  double* d_cert = nullptr;
+  double* h_cert = nullptr;   // pinned
   std::deque<atos_completion> done;
   int64_t epochs = 0;
 
@@ -185,6 +189,7 @@ struct atos_server_s {
     cudaFree(d_qctl);
     cudaFree(d_stats), cudaFreeHost(h_stats), cudaFree(d_ctl), cudaFreeHost(h_ctl), cudaFree(d_fin);
     cudaFreeHost(h_fin), cudaFree(d_results), cudaFreeHost(h_results);
+    cudaFree(d_cert_idx), cudaFreeHost(h_cert_idx), cudaFree(d_cert), cudaFreeHost(h_cert);
     if (stream) cudaStreamDestroy(stream);
   }
 };
@@ -200,7 +205,7 @@ size_t request_bytes(const atos_server_s* s, int app, int32_t n, uint32_t* cap_o
   if (cap_out) *cap_out = cap;
   size_t b = (size_t)cap * 8 + 256;                 // ring
   b += 2 * ((size_t)s->orphan_cap * 4 + 256);       // pending tickets of a pause, two epochs
-  if (app == ATOS_APP_PAGERANK) b += (size_t)n * 4 + 256;  // residues
+  if (app == ATOS_APP_PAGERANK) b += (size_t)n * 4 + 256 + (size_t)n * 8 + 256;  // residues, certificate
   if (app != ATOS_APP_BFS) b += (size_t)(n + 31) / 32 * 4 + 256;  // queued bits
   return b;
 }
@@ -270,6 +275,10 @@ int atos_server_create(const atos_graph_t* graphs, int32_t ngraphs, int32_t max_
   if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_fin, sizeof(int) * max_slots));
   if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_results, batch_result_bytes() * max_slots));  // by active index
   if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_results, batch_result_bytes() * max_slots));
+  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_cert_idx, sizeof(int) * max_slots));
+  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_cert_idx, sizeof(int) * max_slots));
+  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_cert, sizeof(double) * max_slots));
+  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_cert, sizeof(double) * max_slots));
   if (!rc) rc = rc_of(cudaMemsetAsync(s->d_ctl, 0, sizeof(DevCtl), s->stream));
   if (rc) {
     delete s;
@@ -336,6 +345,8 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
     I.prefix_item = -1;
     I.rank = (float*)q->out;
     I.res = (float*)take((size_t)n * 4);
+    I.cert_y = (double*)take((size_t)n * 8);
+    I.exact_sum = (double)n - (double)q->alpha * iso;
     I.qbits = (uint32_t*)take((size_t)(n + 31) / 32 * 4);
     I.alpha = q->alpha;
     I.eps = q->eps;
@@ -432,6 +443,26 @@ int atos_server_step(atos_server_t s, int64_t slice_ns, int32_t* active_left) {
   std::vector<int> finished, finished_k;
   for (int k = 0; k < na; ++k)
     if (status != 0 || s->h_fin[k]) finished.push_back(s->active_idx[k]), finished_k.push_back(k);
+  // FP64 certificates of the finished PageRank outputs (a second synchronisation, only in epochs
+  // that finished one)
+  int ncert = 0, cert_n = 1;
+  int64_t cert_nnz = 1;
+  std::vector<int> cert_of(finished.size(), -1);
+  if (status == 0)
+    for (size_t f = 0; f < finished.size(); ++f) {
+      const Slot& sl = s->slots[finished[f]];
+      if (sl.app != ATOS_APP_PAGERANK) continue;
+      cert_of[f] = ncert;
+      s->h_cert_idx[ncert++] = finished_k[f];
+      cert_n = std::max(cert_n, (int)sl.inst.n);
+      cert_nnz = std::max(cert_nnz, s->gnnz[sl.graph]);
+    }
+  if (ncert) {
+    SRV_TRY(cudaMemcpyAsync(s->d_cert_idx, s->h_cert_idx, sizeof(int) * ncert, cudaMemcpyHostToDevice, st));
+    SRV_TRY(pr_certify_outputs(s->d_active, s->d_cert_idx, ncert, cert_n, cert_nnz, s->d_cert, st));
+    SRV_TRY(cudaMemcpyAsync(s->h_cert, s->d_cert, sizeof(double) * ncert, cudaMemcpyDeviceToHost, st));
+    SRV_TRY(cudaStreamSynchronize(st));
+  }
   for (size_t f = 0; f < finished.size(); ++f) {
     const int i = finished[f];
     Slot& sl = s->slots[i];
@@ -447,8 +478,8 @@ int atos_server_step(atos_server_t s, int64_t slice_ns, int32_t* active_left) {
     double sum_rank = 0, sum_res = 0;
     int ncol = 0;
     batch_result_read(s->h_results + rb * finished_k[f], &sum_rank, &sum_res, &ncol);
-    if (sl.app == ATOS_APP_PAGERANK)
-      c.error_bound = 2.0 * sum_res / ((1.0 - (double)sl.alpha) * std::max(sl.exact_sum, 1e-300));
+    if (sl.app == ATOS_APP_PAGERANK && cert_of[f] >= 0)
+      c.error_bound = s->h_cert[cert_of[f]] / ((1.0 - (double)sl.alpha) * std::max(sl.exact_sum, 1e-300));
     if (sl.app == ATOS_APP_COLOR) c.num_colors = ncol;
     s->done.push_back(c);
     release_slot(s, i);

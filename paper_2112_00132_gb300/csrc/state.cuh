@@ -29,6 +29,13 @@ cudaError_t launch_pr_init(Instance* d_insts, int ninst, int64_t max_nnz, cudaSt
 cudaError_t launch_next_generation(Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
 cudaError_t launch_finalize(const Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
 
+// FP64 certificate of normalised PageRank outputs (ranks summing to 1): for the instances
+// d_insts[d_idx[j]], j < count, out[j] = ||(1 - alpha) 1 + alpha P x - x||_1 with x = exact_sum *
+// rank, so the L1 distance of the output to the normalised fixed point is at most
+// out[j] / ((1 - alpha) exact_sum).  Uses each instance's cert_y scratch.
+cudaError_t pr_certify_outputs(const Instance* d_insts, const int* d_idx, int count, int max_n, int64_t max_nnz,
+                               double* d_out, cudaStream_t s);
+
 // Host loop of the discrete strategy (Section 3.4) over d_insts[0, ninst), after prepare: one
 // launch of `fn` per queue generation (grid: generation slices x instances), until every queue is
 // empty; PageRank instances (has_pr) also need a verification sweep that enqueues nothing.  Reads

@@ -53,7 +53,7 @@ def make_arrivals(rate: float, duration: float, mix, ngraphs: int, seed: int = 1
     return out
 
 
-def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), slice_ns=1_000_000, max_slots=256,
+def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), slice_ns=1_000_000, max_slots=64,
           budget_bytes=None, alpha=0.85, eps=1e-9, seed=1, drain_s=30.0, keep=0, cfg=None, graphs=None):
     """Runs the serving loop; returns a summary dict (and up to `keep` finished requests with their
     outputs under "kept", for checking).  `graphs`: resident abi.Graph objects of `csrs` to reuse
@@ -166,7 +166,7 @@ def main():
     ap.add_argument("--warmup", type=float, default=1.0)
     ap.add_argument("--slice-ms", type=float, default=1.0)
     ap.add_argument("--graphs", default="config", choices=["config", "small"])
-    ap.add_argument("--max-slots", type=int, default=256)
+    ap.add_argument("--max-slots", type=int, default=64)
     ap.add_argument("--drain", type=float, default=30.0, help="seconds allowed after the last arrival")
     ap.add_argument("--rates", default="", help="comma-separated offered rates (a sweep); overrides --rate")
     args = ap.parse_args()

@@ -44,7 +44,7 @@ def check_results(graphs, specs, outputs, per):
             x, _, _ = oracle.pagerank(g, ALPHA)
             l1 = np.abs(res.astype(np.float64) - x / x.sum()).sum()
             assert l1 <= PR_L1_TOL, f"pagerank graph {gi}: L1 {l1}"
-            assert l1 <= st.error_bound * 1.0001 + 1e-6
+            assert l1 <= st.error_bound * 1.0001 + 1e-9  # the FP64 certificate covers the FP32 output
         else:
             code, bad, k = oracle.check_coloring(g, res)
             assert code == 0 and k == st.num_colors, f"colouring graph {gi}: code {code} vertex {bad}"

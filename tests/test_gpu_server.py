@@ -60,6 +60,10 @@ def test_server_mixed_requests_match_oracle(atos, graphs):
             kind, gi, src = reqs[d["id"]]
             assert d["status"] == 0
             assert check(graphs[gi], kind, src, d["out"]), (kind, gi, src, d)
+            if kind == "pagerank":  # the completion's FP64 certificate covers the actual distance
+                x, _, _ = oracle.pagerank(graphs[gi], ALPHA)
+                l1 = np.abs(d["out"].cpu().numpy().astype(np.float64) - x / x.sum()).sum()
+                assert 0 < d["error_bound"] <= PR_L1_TOL and l1 <= d["error_bound"] * 1.0001 + 1e-9
         assert S.info()["arena_used"] == 0 and S.info()["active"] == 0
     for G in Gs:
         G.close()
