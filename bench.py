@@ -275,6 +275,23 @@ def run_atos(args, rank: int, world: int):
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src, "traffic": None,
                 "algorithmic_bytes": dom_bytes, "launch_ms": round(dom_ms, 3)}
+    # the edge-loop ceilings on this graph (library probe, no scheduler): the rate the bodies'
+    # inner loops could reach; the kernels are bound by L2 atomics and gather latency, not HBM
+    scatter_ms = G.edge_ceiling("scatter", repeats=3, stream=stream)
+    gather_ms = G.edge_ceiling("gather", repeats=3, stream=stream)
+    scatter_g, gather_g = g.nnz / scatter_ms / 1e6, g.nnz / gather_ms / 1e6
+    bfs_reads = float(bfs_stats.edges)
+    edge_ceiling = {
+        "unit": "G edge operations/s", "scatter_ceiling": round(scatter_g, 1), "gather_ceiling": round(gather_g, 1),
+        "pagerank_achieved": round(pr_edges / (mean(pr_ms) * 1e-3) / 1e9, 1),
+        "pagerank_frac": round(pr_edges / (mean(pr_ms) * 1e-3) / 1e9 / scatter_g, 3),
+        "bfs_achieved": round(bfs_reads / (mean(bfs_ms) * 1e-3) / 1e9, 1),
+        "bfs_frac": round(bfs_reads / (mean(bfs_ms) * 1e-3) / 1e9 / gather_g, 3),
+        "color_achieved": round(gc_edges / (mean(gc_ms) * 1e-3) / 1e9, 1),
+        "color_frac": round(gc_edges / (mean(gc_ms) * 1e-3) / 1e9 / gather_g, 3),
+        "probe": "atos_edge_ceiling: one pass over every CSR entry in order, col[e] then red.add.f32 "
+                 "(scatter) or a load (gather) of state[col[e]]; BFS/colouring counted as neighbour entries read",
+    }
 
     def brief(c):
         names = {0: "persistent", 1: "discrete", 2: "bsp"}
@@ -319,6 +336,7 @@ def run_atos(args, rank: int, world: int):
                                             "autotune_best_ms": tune_ms, "parallelism": f"replicas x{world}"}),
         "comparisons": comparisons,
         "roofline": roofline,
+        "edge_ceiling": edge_ceiling,
         "gpu_launches": launches,
         "breakdown": {
             "bfs_ms": round(mean(bfs_ms), 3), "pagerank_ms": round(mean(pr_ms), 3), "color_ms": round(mean(gc_ms), 3),

@@ -177,6 +177,18 @@ int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint3
  * zero.  Either pointer may be NULL. */
 int atos_debug_scratch_check(atos_graph_t g, uint64_t* set_bits, uint64_t* busy_slots);
 
+/* Ceilings of the task bodies' edge loops on g, with no scheduler: one pass over every CSR
+ * entry in order, a coalesced read of col[e] and then
+ *   ATOS_CEILING_SCATTER: red.add.f32 into state[col[e]] (PageRank's residue scatter), or
+ *   ATOS_CEILING_GATHER:  a load of state[col[e]] (BFS's and colouring's neighbour reads),
+ * into an n-float scratch the call allocates.  *ms_per_pass: mean device time of one pass over
+ * `repeats` passes after a warm-up pass (stream-ordered on `stream`, which it synchronises).
+ * nnz / ms_per_pass is the edge rate those loops can reach on this graph: the roofline of
+ * the PageRank kernel (limited on scale-free graphs by same-address atomics at the hubs). */
+#define ATOS_CEILING_SCATTER 0
+#define ATOS_CEILING_GATHER 1
+int atos_edge_ceiling(atos_graph_t g, int32_t kind, int32_t repeats, double* ms_per_pass, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process (monotone counter, all
  * threads, all devices); lets a caller count the launches of a region of its own program. */
 uint64_t atos_kernel_launches(void);

@@ -156,6 +156,8 @@ def lib() -> ctypes.CDLL:
         for name in ("atos_server_create", "atos_server_submit", "atos_server_step", "atos_server_poll",
                      "atos_server_info", "atos_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
+        L.atos_edge_ceiling.argtypes = [vp, i32, i32, P(ctypes.c_double), vp]
+        L.atos_edge_ceiling.restype = ctypes.c_int
         L.atos_autotune.argtypes = [vp, i32, vp, i32, vp, i32, P(Config), P(ctypes.c_double), vp]
         L.atos_autotune.restype = ctypes.c_int
         L.atos_batch_autotune.argtypes = [vp, i32, P(Instance), i32, i32, P(Config), P(ctypes.c_double), vp]
@@ -318,6 +320,15 @@ class Graph:
         _check(lib().atos_autotune(self._h, code, src.ctypes.data, src.shape[0], scratch.data_ptr(), repeats,
                                    ctypes.byref(best), ctypes.byref(ms), _stream_handle(stream)), "atos_autotune")
         return best, ms.value
+
+    def edge_ceiling(self, kind: str = "scatter", repeats: int = 3, stream=None) -> float:
+        """Device ms of one ideal pass over every CSR entry ("scatter": red.add into state[col[e]],
+        "gather": a load of state[col[e]]), with no scheduler: the edge-loop roofline."""
+        ms = ctypes.c_double(0)
+        code = {"scatter": 0, "gather": 1}[kind]
+        _check(lib().atos_edge_ceiling(self._h, code, repeats, ctypes.byref(ms), _stream_handle(stream)),
+               "atos_edge_ceiling")
+        return ms.value
 
     def tuned_config(self, app: str):
         """The cached tuned Config for this graph's class, or None if the class was not tuned."""

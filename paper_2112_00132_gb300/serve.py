@@ -3,10 +3,15 @@
 Requests arrive as a Poisson process (seeded; exponential inter-arrival times), each a BFS (from a
 random source of nonzero degree), a PageRank or a colouring on a graph drawn uniformly from the
 resident set, in the proportions of ``mix``.  The loop admits every arrived request it can (the
-server refuses while no slot or arena memory is free; refused requests wait in FIFO order), runs
-one server epoch (a persistent launch bounded by ``slice_ns`` over every admitted request), and
-records each completion's latency = completion time - arrival time.  Requests that arrive during
-the warm-up are served but not counted.
+server refuses while no slot or arena memory is free), runs one server epoch (a persistent launch
+bounded by ``slice_ns`` over every admitted request), and records each completion's latency =
+completion time - arrival time.  Requests that arrive during the warm-up are served but not
+counted.
+
+Admission keeps two FIFO queues: requests on graphs of more than ``large_n`` vertices, of which at
+most ``max_large`` are admitted at a time, and the rest.  Without the split, slots fill up with
+the long requests under overload (each finishes late, so the slots they hold turn over slowly)
+and the completion rate falls below what the GPU sustains.
 
 Usage: python -m paper_2112_00132_gb300.serve [--rate 2000] [--duration 10] [--warmup 1]
        [--graphs small|config]   (``config``: 64 graphs of the batched mix plus RMAT 23)
@@ -54,7 +59,8 @@ def make_arrivals(rate: float, duration: float, mix, ngraphs: int, seed: int = 1
 
 
 def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), slice_ns=1_000_000, max_slots=64,
-          budget_bytes=None, alpha=0.85, eps=1e-9, seed=1, drain_s=30.0, keep=0, cfg=None, graphs=None):
+          budget_bytes=None, alpha=0.85, eps=1e-9, seed=1, drain_s=30.0, keep=0, cfg=None, graphs=None,
+          large_n=1 << 21, max_large=1):
     """Runs the serving loop; returns a summary dict (and up to `keep` finished requests with their
     outputs under "kept", for checking).  `graphs`: resident abi.Graph objects of `csrs` to reuse
     (created here, and closed at the end, when None)."""
@@ -69,7 +75,9 @@ def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), sli
         budget_bytes = int(min(free * 0.5, 64 << 30))
     server = abi.Server(graphs, max_slots=max_slots, budget_bytes=budget_bytes, cfg=cfg)
     arrivals = make_arrivals(rate, duration, mix, len(graphs), seed)
-    backlog = []
+    backlog, backlog_large = [], []
+    large_active = 0
+    is_large = [g.n > large_n for g in csrs]
     meta = {}
     lat = []
     kept = []
@@ -82,22 +90,26 @@ def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), sli
     while True:
         now = time.perf_counter() - t0
         while nxt < len(arrivals) and arrivals[nxt][0] <= now:
-            backlog.append((nxt,) + arrivals[nxt])
+            (backlog_large if is_large[arrivals[nxt][2]] else backlog).append((nxt,) + arrivals[nxt])
             nxt += 1
-        # admit in arrival order while the server accepts
-        while backlog:
-            idx, t_arr, kind, gi = backlog[0]
-            src = int(sources[gi][idx % len(sources[gi])])
-            got = server.submit(kind, gi, source=src, alpha=alpha, eps=eps)
-            if got is None:
-                break
-            meta[got[0]] = (t_arr, kind, gi, src)
-            backlog.pop(0)
+        # admit in arrival order while the server accepts: the large-graph queue first, up to
+        # max_large of them in flight, then the others
+        for queue, large in ((backlog_large, True), (backlog, False)):
+            while queue and (not large or large_active < max_large):
+                idx, t_arr, kind, gi = queue[0]
+                src = int(sources[gi][idx % len(sources[gi])])
+                got = server.submit(kind, gi, source=src, alpha=alpha, eps=eps)
+                if got is None:
+                    break
+                meta[got[0]] = (t_arr, kind, gi, src)
+                large_active += large
+                queue.pop(0)
         left = server.step(slice_ns)
         steps += 1
         t_done = time.perf_counter() - t0
         for c in server.poll():
             t_arr, kind, gi, src = meta.pop(c["id"])
+            large_active -= is_large[gi]
             completed += 1
             if c["status"] != 0:
                 continue
@@ -108,11 +120,11 @@ def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), sli
             if len(kept) < keep:
                 kept.append({"kind": kind, "graph": gi, "source": src, "out": c["out"], "error_bound": c["error_bound"]})
         now = time.perf_counter() - t0
-        if nxt >= len(arrivals) and not backlog and left == 0:
+        if nxt >= len(arrivals) and not backlog and not backlog_large and left == 0:
             break
         if now > duration + drain_s:
             break
-        if left == 0 and not backlog and nxt < len(arrivals):
+        if left == 0 and not backlog and not backlog_large and nxt < len(arrivals):
             time.sleep(max(0.0, min(arrivals[nxt][0] - now, 0.001)))
     wall = time.perf_counter() - t0
     window = max(1e-9, min(wall, duration) - warmup)
@@ -129,7 +141,7 @@ def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), sli
     res = {
         "offered_rps": round(offered, 1), "achieved_rps": round(achieved, 1),
         "sustainable": bool(len(lat) >= 0.95 * len(measured) and wall <= duration + 1.0),
-        "requests": len(arrivals), "completed": completed, "unfinished": len(meta) + len(backlog),
+        "requests": len(arrivals), "completed": completed, "unfinished": len(meta) + len(backlog) + len(backlog_large),
         "p50_ms": pct(lat_ms, 50), "p99_ms": pct(lat_ms, 99), "mean_ms": float(lat_ms.mean()) if len(lat) else None,
         "p50_ms_by_kind": {k: pct(np.array(v) * 1e3, 50) for k, v in per_kind.items()},
         "p99_ms_by_kind": {k: pct(np.array(v) * 1e3, 99) for k, v in per_kind.items()},
@@ -137,6 +149,7 @@ def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), sli
         "gteps_unit": "neighbour entries read by task bodies per second (directed, includes overwork)",
         "epochs": info["epochs"], "steps": steps, "slice_ms": slice_ns / 1e6, "wall_s": round(wall, 2),
         "graphs": len(csrs), "max_slots": max_slots, "arena_bytes": budget_bytes,
+        "admission": f"two FIFO queues; at most {max_large} requests on graphs of > {large_n} vertices in flight",
     }
     if keep:
         res["kept"] = kept
@@ -169,6 +182,7 @@ def main():
     ap.add_argument("--max-slots", type=int, default=64)
     ap.add_argument("--drain", type=float, default=30.0, help="seconds allowed after the last arrival")
     ap.add_argument("--rates", default="", help="comma-separated offered rates (a sweep); overrides --rate")
+    ap.add_argument("--max-large", type=int, default=1, help="requests on large graphs in flight at most")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -178,7 +192,7 @@ def main():
     rates = [float(r) for r in args.rates.split(",") if r] or [args.rate]
     for rate in rates:
         res = serve(csrs, rate=rate, duration=args.duration, warmup=args.warmup, slice_ns=int(args.slice_ms * 1e6),
-                    max_slots=args.max_slots, drain_s=args.drain, graphs=graphs)
+                    max_slots=args.max_slots, drain_s=args.drain, graphs=graphs, max_large=args.max_large)
         res["workload"] = ("64 graphs of the batched mix + RMAT 23" if args.graphs == "config" else "4 small graphs")
         res["mix"] = "BFS 60% / PageRank 30% / colouring 10%"
         print(json.dumps(res), flush=True)

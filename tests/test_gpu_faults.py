@@ -2,6 +2,8 @@
 anything: a task that is counted but never pushed (the workers' waits run out and report
 ATOS_ERR_TIMEOUT), and a ring too small for a single worker (ATOS_ERR_QUEUE_OVERFLOW).  After each
 failure the same graph object must run correctly again."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -59,3 +61,15 @@ def test_malformed_csr_rejected_on_host(atos):
     with pytest.raises(atos.AtosError) as e:
         atos.Graph(np.array([0, 1, 1]), np.array([1]), check_symmetric=True)
     assert e.value.status == atos.abi.ERR_BAD_CSR
+
+
+def test_edge_ceiling_probe(atos):
+    g = gg.rmat(12, 16, seed=1)
+    with atos.Graph.from_csr(g) as G:
+        for kind in ("scatter", "gather"):
+            ms = G.edge_ceiling(kind, repeats=2)
+            assert ms > 0
+        rc = atos.abi.lib().atos_edge_ceiling(G._h, 7, 1, ctypes.byref(ctypes.c_double()), None)
+        assert rc == atos.abi.ERR_INVALID_ARG
+    with atos.Graph.from_csr(gg.from_edges(3, [], "isolated3")) as G:
+        assert G.edge_ceiling("scatter") == 0.0
