@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--worker", type=int, default=256, help="with --no-tune: worker size for every app")
     ap.add_argument("--fetch", type=int, default=256, help="with --no-tune: fetch size for every app")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use --worker / --fetch")
+    ap.add_argument("--check-size", type=int, default=32, help="with --no-tune: PageRank's Check_Size")
     ap.add_argument("--no-compare", action="store_true", help="skip the BSP / unbatched comparisons")
     ap.add_argument("--workload", default="rmat22", choices=["rmat22", "batched"],
                     help="rmat22: the single-graph step (default); batched: 256 graphs x (4 BFS + 1 PageRank) "
@@ -155,6 +156,26 @@ def replica_throughput(work_per_replica: float, total_ms: float, steps: int, wor
     return ms_step, world * work_per_replica / (ms_step * 1e-3) / 1e9
 
 
+def recorded_traffic(cfg_pr):
+    """DRAM bytes per launch of the PageRank kernel from the committed ncu record, or None when
+    the kernel's sources changed since it was taken or the configuration differs."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "pagerank_traffic_rmat22.txt")
+    try:
+        rec = dict(line.split(": ", 1) for line in open(path).read().splitlines()
+                   if ": " in line and not line.startswith((" ", "#")))
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for f in ("engine.cuh", "pagerank.cuh", "pagerank.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2112_00132_gb300", "csrc", f), "rb").read())
+    if rec.get("kernel_sources_sha256", "").strip() != h.hexdigest():
+        return None
+    if int(rec.get("worker", 0)) != cfg_pr.worker_size or int(rec.get("check_size", 0)) != cfg_pr.check_size:
+        return None
+    return float(rec["traffic_bytes_per_launch"])
+
+
 # ------------------------------------------------------------------------------- atos arm
 
 def component_edges(depths, deg_t):
@@ -186,7 +207,8 @@ def run_atos(args, rank: int, world: int):
 
     # configuration per application: the autotuner's choice (untimed sweep), unless fixed
     if args.no_tune:
-        cfg_bfs = cfg_pr = cfg_gc = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch)
+        cfg_bfs = cfg_gc = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch)
+        cfg_pr = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch, check_size=args.check_size)
         tune_ms = {}
     else:
         cfg_bfs, t_b = G.autotune("bfs", srcs, repeats=1, stream=stream)
@@ -272,8 +294,11 @@ def run_atos(args, rank: int, world: int):
     dom = max(parts, key=lambda k: parts[k][0])
     dom_ms, dom_bytes = parts[dom]
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(cfg_pr) if (dom == "pagerank_persistent" and args.scale == 22
+                                           and cfg_pr.flags == 0 and cfg_pr.strategy == 0) else None
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src, "traffic": None,
+                "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src, "traffic": traffic,
+                "traffic_source": "profiles/pagerank_traffic_rmat22.txt (ncu, one launch)" if traffic else None,
                 "algorithmic_bytes": dom_bytes, "launch_ms": round(dom_ms, 3)}
     # the edge-loop ceilings on this graph (library probe, no scheduler): the rate the bodies'
     # inner loops could reach; the kernels are bound by L2 atomics and gather latency, not HBM
