@@ -339,6 +339,16 @@ def run_atos(args, rank: int, world: int):
         bsp = atos.queue_config("bsp")
         comparisons["bfs64_bsp_ms"] = round(timed(lambda: G.bfs(srcs, depths, cfg=bsp, stream=stream,
                                                                   stats=False)), 3)
+        # work of the level-synchronous forms (neighbour entries read), for the workload ratio
+        # of Table 4: persistent work / BSP work
+        _, bsp_bfs = G.bfs(srcs, depths, cfg=bsp, stream=stream)
+        _, bsp_pr = G.pagerank(ALPHA, EPS, rank_t, cfg=bsp, stream=stream)
+        _, _, bsp_gc = G.color(colors, cfg=bsp, stream=stream)
+        comparisons["workload_ratio"] = {
+            "bfs": round(bfs_stats.edges / max(1, bsp_bfs.edges), 3),
+            "pagerank": round(pr_edges / max(1, bsp_pr.edges), 3),
+            "color": round(gc_edges / max(1, bsp_gc.edges), 3),
+            "note": "neighbour entries read by the persistent path / by the BSP path (Table 4's ratio)"}
         one = torch.empty((1, g.n), dtype=torch.int32, device="cuda")
 
         def unbatched():
@@ -648,8 +658,9 @@ def cpu_baseline_batched(graphs, specs, stride=BATCH_SAMPLE_STRIDE):
 
 # --------------------------------------------------------------------------- CPU oracle arm
 
-def oracle_sample(g, srcs, nbfs=1, sweeps=3, color=True):
-    """Serial oracle on a bounded sample of the step; returns (work in the metric's units, seconds)."""
+def oracle_sample(g, srcs, nbfs=1, sweeps=3, color=True, info=None):
+    """Serial oracle on a bounded sample of the step; returns (work in the metric's units, seconds).
+    `info` (a dict) receives the serial greedy colour count when the sample colours."""
     import oracle
     oracle.build()
     deg = np.diff(g.row_ptr)
@@ -662,17 +673,20 @@ def oracle_sample(g, srcs, nbfs=1, sweeps=3, color=True):
         oracle.pagerank_sweeps(g, ALPHA, sweeps)
         work += sweeps * g.nnz
     if color:
-        oracle.greedy_color(g)
+        _, k = oracle.greedy_color(g)
         work += g.nnz
+        if info is not None:
+            info["serial_greedy_colors"] = k
     return work, time.perf_counter() - t0
 
 
 def cpu_baseline(g, srcs):
-    work, dt = oracle_sample(g, srcs, nbfs=2, sweeps=3, color=True)
+    info = {}
+    work, dt = oracle_sample(g, srcs, nbfs=2, sweeps=3, color=True, info=info)
     return {"value": round(work / dt / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "serial C oracle, one thread: BFS from 2 of the 64 sources, 3 FP64 power-iteration "
                       "sweeps (nnz edge operations each), one greedy colouring (nnz entries)",
-            "seconds": round(dt, 2), "host_cores": os.cpu_count()}
+            "seconds": round(dt, 2), "host_cores": os.cpu_count(), **info}
 
 
 def run_reference(args, rank, world):
@@ -743,6 +757,7 @@ def main():
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             g, srcs = workload(args.scale)
             res["cpu_baseline"] = cpu_baseline(g, srcs)
+            res["breakdown"]["colors_serial_greedy"] = res["cpu_baseline"].get("serial_greedy_colors")
     if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)
     if world > 1:
