@@ -70,12 +70,13 @@ std::vector<atos_config> candidates(int app, int nsrc) {
     }
   }
   if (app == ATOS_APP_BFS && nsrc > 1) {
-    for (int win : {1, 2, 8, 32}) {
-      if (win >= nsrc) break;
-      atos_config c = make(nullptr, 256, 256, ATOS_FETCH_SPREAD);
-      c.window = win;
-      out.push_back(c);
-    }
+    for (int w : {256, 512})
+      for (int win : {1, 2, 4, 8, 16, 32}) {
+        if (win >= nsrc) break;
+        atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
+        c.window = win;
+        out.push_back(c);
+      }
   }
   return out;
 }
