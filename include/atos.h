@@ -67,6 +67,16 @@ extern "C" {
                                      point and the same final verification sweep; check_size is
                                      ignored.  Persistent and discrete strategies; BSP ignores it. */
 
+#define ATOS_FLAG_SPREAD_IDS 4u   /* PageRank and colouring (persistent and discrete strategies) run on
+                                     an internal copy of the graph whose vertex ids are spread by the
+                                     bijection v -> (a v + c) mod n (a ~ 0.618 n, coprime to n), built
+                                     on the device at the first such call (4 (n + 1) + 4 nnz bytes).
+                                     On scale-free graphs sorted rows all begin with the few low-id
+                                     hubs, so a warp's 32 state updates land in a few L2 slices;
+                                     spread ids balance them over the slices.  Results come back in
+                                     the caller's ids (one gather).  BFS, BSP, batches and serving
+                                     ignore the flag. */
+
 typedef struct atos_config {
   int32_t worker_size;    /* 32 (warp worker) or a CTA worker of 64, 128, 256, 512 or 1024 threads */
   int32_t fetch_size;     /* tasks per pop, 1..1024; at most worker_size for CTA workers (FETCH_SIZE

@@ -23,6 +23,11 @@ cudaError_t pr_verify_sweep(Instance* d_insts, int ninst, int max_n, DevCtl* d_c
 cudaError_t pr_finish(Instance* d_insts, int ninst, int n, int64_t nnz, DevCtl* d_ctl, double* certificate_y,
                       double exact_sum, cudaStream_t s);
 cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s);
+uint64_t spread_multiplier(int32_t n);
+cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, uint64_t a, uint64_t c, int32_t* new_rp,
+                         int32_t* new_col, int32_t* bsums, cudaStream_t s);
+cudaError_t unspread_f32(const float* src, float* dst, int32_t n, uint64_t a, uint64_t c, cudaStream_t s);
+cudaError_t unspread_i32(const int32_t* src, int32_t* dst, int32_t n, uint64_t a, uint64_t c, cudaStream_t s);
 unsigned long long launches_so_far();
 int bsp_pagerank(const int32_t* row_ptr, const int32_t* col, int32_t n, float alpha, float eps, float* rank,
                  float* res, void* scratch, size_t scratch_bytes, int32_t* hcount, cudaStream_t s,
@@ -108,9 +113,38 @@ struct atos_graph_s {
   double* d_cert = nullptr;  // PageRank FP64 certificate scratch (n entries)
   void* d_bsp = nullptr;  // BSP comparator frontiers and scan space
   size_t bsp_bytes = 0;
+  // the spread-id copy (ATOS_FLAG_SPREAD_IDS): CSR with vertex v renamed (sp_a v + sp_c) mod n,
+  // and an n-entry output buffer in the copy's ids
+  int32_t* sp_row_ptr = nullptr;
+  int32_t* sp_col = nullptr;
+  void* sp_out = nullptr;
+  uint64_t sp_a = 1, sp_c = 0;
 };
 
 namespace {
+
+// Builds the spread-id copy of g on `st` the first time it is needed.
+int ensure_spread(atos_graph_s* g, cudaStream_t st) {
+  if (g->sp_row_ptr) return ATOS_OK;
+  const int32_t n = g->n;
+  int32_t* bsums = nullptr;
+  int32_t *rp = nullptr, *col = nullptr;
+  void* out = nullptr;
+  int rc = from_cuda(dev_alloc(&rp, (size_t)n + 1));
+  if (!rc) rc = from_cuda(dev_alloc(&col, (size_t)std::max<int64_t>(g->nnz, 1)));
+  if (!rc) rc = from_cuda(dev_alloc(&bsums, (size_t)n / 1024 + 2));
+  if (!rc) rc = from_cuda(cudaMalloc(&out, sizeof(int32_t) * (size_t)n));
+  const uint64_t sa = spread_multiplier(n), sc = (uint64_t)(n / 2);
+  if (!rc) rc = from_cuda(spread_build(g->row_ptr, g->col, n, sa, sc, rp, col, bsums, st));
+  if (!rc) rc = from_cuda(cudaStreamSynchronize(st));  // bsums is freed next
+  cudaFree(bsums);
+  if (rc) {
+    cudaFree(rp), cudaFree(col), cudaFree(out);
+    return rc;
+  }
+  g->sp_row_ptr = rp, g->sp_col = col, g->sp_out = out, g->sp_a = sa, g->sp_c = sc;
+  return ATOS_OK;
+}
 
 int ensure_scratch(atos_graph_s* g, int ninst, uint32_t cap) {
   Scratch& s = g->s;
@@ -190,7 +224,7 @@ int check_config(const atos_config& c) {
   if (c.fetch_policy < ATOS_FETCH_FIXED || c.fetch_policy > ATOS_FETCH_SPREAD) return ATOS_ERR_INVALID_ARG;
   if (c.num_blocks < 0 || c.check_size < 0 || c.window < 0 || c.queue_capacity < 0 || c.spin_limit_ns < 0)
     return ATOS_ERR_INVALID_ARG;
-  if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING)) return ATOS_ERR_INVALID_ARG;
+  if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS)) return ATOS_ERR_INVALID_ARG;
   return ATOS_OK;
 }
 
@@ -450,6 +484,7 @@ int atos_graph_destroy(atos_graph_t g) {
   cudaDeviceSynchronize();
   if (g->owned) cudaFree(g->row_ptr), cudaFree(g->col);
   cudaFree(g->d_res), cudaFree(g->d_qbits), cudaFree(g->d_bsp), cudaFree(g->d_cert);
+  cudaFree(g->sp_row_ptr), cudaFree(g->sp_col), cudaFree(g->sp_out);
   g->s.release();
   delete g;
   return ATOS_OK;
@@ -554,8 +589,14 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   if (rc) return rc;
   if (!g->d_res) ATOS_TRY(dev_alloc(&g->d_res, (size_t)n));
   if (!g->d_qbits) ATOS_TRY(dev_alloc(&g->d_qbits, (size_t)(n + 31) / 32));
+  const bool spread = (cfg.flags & ATOS_FLAG_SPREAD_IDS) && !bsp;
+  if (spread) {
+    rc = ensure_spread(g, st);
+    if (rc) return rc;
+  }
   Instance I = base_instance(g, 0, kAppPr, cap, (uint32_t)n, -1);
-  I.rank = rank;
+  I.rank = spread ? (float*)g->sp_out : rank;
+  if (spread) I.row_ptr = g->sp_row_ptr, I.col = g->sp_col;
   I.res = g->d_res;
   I.qbits = g->d_qbits;
   I.alpha = alpha;
@@ -582,6 +623,7 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   }
   if (stats && !g->d_cert) ATOS_TRY(dev_alloc(&g->d_cert, (size_t)n));
   ATOS_TRY(pr_finish(g->s.d_insts, 1, n, g->nnz, g->s.d_ctl, stats ? g->d_cert : nullptr, exact_sum, st));
+  if (spread) ATOS_TRY(unspread_f32((const float*)g->sp_out, rank, n, g->sp_a, g->sp_c, st));
   ATOS_TRY(cudaEventRecord(g->s.ev1, st));
   if (stats) {
     rc = collect_stats(g, 1, st, stats);
@@ -650,8 +692,14 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   rc = ensure_scratch(g, 1, cap);
   if (rc) return rc;
   if (!g->d_qbits) ATOS_TRY(dev_alloc(&g->d_qbits, (size_t)(n + 31) / 32));
+  const bool spread = (cfg.flags & ATOS_FLAG_SPREAD_IDS) != 0;
+  if (spread) {
+    rc = ensure_spread(g, st);
+    if (rc) return rc;
+  }
   Instance I = base_instance(g, 0, kAppGc, cap, (uint32_t)n, -1);
-  I.color = colors;
+  I.color = spread ? (int32_t*)g->sp_out : colors;
+  if (spread) I.row_ptr = g->sp_row_ptr, I.col = g->sp_col;
   I.qbits = g->d_qbits;
   g->s.h_insts[0] = I;
   cfg.window = 1;
@@ -660,6 +708,7 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   rc = run_instances(g, 1, n, cfg, gc_persistent_kernel, gc_discrete_kernel, kAppGc, st, &iters);
   if (rc) return rc;
   ATOS_TRY(gc_finish(&I, g->s.d_ctl, st));
+  if (spread) ATOS_TRY(unspread_i32((const int32_t*)g->sp_out, colors, n, g->sp_a, g->sp_c, st));
   ATOS_TRY(cudaEventRecord(g->s.ev1, st));
   if (stats || num_colors) {
     atos_stats local;

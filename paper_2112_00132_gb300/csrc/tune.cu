@@ -1,6 +1,7 @@
 // tune.cu -- autotuner: picks worker size, fetch size, fetch policy, strategy and (BFS with many
 // sources) the instance window for one application on one graph by timing the candidates, the
-// sweep of Figure 4 (worker size x FETCH_SIZE) extended with the kernel strategy (Section 3.4).
+// sweep of Figure 4 (worker size x FETCH_SIZE) extended with the kernel strategy (Section 3.4) and,
+// for PageRank and colouring, the spread-id layout of the graph.
 //
 // Candidates are run on the caller's graph through the public entry points (each run is checked:
 // a candidate that fails, or a PageRank candidate whose FP64 error bound exceeds
@@ -68,6 +69,16 @@ std::vector<atos_config> candidates(int app, int nsrc) {
       c.flags |= ATOS_FLAG_PR_CROSSING;
       out.push_back(c);
     }
+  }
+  if (app == ATOS_APP_PAGERANK || app == ATOS_APP_COLOR) {
+    // the same shapes on the spread-id copy of the graph
+    const size_t k = out.size();
+    for (size_t i = 0; i < k; ++i)
+      if (out[i].strategy != ATOS_BSP && !(out[i].flags & ATOS_FLAG_PR_CROSSING)) {
+        atos_config c = out[i];
+        c.flags |= ATOS_FLAG_SPREAD_IDS;
+        out.push_back(c);
+      }
   }
   if (app == ATOS_APP_BFS && nsrc > 1) {
     for (int w : {256, 512})

@@ -216,3 +216,38 @@ def test_stats_batches_and_idle_polls(atos):
             assert 0 < st.batches <= st.tasks <= st.batches * fetch
         _, st = G.pagerank(ALPHA, EPS, cfg=atos.queue_config("bsp"))
         assert st.batches == 0
+
+
+@pytest.mark.parametrize("gname", ["rmat12", "rmat11_del", "grid97x61_del", "star1000", "clique40", "two_parts",
+                                   "path300", "single", "isolated3"])
+def test_spread_ids_all_configs(atos, graphs, gname):
+    """PageRank and colouring on the spread-id copy of the graph (ATOS_FLAG_SPREAD_IDS): results in
+    the caller's ids, the same gates as on the original layout."""
+    g = graphs[gname]
+    ref = pr_reference(g)
+    with atos.Graph.from_csr(g) as G:
+        for cname, cfg in configs(atos).items():
+            cfg.flags |= atos.FLAG_SPREAD_IDS
+            rank, st = G.pagerank(ALPHA, EPS, cfg=cfg)
+            q = rank.cpu().numpy().astype(np.float64)
+            l1 = np.abs(q - ref).sum()
+            assert st.status == 0 and l1 <= PR_L1_TOL, f"{gname}/{cname}: L1 {l1}"
+            assert l1 <= st.error_bound * 1.0001 + 1e-12, f"{gname}/{cname}: L1 {l1} > bound {st.error_bound}"
+            colors, k, st = G.color(cfg=cfg)
+            code, bad, kk = oracle.check_coloring(g, colors.cpu().numpy())
+            assert st.status == 0 and code == 0 and k == kk, f"{gname}/{cname}: code {code} vertex {bad}"
+            if cname != "bsp":
+                assert G.scratch_check() == (0, 0), f"{gname}/{cname}: {G.scratch_check()}"
+
+
+def test_spread_ids_full_size_rmat22(atos):
+    g = gg.rmat(22, 16, seed=1)
+    cfg = atos.queue_config(worker_size=1024, fetch_size=1024, check_size=8, flags=atos.FLAG_SPREAD_IDS)
+    with atos.Graph.from_csr(g) as G:
+        rank, st = G.pagerank(ALPHA, EPS, cfg=cfg)
+        colors, k, st_c = G.color(cfg=atos.queue_config(flags=atos.FLAG_SPREAD_IDS))
+    q = rank.cpu().numpy().astype(np.float64)
+    bound = oracle.pr_error_bound(g, q / q.sum(), ALPHA)
+    assert st.status == 0 and bound <= PR_L1_TOL and st.error_bound <= PR_L1_TOL
+    code, bad, kk = oracle.check_coloring(g, colors.cpu().numpy())
+    assert st_c.status == 0 and code == 0 and k == kk
