@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--fetch", type=int, default=256, help="with --no-tune: fetch size for every app")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use --worker / --fetch")
     ap.add_argument("--check-size", type=int, default=32, help="with --no-tune: PageRank's Check_Size")
+    ap.add_argument("--flags", type=int, default=0, help="with --no-tune: atos_config.flags of PageRank and colouring")
     ap.add_argument("--no-compare", action="store_true", help="skip the BSP / unbatched comparisons")
     ap.add_argument("--workload", default="rmat22", choices=["rmat22", "batched"],
                     help="rmat22: the single-graph step (default); batched: 256 graphs x (4 BFS + 1 PageRank) "
@@ -162,18 +163,21 @@ def recorded_traffic(cfg_pr):
     import hashlib
     path = os.path.join(ROOT, "profiles", "pagerank_traffic_rmat22.txt")
     try:
-        rec = dict(line.split(": ", 1) for line in open(path).read().splitlines()
-                   if ": " in line and not line.startswith((" ", "#")))
+        lines = open(path).read().splitlines()
     except OSError:
         return None
+    digest = [ln.split(": ", 1)[1].strip() for ln in lines if ln.startswith("kernel_sources_sha256: ")]
     h = hashlib.sha256()
-    for f in ("engine.cuh", "pagerank.cuh", "pagerank.cu"):
+    for f in ("engine.cuh", "pagerank.cuh", "pagerank.cu", "relabel.cu"):
         h.update(open(os.path.join(ROOT, "paper_2112_00132_gb300", "csrc", f), "rb").read())
-    if rec.get("kernel_sources_sha256", "").strip() != h.hexdigest():
+    if not digest or digest[0] != h.hexdigest():
         return None
-    if int(rec.get("worker", 0)) != cfg_pr.worker_size or int(rec.get("check_size", 0)) != cfg_pr.check_size:
-        return None
-    return float(rec["traffic_bytes_per_launch"])
+    for ln in lines:
+        if ln.startswith("entry: "):
+            w, cs, fl, traffic = ln.split()[1:5]
+            if (int(w), int(cs), int(fl)) == (cfg_pr.worker_size, cfg_pr.check_size, cfg_pr.flags):
+                return float(traffic)
+    return None
 
 
 # ------------------------------------------------------------------------------- atos arm
@@ -207,8 +211,10 @@ def run_atos(args, rank: int, world: int):
 
     # configuration per application: the autotuner's choice (untimed sweep), unless fixed
     if args.no_tune:
-        cfg_bfs = cfg_gc = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch)
-        cfg_pr = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch, check_size=args.check_size)
+        cfg_bfs = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch)
+        cfg_gc = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch, flags=args.flags)
+        cfg_pr = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch, check_size=args.check_size,
+                                   flags=args.flags)
         tune_ms = {}
     else:
         cfg_bfs, t_b = G.autotune("bfs", srcs, repeats=1, stream=stream)
@@ -295,27 +301,33 @@ def run_atos(args, rank: int, world: int):
     dom_ms, dom_bytes = parts[dom]
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     traffic = recorded_traffic(cfg_pr) if (dom == "pagerank_persistent" and args.scale == 22
-                                           and cfg_pr.flags == 0 and cfg_pr.strategy == 0) else None
+                                           and cfg_pr.strategy == 0) else None
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src, "traffic": traffic,
                 "traffic_source": "profiles/pagerank_traffic_rmat22.txt (ncu, one launch)" if traffic else None,
                 "algorithmic_bytes": dom_bytes, "launch_ms": round(dom_ms, 3)}
     # the edge-loop ceilings on this graph (library probe, no scheduler): the rate the bodies'
     # inner loops could reach; the kernels are bound by L2 atomics and gather latency, not HBM
-    scatter_ms = G.edge_ceiling("scatter", repeats=3, stream=stream)
-    gather_ms = G.edge_ceiling("gather", repeats=3, stream=stream)
-    scatter_g, gather_g = g.nnz / scatter_ms / 1e6, g.nnz / gather_ms / 1e6
+    # each on the layout the application ran on (spread ids when its configuration says so)
+    def ceiling(kind, spread):
+        return g.nnz / G.edge_ceiling(kind, repeats=3, stream=stream, spread_ids=spread) / 1e6
+    pr_spread, gc_spread = bool(cfg_pr.flags & atos.FLAG_SPREAD_IDS), bool(cfg_gc.flags & atos.FLAG_SPREAD_IDS)
+    scatter_g = ceiling("scatter", pr_spread)
+    gather_bfs_g = ceiling("gather", False)
+    gather_gc_g = ceiling("gather", gc_spread)
     bfs_reads = float(bfs_stats.edges)
+    rate = lambda work, ms: work / (mean(ms) * 1e-3) / 1e9  # noqa: E731
     edge_ceiling = {
-        "unit": "G edge operations/s", "scatter_ceiling": round(scatter_g, 1), "gather_ceiling": round(gather_g, 1),
-        "pagerank_achieved": round(pr_edges / (mean(pr_ms) * 1e-3) / 1e9, 1),
-        "pagerank_frac": round(pr_edges / (mean(pr_ms) * 1e-3) / 1e9 / scatter_g, 3),
-        "bfs_achieved": round(bfs_reads / (mean(bfs_ms) * 1e-3) / 1e9, 1),
-        "bfs_frac": round(bfs_reads / (mean(bfs_ms) * 1e-3) / 1e9 / gather_g, 3),
-        "color_achieved": round(gc_edges / (mean(gc_ms) * 1e-3) / 1e9, 1),
-        "color_frac": round(gc_edges / (mean(gc_ms) * 1e-3) / 1e9 / gather_g, 3),
-        "probe": "atos_edge_ceiling: one pass over every CSR entry in order, col[e] then red.add.f32 "
-                 "(scatter) or a load (gather) of state[col[e]]; BFS/colouring counted as neighbour entries read",
+        "unit": "G edge operations/s",
+        "pagerank": {"achieved": round(rate(pr_edges, pr_ms), 1), "ceiling": round(scatter_g, 1),
+                     "frac": round(rate(pr_edges, pr_ms) / scatter_g, 3), "layout": "spread" if pr_spread else "input"},
+        "bfs": {"achieved": round(rate(bfs_reads, bfs_ms), 1), "ceiling": round(gather_bfs_g, 1),
+                "frac": round(rate(bfs_reads, bfs_ms) / gather_bfs_g, 3), "layout": "input"},
+        "color": {"achieved": round(rate(gc_edges, gc_ms), 1), "ceiling": round(gather_gc_g, 1),
+                  "frac": round(rate(gc_edges, gc_ms) / gather_gc_g, 3), "layout": "spread" if gc_spread else "input"},
+        "probe": "atos_edge_ceiling: one pass over every CSR entry in order, col[e] then red.add.f32 (PageRank: "
+                 "scatter) or a load (BFS, colouring: gather) of state[col[e]], on the application's layout; "
+                 "BFS and colouring work counted as neighbour entries read",
     }
 
     def brief(c):

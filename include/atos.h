@@ -197,6 +197,8 @@ int atos_debug_scratch_check(atos_graph_t g, uint64_t* set_bits, uint64_t* busy_
  * the PageRank kernel (limited on scale-free graphs by same-address atomics at the hubs). */
 #define ATOS_CEILING_SCATTER 0
 #define ATOS_CEILING_GATHER 1
+#define ATOS_CEILING_SPREAD_IDS 2 /* or-ed into kind: measure on the spread-id copy of the graph
+                                     (the layout ATOS_FLAG_SPREAD_IDS runs on; built if needed) */
 int atos_edge_ceiling(atos_graph_t g, int32_t kind, int32_t repeats, double* ms_per_pass, void* stream);
 
 /* Number of CUDA kernels this library has launched in this process (monotone counter, all

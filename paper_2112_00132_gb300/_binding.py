@@ -322,11 +322,12 @@ class Graph:
                                    ctypes.byref(best), ctypes.byref(ms), _stream_handle(stream)), "atos_autotune")
         return best, ms.value
 
-    def edge_ceiling(self, kind: str = "scatter", repeats: int = 3, stream=None) -> float:
+    def edge_ceiling(self, kind: str = "scatter", repeats: int = 3, stream=None, spread_ids: bool = False) -> float:
         """Device ms of one ideal pass over every CSR entry ("scatter": red.add into state[col[e]],
-        "gather": a load of state[col[e]]), with no scheduler: the edge-loop roofline."""
+        "gather": a load of state[col[e]]), with no scheduler: the edge-loop roofline (on the
+        spread-id copy of the graph when ``spread_ids``)."""
         ms = ctypes.c_double(0)
-        code = {"scatter": 0, "gather": 1}[kind]
+        code = {"scatter": 0, "gather": 1}[kind] | (2 if spread_ids else 0)
         _check(lib().atos_edge_ceiling(self._h, code, repeats, ctypes.byref(ms), _stream_handle(stream)),
                "atos_edge_ceiling")
         return ms.value

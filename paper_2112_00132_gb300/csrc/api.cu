@@ -343,6 +343,15 @@ Instance base_instance(atos_graph_s* g, int i, int app, uint32_t cap, uint32_t p
 
 namespace atos {
 // Device CSR of a graph, for the batch API.
+int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st) {
+  if (!g) return ATOS_ERR_INVALID_ARG;
+  const int rc = ensure_spread(g, st);
+  if (rc) return rc;
+  *row_ptr = g->sp_row_ptr;
+  *col = g->sp_col;
+  return ATOS_OK;
+}
+
 int graph_device_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, int32_t* n_isolated) {
   if (!g) return ATOS_ERR_INVALID_ARG;
   *row_ptr = g->row_ptr;

@@ -16,6 +16,7 @@
 
 namespace atos {
 int graph_device_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, int32_t* n_isolated);
+int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st);
 
 namespace {
 
@@ -39,7 +40,9 @@ __global__ void ideal_gather_kernel(const int32_t* __restrict__ col, int64_t nnz
 using namespace atos;
 
 extern "C" int atos_edge_ceiling(atos_graph_t g, int32_t kind, int32_t repeats, double* ms_per_pass, void* stream) {
-  if (!g || !ms_per_pass || repeats < 1 || (kind != ATOS_CEILING_SCATTER && kind != ATOS_CEILING_GATHER))
+  const int base_kind = kind & ~ATOS_CEILING_SPREAD_IDS;
+  if (!g || !ms_per_pass || repeats < 1 || (base_kind != ATOS_CEILING_SCATTER && base_kind != ATOS_CEILING_GATHER) ||
+      (kind & ~(ATOS_CEILING_SPREAD_IDS | 1)))
     return ATOS_ERR_INVALID_ARG;
   int32_t n = 0;
   int64_t nnz = 0;
@@ -48,8 +51,13 @@ extern "C" int atos_edge_ceiling(atos_graph_t g, int32_t kind, int32_t repeats, 
   if (n < 1 || nnz < 1) return ATOS_OK;
   const int32_t *rp = nullptr, *col = nullptr;
   int32_t iso = 0;
-  graph_device_csr(g, &rp, &col, &iso);
   cudaStream_t st = (cudaStream_t)stream;
+  if (kind & ATOS_CEILING_SPREAD_IDS) {
+    const int rc0 = graph_spread_csr(g, &rp, &col, st);
+    if (rc0) return rc0;
+  } else {
+    graph_device_csr(g, &rp, &col, &iso);
+  }
   float* state = nullptr;
   cudaEvent_t a = nullptr, b = nullptr;
   int rc = ATOS_OK;
@@ -63,7 +71,7 @@ extern "C" int atos_edge_ceiling(atos_graph_t g, int32_t kind, int32_t repeats, 
   for (int r = 0; !rc && r <= repeats; ++r) {  // pass 0 warms up
     if (r == 1) cudaEventRecord(a, st);
     count_launches(1);
-    if (kind == ATOS_CEILING_SCATTER) ideal_scatter_kernel<<<blocks, threads, 0, st>>>(col, nnz, state);
+    if (base_kind == ATOS_CEILING_SCATTER) ideal_scatter_kernel<<<blocks, threads, 0, st>>>(col, nnz, state);
     else ideal_gather_kernel<<<blocks, threads, 0, st>>>(col, nnz, state, state + n);
     if (cudaGetLastError() != cudaSuccess) rc = ATOS_ERR_CUDA;
   }

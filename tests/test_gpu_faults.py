@@ -67,9 +67,10 @@ def test_edge_ceiling_probe(atos):
     g = gg.rmat(12, 16, seed=1)
     with atos.Graph.from_csr(g) as G:
         for kind in ("scatter", "gather"):
-            ms = G.edge_ceiling(kind, repeats=2)
-            assert ms > 0
-        rc = atos.abi.lib().atos_edge_ceiling(G._h, 7, 1, ctypes.byref(ctypes.c_double()), None)
+            for spread in (False, True):
+                ms = G.edge_ceiling(kind, repeats=2, spread_ids=spread)
+                assert ms > 0
+        rc = atos.abi.lib().atos_edge_ceiling(G._h, 9, 1, ctypes.byref(ctypes.c_double()), None)
         assert rc == atos.abi.ERR_INVALID_ARG
     with atos.Graph.from_csr(gg.from_edges(3, [], "isolated3")) as G:
         assert G.edge_ceiling("scatter") == 0.0
