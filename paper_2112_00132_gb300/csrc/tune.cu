@@ -143,12 +143,19 @@ int atos_batch_autotune(const atos_graph_t* graphs, int32_t ngraphs, const atos_
   for (int w : {128, 256, 512, 1024}) cands.push_back(make(nullptr, w, w, ATOS_FETCH_SPREAD));
   cands.push_back(make(nullptr, 256, 64, ATOS_FETCH_GREEDY));
   cands.push_back(make(nullptr, 32, 32, ATOS_FETCH_SPREAD));
-  for (int win : {8, 64, 512}) {
-    if (win >= ninst) break;
-    atos_config c = make(nullptr, 256, 256, ATOS_FETCH_SPREAD);
-    c.window = win;
-    cands.push_back(c);
-  }
+  for (int w : {256, 512})
+    for (int win : {8, 64, 512}) {
+      if (win >= ninst) break;
+      atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
+      c.window = win;
+      cands.push_back(c);
+      if (has_pr && win == 512)
+        for (int cs : {8, 16}) {  // PageRank's Check_Size at the widest window
+          atos_config d = c;
+          d.check_size = cs;
+          cands.push_back(d);
+        }
+    }
   cands.push_back(make("discrete-cta", 0, 0, -1));
   if (has_pr)
     for (int w : {256, 512}) {
