@@ -74,8 +74,8 @@ extern "C" {
                                      On scale-free graphs sorted rows all begin with the few low-id
                                      hubs, so a warp's 32 state updates land in a few L2 slices;
                                      spread ids balance them over the slices.  Results come back in
-                                     the caller's ids (one gather).  BFS, BSP, batches and serving
-                                     ignore the flag. */
+                                     the caller's ids (one gather).  Batches and servers apply it to
+                                     their PageRank and colouring instances; BFS and BSP ignore it. */
 
 typedef struct atos_config {
   int32_t worker_size;    /* 32 (warp worker) or a CTA worker of 64, 128, 256, 512 or 1024 threads */

@@ -343,12 +343,15 @@ Instance base_instance(atos_graph_s* g, int i, int app, uint32_t cap, uint32_t p
 
 namespace atos {
 // Device CSR of a graph, for the batch API.
-int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st) {
+int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st, uint64_t* a,
+                     uint64_t* c) {
   if (!g) return ATOS_ERR_INVALID_ARG;
   const int rc = ensure_spread(g, st);
   if (rc) return rc;
   *row_ptr = g->sp_row_ptr;
   *col = g->sp_col;
+  if (a) *a = g->sp_a;
+  if (c) *c = g->sp_c;
   return ATOS_OK;
 }
 

@@ -187,6 +187,11 @@ struct atos_batch_s {
   double* d_cert_y = nullptr;
   double* d_cert = nullptr;
   double* h_cert = nullptr;
+  // ATOS_FLAG_SPREAD_IDS: PageRank / colouring instances run on their graph's spread-id copy,
+  // write into d_sp_out and are mapped back to the caller's outputs at the end of a run
+  char* d_sp_out = nullptr;
+  SpreadJob* d_jobs = nullptr;
+  int njobs = 0, max_n_jobs = 0;
   const void* fn_discrete = nullptr;
   unsigned first_gen = 0;      // discrete strategy: the largest virtual prefix (first generation)
 
@@ -200,6 +205,7 @@ struct atos_batch_s {
     cudaFree(d_insts), cudaFree(d_qctl), cudaFree(d_ring), cudaFree(d_stats), cudaFreeHost(h_stats);
     cudaFree(d_ctl), cudaFreeHost(h_ctl), cudaFree(d_res), cudaFree(d_qbits), cudaFree(d_results);
     cudaFree(d_pr_idx), cudaFree(d_cert_y), cudaFree(d_cert), cudaFreeHost(h_cert);
+    cudaFree(d_sp_out), cudaFree(d_jobs);
     cudaFreeHost(h_results);
   }
 };
@@ -259,6 +265,7 @@ int enqueue_run(atos_batch_s* b, cudaStream_t st) {
   BATCH_TRY(cudaGetLastError());
   // FP64 certificate of every PageRank output (it certifies the FP32 vector returned)
   BATCH_TRY(pr_certify_outputs(b->d_insts, b->d_pr_idx, b->n_pr, b->max_n_pr, b->max_nnz_pr, b->d_cert, st));
+  BATCH_TRY(unspread_jobs(b->d_jobs, b->njobs, b->max_n_jobs, st));  // spread-id results to caller ids
   return ATOS_OK;
 }
 
@@ -268,6 +275,8 @@ int enqueue_run(atos_batch_s* b, cudaStream_t st) {
 extern "C" int atos_graph_info(atos_graph_t g, int32_t* n, int64_t* nnz, int32_t* max_degree);
 namespace atos {
 int graph_device_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, int32_t* n_isolated);
+int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st, uint64_t* a,
+                     uint64_t* c);
 }
 
 extern "C" {
@@ -346,6 +355,19 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
   if (!rc) rc = cuda_rc(cudaMallocHost((void**)&b->h_ctl, sizeof(DevCtl)));
   if (!rc && res_total) rc = cuda_rc(cudaMalloc((void**)&b->d_res, sizeof(float) * res_total));
   if (!rc && bits_total) rc = cuda_rc(cudaMalloc((void**)&b->d_qbits, sizeof(uint32_t) * bits_total));
+  const bool spread = (cfg.flags & ATOS_FLAG_SPREAD_IDS) != 0;
+  std::vector<uint64_t> sp_off(ninst, 0);
+  uint64_t sp_total = 0;
+  if (spread)
+    for (int32_t i = 0; i < ninst; ++i)
+      if (inst[i].app != ATOS_APP_BFS) {
+        sp_off[i] = sp_total;
+        sp_total += ((uint64_t)gn[inst[i].graph] + 63) & ~(uint64_t)63;
+        b->njobs++;
+        b->max_n_jobs = std::max(b->max_n_jobs, gn[inst[i].graph]);
+      }
+  if (!rc && sp_total) rc = cuda_rc(cudaMalloc((void**)&b->d_sp_out, sizeof(int32_t) * sp_total));
+  if (!rc && b->njobs) rc = cuda_rc(cudaMalloc((void**)&b->d_jobs, sizeof(SpreadJob) * b->njobs));
   if (!rc && b->n_pr) {
     rc = cuda_rc(cudaMalloc((void**)&b->d_cert_y, sizeof(double) * res_total));  // same row offsets as res
     if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_pr_idx, sizeof(int) * b->n_pr));
@@ -364,12 +386,26 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
   b->exact_sum.assign(ninst, 0.0);
   b->alpha.assign(ninst, 0.0f);
   std::vector<int> pr_idx;
+  std::vector<SpreadJob> jobs;
   for (int32_t i = 0; i < ninst; ++i) {
     const atos_instance& q = inst[i];
     const int32_t* rp = nullptr;
     const int32_t* col = nullptr;
     int32_t iso = 0;
     graph_device_csr(graphs[q.graph], &rp, &col, &iso);
+    SpreadJob job;
+    memset(&job, 0, sizeof(job));
+    if (spread && q.app != ATOS_APP_BFS) {
+      // the spread-id copy of the graph (built on the legacy stream the first time; create is synchronous)
+      const int rc2 = graph_spread_csr(graphs[q.graph], &rp, &col, 0, &job.a, &job.c);
+      if (rc2) {
+        delete b;
+        return rc2;
+      }
+      job.src = b->d_sp_out + sizeof(int32_t) * sp_off[i];
+      job.dst = q.out;
+      job.n = gn[q.graph];
+    }
     Instance I;
     memset(&I, 0, sizeof(I));
     I.row_ptr = rp;
@@ -388,7 +424,7 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
       I.app = kAppPr;
       I.prefix_len = (uint32_t)I.n;
       I.prefix_item = -1;
-      I.rank = (float*)q.out;
+      I.rank = job.src ? (float*)job.src : (float*)q.out;
       I.res = b->d_res + res_off[i];
       I.qbits = b->d_qbits + bits_off[i];
       I.alpha = q.alpha;
@@ -404,15 +440,18 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
       I.app = kAppGc;
       I.prefix_len = (uint32_t)I.n;
       I.prefix_item = -1;
-      I.color = (int32_t*)q.out;
+      I.color = job.src ? (int32_t*)job.src : (int32_t*)q.out;
       I.qbits = b->d_qbits + bits_off[i];
     }
     b->h_insts[i] = I;
     b->first_gen = std::max(b->first_gen, I.prefix_len);
+    if (job.src) jobs.push_back(job);
   }
   rc = cuda_rc(cudaMemcpy(b->d_insts, b->h_insts.data(), sizeof(Instance) * ninst, cudaMemcpyHostToDevice));
   if (!rc && b->n_pr)
     rc = cuda_rc(cudaMemcpy(b->d_pr_idx, pr_idx.data(), sizeof(int) * b->n_pr, cudaMemcpyHostToDevice));
+  if (!rc && b->njobs)
+    rc = cuda_rc(cudaMemcpy(b->d_jobs, jobs.data(), sizeof(SpreadJob) * b->njobs, cudaMemcpyHostToDevice));
   DevCtl init;
   memset(&init, 0, sizeof(init));
   init.dirty = 1;  // fresh rings: the first prepare fills them

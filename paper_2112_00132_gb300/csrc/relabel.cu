@@ -14,6 +14,7 @@
 #include <numeric>
 
 #include "launch.cuh"
+#include "state.cuh"
 
 namespace atos {
 namespace bsp {
@@ -78,6 +79,21 @@ cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, uint6
   e = bsp::scan_inplace(new_rp, n, bsums, s);  // exclusive scan; new_rp[n] = nnz
   if (e != cudaSuccess) return e;
   spread_cols_kernel<<<grid_for((int64_t)n * 32, 256, 8192), 256, 0, s>>>(rp, col, n, a, c, new_rp, new_col);
+  return cudaGetLastError();
+}
+
+__global__ void unspread_jobs_kernel(const SpreadJob* jobs) {
+  const SpreadJob J = jobs[blockIdx.y];
+  const int32_t* src = (const int32_t*)J.src;  // 4-byte elements (float ranks or int32 colours)
+  int32_t* dst = (int32_t*)J.dst;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < J.n; v += gridDim.x * blockDim.x)
+    dst[v] = src[spread_id((uint32_t)v, J.a, J.c, (uint32_t)J.n)];
+}
+
+cudaError_t unspread_jobs(const SpreadJob* d_jobs, int njobs, int max_n, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  count_launches(1);
+  unspread_jobs_kernel<<<dim3(grid_for(max_n, 256, 1024), njobs), 256, 0, s>>>(d_jobs);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,8 @@
 namespace atos {
 const void* mixed_persistent_kernel(int worker);
 int graph_device_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, int32_t* n_isolated);
+int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st, uint64_t* a,
+                     uint64_t* c);
 cudaError_t batch_finish_terminated(const Instance* d_insts, int ninst, int max_n, void* d_results, cudaStream_t s);
 size_t batch_result_bytes();
 void batch_result_read(const void* h_result, double* sum_rank, double* sum_res, int* num_colors);
@@ -126,6 +128,7 @@ struct Slot {
   float alpha = 0.85f;
   double exact_sum = 0.0;
   Instance inst;
+  SpreadJob job;  // spread-id requests: the result's way back to the caller's ids (src == nullptr: none)
 };
 
 uint32_t pow2_ceil(uint64_t x) {
@@ -180,6 +183,8 @@ struct atos_server_s {
   int* h_cert_idx = nullptr;  // pinned
   double* d_cert = nullptr;
   double* h_cert = nullptr;   // pinned
+  SpreadJob* d_jobs = nullptr;
+  SpreadJob* h_jobs = nullptr;  // pinned
   std::deque<atos_completion> done;
   int64_t epochs = 0;
 
@@ -190,6 +195,7 @@ struct atos_server_s {
     cudaFree(d_stats), cudaFreeHost(h_stats), cudaFree(d_ctl), cudaFreeHost(h_ctl), cudaFree(d_fin);
     cudaFreeHost(h_fin), cudaFree(d_results), cudaFreeHost(h_results);
     cudaFree(d_cert_idx), cudaFreeHost(h_cert_idx), cudaFree(d_cert), cudaFreeHost(h_cert);
+    cudaFree(d_jobs), cudaFreeHost(h_jobs);
     if (stream) cudaStreamDestroy(stream);
   }
 };
@@ -207,6 +213,7 @@ size_t request_bytes(const atos_server_s* s, int app, int32_t n, uint32_t* cap_o
   b += 2 * ((size_t)s->orphan_cap * 4 + 256);       // pending tickets of a pause, two epochs
   if (app == ATOS_APP_PAGERANK) b += (size_t)n * 4 + 256 + (size_t)n * 8 + 256;  // residues, certificate
   if (app != ATOS_APP_BFS) b += (size_t)(n + 31) / 32 * 4 + 256;  // queued bits
+  if (app != ATOS_APP_BFS && (s->cfg.flags & ATOS_FLAG_SPREAD_IDS)) b += (size_t)n * 4 + 256;  // spread-id output
   return b;
 }
 
@@ -279,6 +286,8 @@ int atos_server_create(const atos_graph_t* graphs, int32_t ngraphs, int32_t max_
   if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_cert_idx, sizeof(int) * max_slots));
   if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_cert, sizeof(double) * max_slots));
   if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_cert, sizeof(double) * max_slots));
+  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_jobs, sizeof(SpreadJob) * max_slots));
+  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_jobs, sizeof(SpreadJob) * max_slots));
   if (!rc) rc = rc_of(cudaMemsetAsync(s->d_ctl, 0, sizeof(DevCtl), s->stream));
   if (rc) {
     delete s;
@@ -319,6 +328,19 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
   const int32_t *rp, *col;
   int32_t iso = 0;
   graph_device_csr(s->graphs[q->graph], &rp, &col, &iso);
+  SpreadJob job;
+  memset(&job, 0, sizeof(job));
+  if (q->app != ATOS_APP_BFS && (s->cfg.flags & ATOS_FLAG_SPREAD_IDS)) {
+    // the graph's spread-id copy (built the first time, synchronising the server stream)
+    const int rc2 = graph_spread_csr(s->graphs[q->graph], &rp, &col, s->stream, &job.a, &job.c);
+    if (rc2) {
+      s->arena.release(off, bytes);
+      return rc2;
+    }
+    job.src = take((size_t)n * 4);
+    job.dst = q->out;
+    job.n = n;
+  }
   Instance I;
   memset(&I, 0, sizeof(I));
   I.row_ptr = rp;
@@ -343,7 +365,7 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
     I.app = kAppPr;
     I.prefix_len = (uint32_t)n;
     I.prefix_item = -1;
-    I.rank = (float*)q->out;
+    I.rank = job.src ? (float*)job.src : (float*)q->out;
     I.res = (float*)take((size_t)n * 4);
     I.cert_y = (double*)take((size_t)n * 8);
     I.exact_sum = (double)n - (double)q->alpha * iso;
@@ -358,7 +380,7 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
     I.app = kAppGc;
     I.prefix_len = (uint32_t)n;
     I.prefix_item = -1;
-    I.color = (int32_t*)q->out;
+    I.color = job.src ? (int32_t*)job.src : (int32_t*)q->out;
     I.qbits = (uint32_t*)take((size_t)(n + 31) / 32 * 4);
   }
   sl.state = kActive;
@@ -368,6 +390,7 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
   sl.off = off;
   sl.bytes = bytes;
   sl.inst = I;
+  sl.job = job;
   // initialise on the server stream: descriptor, free ring, state (prepare), PageRank residues.
   // Nothing waits here: the descriptor is copied from pinned staging that this slot alone uses
   // (the slot is not reused before a later step has synchronised the stream), and the next
@@ -457,12 +480,25 @@ int atos_server_step(atos_server_t s, int64_t slice_ns, int32_t* active_left) {
       cert_n = std::max(cert_n, (int)sl.inst.n);
       cert_nnz = std::max(cert_nnz, s->gnnz[sl.graph]);
     }
+  // spread-id results back to the callers' ids
+  int njobs = 0, jobs_n = 1;
+  if (status == 0)
+    for (size_t f = 0; f < finished.size(); ++f) {
+      const Slot& sl = s->slots[finished[f]];
+      if (!sl.job.src) continue;
+      s->h_jobs[njobs++] = sl.job;
+      jobs_n = std::max(jobs_n, (int)sl.job.n);
+    }
+  if (njobs) {
+    SRV_TRY(cudaMemcpyAsync(s->d_jobs, s->h_jobs, sizeof(SpreadJob) * njobs, cudaMemcpyHostToDevice, st));
+    SRV_TRY(unspread_jobs(s->d_jobs, njobs, jobs_n, st));
+  }
   if (ncert) {
     SRV_TRY(cudaMemcpyAsync(s->d_cert_idx, s->h_cert_idx, sizeof(int) * ncert, cudaMemcpyHostToDevice, st));
     SRV_TRY(pr_certify_outputs(s->d_active, s->d_cert_idx, ncert, cert_n, cert_nnz, s->d_cert, st));
     SRV_TRY(cudaMemcpyAsync(s->h_cert, s->d_cert, sizeof(double) * ncert, cudaMemcpyDeviceToHost, st));
-    SRV_TRY(cudaStreamSynchronize(st));
   }
+  if (ncert || njobs) SRV_TRY(cudaStreamSynchronize(st));
   for (size_t f = 0; f < finished.size(); ++f) {
     const int i = finished[f];
     Slot& sl = s->slots[i];

@@ -29,6 +29,17 @@ cudaError_t launch_pr_init(Instance* d_insts, int ninst, int64_t max_nnz, cudaSt
 cudaError_t launch_next_generation(Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
 cudaError_t launch_finalize(const Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
 
+// Results computed on the spread-id copy of a graph, to be returned in the caller's ids:
+// dst[v] = src[(a v + c) mod n] for 4-byte elements.
+struct SpreadJob {
+  const void* src;
+  void* dst;
+  int32_t n;
+  int32_t pad;
+  uint64_t a, c;
+};
+cudaError_t unspread_jobs(const SpreadJob* d_jobs, int njobs, int max_n, cudaStream_t s);
+
 // FP64 certificate of normalised PageRank outputs (ranks summing to 1): for the instances
 // d_insts[d_idx[j]], j < count, out[j] = ||(1 - alpha) 1 + alpha P x - x||_1 with x = exact_sum *
 // rank, so the L1 distance of the output to the normalised fixed point is at most

@@ -157,6 +157,16 @@ int atos_batch_autotune(const atos_graph_t* graphs, int32_t ngraphs, const atos_
         }
     }
   cands.push_back(make("discrete-cta", 0, 0, -1));
+  {
+    // the persistent shapes so far on the spread-id copies of the graphs
+    const size_t k = cands.size();
+    for (size_t i = 0; i < k; ++i)
+      if (cands[i].strategy == ATOS_PERSISTENT) {
+        atos_config c = cands[i];
+        c.flags |= ATOS_FLAG_SPREAD_IDS;
+        cands.push_back(c);
+      }
+  }
   if (has_pr)
     for (int w : {256, 512}) {
       atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);

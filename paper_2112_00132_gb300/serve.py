@@ -73,6 +73,8 @@ def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), sli
     if budget_bytes is None:
         free, _ = torch.cuda.mem_get_info()
         budget_bytes = int(min(free * 0.5, 64 << 30))
+    if cfg is None:  # PageRank and colouring on the graphs' spread-id copies (faster on every graph measured)
+        cfg = abi.queue_config(flags=abi.FLAG_SPREAD_IDS)
     server = abi.Server(graphs, max_slots=max_slots, budget_bytes=budget_bytes, cfg=cfg)
     arrivals = make_arrivals(rate, duration, mix, len(graphs), seed)
     backlog, backlog_large = [], []
@@ -150,6 +152,7 @@ def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), sli
         "epochs": info["epochs"], "steps": steps, "slice_ms": slice_ns / 1e6, "wall_s": round(wall, 2),
         "graphs": len(csrs), "max_slots": max_slots, "arena_bytes": budget_bytes,
         "admission": f"two FIFO queues; at most {max_large} requests on graphs of > {large_n} vertices in flight",
+        "config": {"worker": cfg.worker_size, "fetch": cfg.fetch_size, "flags": cfg.flags},
     }
     if keep:
         res["kept"] = kept

@@ -168,3 +168,20 @@ def test_batch_autotune(atos, graphs):
         check_results(graphs, specs, B.outputs, per)
     for G in Gs:
         G.close()
+
+
+@pytest.mark.parametrize("preset,worker", [(None, 256), (None, 1024), ("discrete-cta", 256), (None, 32)])
+def test_mixed_batch_spread_ids(atos, graphs, preset, worker):
+    """PageRank and colouring instances on their graphs' spread-id copies inside a batch: results in
+    the caller's ids, the same gates; BFS instances of the same batch unaffected."""
+    Gs = [atos.Graph.from_csr(g) for g in graphs]
+    specs = mixed_specs(graphs, per_graph_bfs=2)
+    cfg = atos.queue_config(preset, worker_size=worker, fetch_size=32 if worker == 32 else worker,
+                            flags=atos.FLAG_SPREAD_IDS)
+    with atos.Batch(Gs, specs, cfg) as B:
+        B.run(graph=cfg.strategy == atos.PERSISTENT)
+        total, per = B.stats()
+        assert total.status == 0
+        check_results(graphs, specs, B.outputs, per)
+    for G in Gs:
+        G.close()

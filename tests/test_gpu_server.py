@@ -127,3 +127,31 @@ def test_serving_loop_short_run(atos, graphs):
     assert res["p50_ms"] is not None and res["p99_ms"] >= res["p50_ms"] > 0
     for r in res["kept"]:
         assert check(graphs[r["graph"]], r["kind"], r["source"], r["out"]), r["kind"]
+
+
+def test_server_spread_ids(atos, graphs):
+    """A server whose PageRank and colouring requests run on the graphs' spread-id copies."""
+    Gs = [atos.Graph.from_csr(g) for g in graphs]
+    reqs = {}
+    cfg = atos.queue_config(flags=atos.FLAG_SPREAD_IDS)
+    with atos.Server(Gs, max_slots=16, budget_bytes=2 << 30, cfg=cfg) as S:
+        for gi, g in enumerate(graphs):
+            rid, _ = S.submit("pagerank", gi, alpha=ALPHA, eps=EPS)
+            reqs[rid] = ("pagerank", gi, 0)
+            rid, _ = S.submit("color", gi)
+            reqs[rid] = ("color", gi, 0)
+            src = int(gg.sources(g, 1, seed=gi + 3)[0])
+            rid, _ = S.submit("bfs", gi, src)
+            reqs[rid] = ("bfs", gi, src)
+        done = drain(S, 200_000)
+        assert sorted(d["id"] for d in done) == sorted(reqs)
+        for d in done:
+            kind, gi, src = reqs[d["id"]]
+            assert d["status"] == 0 and check(graphs[gi], kind, src, d["out"]), (kind, gi, src, d)
+            if kind == "pagerank":
+                x, _, _ = oracle.pagerank(graphs[gi], ALPHA)
+                l1 = np.abs(d["out"].cpu().numpy().astype(np.float64) - x / x.sum()).sum()
+                assert l1 <= d["error_bound"] * 1.0001 + 1e-9
+        assert S.info()["arena_used"] == 0
+    for G in Gs:
+        G.close()
