@@ -77,6 +77,10 @@ extern "C" {
                                      the caller's ids (one gather).  Batches and servers apply it to
                                      their PageRank and colouring instances; BFS and BSP ignore it. */
 
+#define ATOS_FLAG_USE_TUNED 8u     /* atos_bfs / atos_pagerank / atos_color use the configuration
+                                     cached by atos_autotune for the graph's class (all fields),
+                                     or this one without the flag when the class is not tuned */
+
 typedef struct atos_config {
   int32_t worker_size;    /* 32 (warp worker) or a CTA worker of 64, 128, 256, 512 or 1024 threads */
   int32_t fetch_size;     /* tasks per pop, 1..1024; at most worker_size for CTA workers (FETCH_SIZE
@@ -125,7 +129,9 @@ typedef struct atos_graph_s* atos_graph_t;
 
 /* Fills *cfg with the preset named `preset`: NULL or "default" (persistent CTA worker of 256
  * threads, fetch 256), "persist-warp" (Section 5's persist-32), "persist-cta", "discrete-cta",
- * "discrete-warp", "bsp".  Returns ATOS_ERR_INVALID_ARG for an unknown name or NULL cfg. */
+ * "discrete-warp", "bsp", or "autotune" (the defaults plus ATOS_FLAG_USE_TUNED: each call takes
+ * the configuration atos_autotune cached for its graph's class and application, and the
+ * defaults when there is none).  Returns ATOS_ERR_INVALID_ARG for an unknown name or NULL cfg. */
 int atos_queue_config(atos_config* cfg, const char* preset);
 
 /* Host-side CSR check (the one atos_graph_create runs on host pointers).  flags may contain

@@ -216,6 +216,14 @@ uint32_t ring_capacity(const atos_config& cfg, int32_t n, uint32_t prefix) {
   return next_pow2(std::max<uint64_t>(want, 1u << 20));
 }
 
+// ATOS_FLAG_USE_TUNED: the configuration cached by the autotuner for g's class, if any.
+void apply_tuned(atos_graph_t g, int32_t app, atos_config* cfg) {
+  if (!(cfg->flags & ATOS_FLAG_USE_TUNED)) return;
+  atos_config t;
+  if (atos_tuned_config(g, app, &t) == ATOS_OK) *cfg = t;
+  cfg->flags &= ~ATOS_FLAG_USE_TUNED;
+}
+
 int check_config(const atos_config& c) {
   if (!worker_supported(c.worker_size)) return ATOS_ERR_UNSUPPORTED;
   if (c.fetch_size < 1 || c.fetch_size > 1024) return ATOS_ERR_INVALID_ARG;
@@ -224,7 +232,8 @@ int check_config(const atos_config& c) {
   if (c.fetch_policy < ATOS_FETCH_FIXED || c.fetch_policy > ATOS_FETCH_SPREAD) return ATOS_ERR_INVALID_ARG;
   if (c.num_blocks < 0 || c.check_size < 0 || c.window < 0 || c.queue_capacity < 0 || c.spin_limit_ns < 0)
     return ATOS_ERR_INVALID_ARG;
-  if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS)) return ATOS_ERR_INVALID_ARG;
+  if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS | ATOS_FLAG_USE_TUNED))
+    return ATOS_ERR_INVALID_ARG;
   return ATOS_OK;
 }
 
@@ -409,6 +418,10 @@ int atos_queue_config(atos_config* cfg, const char* preset) {
     cfg->strategy = ATOS_BSP;
     return ATOS_OK;
   }
+  if (!strcmp(preset, "autotune")) {
+    cfg->flags |= ATOS_FLAG_USE_TUNED;
+    return ATOS_OK;
+  }
   return ATOS_ERR_INVALID_ARG;
 }
 
@@ -518,6 +531,7 @@ int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* dept
   atos_config cfg;
   if (cfg_in) cfg = *cfg_in;
   else default_config(&cfg);
+  apply_tuned(g, ATOS_APP_BFS, &cfg);
   int rc = check_config(cfg);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -583,6 +597,7 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   atos_config cfg;
   if (cfg_in) cfg = *cfg_in;
   else default_config(&cfg);
+  apply_tuned(g, ATOS_APP_PAGERANK, &cfg);
   int rc = check_config(cfg);
   if (rc) return rc;
   if (stats) memset(stats, 0, sizeof(*stats));
@@ -660,6 +675,7 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   atos_config cfg;
   if (cfg_in) cfg = *cfg_in;
   else default_config(&cfg);
+  apply_tuned(g, ATOS_APP_COLOR, &cfg);
   int rc = check_config(cfg);
   if (rc) return rc;
   if (stats) memset(stats, 0, sizeof(*stats));

@@ -46,6 +46,8 @@ def test_queue_config_presets(atos):
     assert (w.worker_size, w.fetch_size) == (32, 1)
     assert atos.queue_config("discrete-cta").strategy == atos.DISCRETE
     assert atos.queue_config("bsp").strategy == atos.BSP
+    t = atos.queue_config("autotune")
+    assert t.flags & atos.abi.FLAG_USE_TUNED and t.worker_size == d.worker_size
     with pytest.raises(atos.AtosError):
         atos.queue_config("no-such-preset")
     assert atos.lib().atos_queue_config(None, None) == atos.abi.ERR_INVALID_ARG

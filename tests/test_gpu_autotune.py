@@ -36,3 +36,22 @@ def test_autotune_each_app(atos):
     with atos.Graph.from_csr(g2) as G2:
         cached = G2.tuned_config("pagerank")
         assert cached is not None and cached.as_dict() == cfg_pr.as_dict()
+
+
+def test_autotune_preset_uses_cached_configs(atos):
+    """queue_config("autotune"): calls take the configuration cached for the graph's class (and the
+    defaults for a class never tuned); results pass the usual gates either way."""
+    g = gg.rmat(11, 16, seed=4)
+    cfg = atos.queue_config("autotune")
+    assert cfg.flags & atos.abi.FLAG_USE_TUNED
+    with atos.Graph.from_csr(gg.path(700)) as P:  # a class nobody tuned
+        d, _ = P.bfs([0], cfg=cfg)
+        assert np.array_equal(d.cpu().numpy()[0], np.arange(700))
+    with atos.Graph.from_csr(g) as G:
+        G.autotune("pagerank", repeats=1)
+        G.autotune("color", repeats=1)
+        rank, st = G.pagerank(0.85, 1e-9, cfg=cfg)
+        x, _, _ = oracle.pagerank(g, 0.85)
+        assert np.abs(rank.cpu().numpy().astype(np.float64) - x / x.sum()).sum() <= 1e-4
+        colors, k, st = G.color(cfg=cfg)
+        assert oracle.check_coloring(g, colors.cpu().numpy())[0] == 0
