@@ -395,6 +395,9 @@ def run_atos(args, rank: int, world: int):
             "bfs_graph500_edges": bfs_edges, "bfs_reached_vertices": reached_v, "bfs_tasks": bfs_stats.tasks,
             "pagerank_edge_pushes": pr_edges, "pagerank_tasks": pr_tasks,
             "pagerank_error_bound": pr_stats.error_bound, "color_edges": gc_edges, "colors": int(ncol),
+            # Table 4's colouring measure: tasks relative to the vertex count (an assign and a
+            # check task per vertex at least, so 2.0 means no recolouring)
+            "color_tasks_per_vertex": round(gc_stats.tasks / g.n, 4),
         },
         "clocks": clocks.summary(),
     }
