@@ -424,13 +424,19 @@ def run_e2e(args, g, srcs, cfgs, work, world):
     colors = torch.empty(g.n, dtype=torch.int32, device="cuda")
 
     cfg_bfs, cfg_pr, cfg_gc = cfgs
+    copy_stream = torch.cuda.Stream()
 
     def step():
         G = atos.Graph(rp_h.numpy(), col_h.numpy(), skip_validation=True, stream=stream)
         G.bfs(srcs, depths, cfg=cfg_bfs, stream=stream, stats=False)
+        # the depths are final: copy them out on a second stream while PageRank and colouring run
+        bfs_done = torch.cuda.Event()
+        bfs_done.record(stream)
+        copy_stream.wait_event(bfs_done)
+        with torch.cuda.stream(copy_stream):
+            depths_h.copy_(depths, non_blocking=True)
         G.pagerank(ALPHA, EPS, rank_t, cfg=cfg_pr, stream=stream, stats=False)
         G.color(colors, cfg=cfg_gc, stream=stream, stats=False)
-        depths_h.copy_(depths, non_blocking=True)
         rank_h.copy_(rank_t, non_blocking=True)
         colors_h.copy_(colors, non_blocking=True)
         torch.cuda.synchronize()
@@ -449,8 +455,9 @@ def run_e2e(args, g, srcs, cfgs, work, world):
     d2h = 4 * NSRC * g.n + 4 * g.n + 4 * g.n
     return {"value": round(world * work / dt / 1e9, 3), "unit": UNIT, "ms_per_step": round(dt * 1e3, 3),
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
-            "note": "graph created from pinned host CSR (validation skipped: checked once before), "
-                    "results copied back to pinned host memory, inside the timed region"}
+            "note": "graph created from pinned host CSR (validation skipped: checked once before), results "
+                    "copied back to pinned host memory (the BFS depths on a second stream, overlapped with "
+                    "PageRank and colouring), all inside the timed region"}
 
 
 # ------------------------------------------------------------------- batched-mix workload

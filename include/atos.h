@@ -207,6 +207,11 @@ int atos_debug_scratch_check(atos_graph_t g, uint64_t* set_bits, uint64_t* busy_
                                      (the layout ATOS_FLAG_SPREAD_IDS runs on; built if needed) */
 int atos_edge_ceiling(atos_graph_t g, int32_t kind, int32_t repeats, double* ms_per_pass, void* stream);
 
+/* The library keeps the device and pinned host blocks of destroyed graphs, batches and servers
+ * for reuse by later ones of the same sizes.  This returns every cached block to the driver
+ * (*cached_bytes_before, may be NULL, receives how many bytes were cached). */
+int atos_pool_trim(int64_t* cached_bytes_before);
+
 /* Number of CUDA kernels this library has launched in this process (monotone counter, all
  * threads, all devices); lets a caller count the launches of a region of its own program. */
 uint64_t atos_kernel_launches(void);

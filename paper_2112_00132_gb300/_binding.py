@@ -158,6 +158,8 @@ def lib() -> ctypes.CDLL:
         for name in ("atos_server_create", "atos_server_submit", "atos_server_step", "atos_server_poll",
                      "atos_server_info", "atos_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
+        L.atos_pool_trim.argtypes = [P(i64)]
+        L.atos_pool_trim.restype = ctypes.c_int
         L.atos_edge_ceiling.argtypes = [vp, i32, i32, P(ctypes.c_double), vp]
         L.atos_edge_ceiling.restype = ctypes.c_int
         L.atos_autotune.argtypes = [vp, i32, vp, i32, vp, i32, P(Config), P(ctypes.c_double), vp]

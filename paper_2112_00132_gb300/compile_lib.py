@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libatos.so")
-SOURCES = ["api.cu", "state.cu", "bfs.cu", "pagerank.cu", "color.cu", "bsp.cu", "batch.cu", "server.cu", "tune.cu", "noalloc.cu", "ceiling.cu", "relabel.cu"]
+SOURCES = ["api.cu", "state.cu", "bfs.cu", "pagerank.cu", "color.cu", "bsp.cu", "batch.cu", "server.cu", "tune.cu", "noalloc.cu", "ceiling.cu", "relabel.cu", "pool.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -24,8 +24,8 @@ cudaError_t pr_finish(Instance* d_insts, int ninst, int n, int64_t nnz, DevCtl* 
                       double exact_sum, cudaStream_t s);
 cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s);
 uint64_t spread_multiplier(int32_t n);
-cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, uint64_t a, uint64_t c, int32_t* new_rp,
-                         int32_t* new_col, int32_t* bsums, cudaStream_t s);
+cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, uint64_t a, uint64_t c, int32_t* perm,
+                         int32_t* new_rp, int32_t* new_col, int32_t* bsums, cudaStream_t s);
 cudaError_t unspread_f32(const float* src, float* dst, int32_t n, uint64_t a, uint64_t c, cudaStream_t s);
 cudaError_t unspread_i32(const int32_t* src, int32_t* dst, int32_t n, uint64_t a, uint64_t c, cudaStream_t s);
 unsigned long long launches_so_far();
@@ -67,7 +67,7 @@ template <class T>
 cudaError_t dev_alloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  return cudaMalloc((void**)p, count * sizeof(T));
+  return pool_malloc((void**)p, count * sizeof(T));
 }
 
 // Scratch owned by a graph: instance table, queue control blocks, rings, statistics and the
@@ -87,8 +87,8 @@ struct Scratch {
   bool upload_pending = false;
 
   void release() {
-    cudaFree(d_insts), cudaFreeHost(h_insts), cudaFree(d_qctl), cudaFree(d_ring);
-    cudaFree(d_stats), cudaFreeHost(h_stats), cudaFree(d_ctl), cudaFreeHost(h_ctl);
+    pool_free(d_insts), pool_free_host(h_insts), pool_free(d_qctl), pool_free(d_ring);
+    pool_free(d_stats), pool_free_host(h_stats), pool_free(d_ctl), pool_free_host(h_ctl);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     if (upload_done) cudaEventDestroy(upload_done);
@@ -117,6 +117,9 @@ struct atos_graph_s {
   // and an n-entry output buffer in the copy's ids
   int32_t* sp_row_ptr = nullptr;
   int32_t* sp_col = nullptr;
+  int32_t* sp_perm = nullptr;  // v -> (sp_a v + sp_c) mod n
+  int32_t* sp_bsums = nullptr;
+  cudaEvent_t sp_ready = nullptr;  // recorded after the build
   void* sp_out = nullptr;
   uint64_t sp_a = 1, sp_c = 0;
 };
@@ -125,24 +128,32 @@ namespace {
 
 // Builds the spread-id copy of g on `st` the first time it is needed.
 int ensure_spread(atos_graph_s* g, cudaStream_t st) {
-  if (g->sp_row_ptr) return ATOS_OK;
+  if (g->sp_row_ptr) {
+    // built earlier, maybe on another stream: order this stream after the build
+    return from_cuda(cudaStreamWaitEvent(st, g->sp_ready, 0));
+  }
   const int32_t n = g->n;
   int32_t* bsums = nullptr;
-  int32_t *rp = nullptr, *col = nullptr;
+  int32_t *rp = nullptr, *col = nullptr, *perm = nullptr;
   void* out = nullptr;
   int rc = from_cuda(dev_alloc(&rp, (size_t)n + 1));
+  if (!rc) rc = from_cuda(dev_alloc(&perm, (size_t)n));
   if (!rc) rc = from_cuda(dev_alloc(&col, (size_t)std::max<int64_t>(g->nnz, 1)));
   if (!rc) rc = from_cuda(dev_alloc(&bsums, (size_t)n / 1024 + 2));
-  if (!rc) rc = from_cuda(cudaMalloc(&out, sizeof(int32_t) * (size_t)n));
+  if (!rc) rc = from_cuda(pool_malloc(&out, sizeof(int32_t) * (size_t)n));
   const uint64_t sa = spread_multiplier(n), sc = (uint64_t)(n / 2);
-  if (!rc) rc = from_cuda(spread_build(g->row_ptr, g->col, n, sa, sc, rp, col, bsums, st));
-  if (!rc) rc = from_cuda(cudaStreamSynchronize(st));  // bsums is freed next
-  cudaFree(bsums);
+  if (!rc) rc = from_cuda(spread_build(g->row_ptr, g->col, n, sa, sc, perm, rp, col, bsums, st));
+  if (!rc && !g->sp_ready) rc = from_cuda(cudaEventCreateWithFlags(&g->sp_ready, cudaEventDisableTiming));
+  if (!rc) rc = from_cuda(cudaEventRecord(g->sp_ready, st));
   if (rc) {
-    cudaFree(rp), cudaFree(col), cudaFree(out);
+    cudaStreamSynchronize(st);  // nothing of a failed build may still run when its buffers go back
+    pool_free(rp), pool_free(col), pool_free(out), pool_free(perm), pool_free(bsums);
     return rc;
   }
-  g->sp_row_ptr = rp, g->sp_col = col, g->sp_out = out, g->sp_a = sa, g->sp_c = sc;
+  // stream-ordered: the build runs before the caller's kernels on `st`; the scan scratch stays
+  // with the graph (freed with it, after the device is idle)
+  g->sp_row_ptr = rp, g->sp_col = col, g->sp_out = out, g->sp_a = sa, g->sp_c = sc, g->sp_perm = perm;
+  g->sp_bsums = bsums;
   return ATOS_OK;
 }
 
@@ -155,7 +166,7 @@ int ensure_scratch(atos_graph_s* g, int ninst, uint32_t cap) {
   }
   if (!s.d_ctl) {
     ATOS_TRY(dev_alloc(&s.d_ctl, 1));
-    ATOS_TRY(cudaMallocHost((void**)&s.h_ctl, sizeof(DevCtl)));
+    ATOS_TRY(pool_malloc_host((void**)&s.h_ctl, sizeof(DevCtl)));
     DevCtl init;
     memset(&init, 0, sizeof(init));
     init.dirty = 1;
@@ -168,19 +179,19 @@ int ensure_scratch(atos_graph_s* g, int ninst, uint32_t cap) {
   if (ninst <= s.ninst && cap == s.cap) return ATOS_OK;
   // (re)allocate; the device must be idle with respect to the old buffers
   cudaDeviceSynchronize();
-  cudaFree(s.d_insts), cudaFreeHost(s.h_insts), cudaFree(s.d_qctl), cudaFree(s.d_ring);
-  cudaFree(s.d_stats), cudaFreeHost(s.h_stats);
+  pool_free(s.d_insts), pool_free_host(s.h_insts), pool_free(s.d_qctl), pool_free(s.d_ring);
+  pool_free(s.d_stats), pool_free_host(s.h_stats);
   s.d_insts = nullptr, s.h_insts = nullptr, s.d_qctl = nullptr, s.d_ring = nullptr;
   s.d_stats = nullptr, s.h_stats = nullptr;
   const int m = std::max(ninst, s.ninst);
   s.ninst = 0;
   s.cap = 0;
   ATOS_TRY(dev_alloc(&s.d_insts, m));
-  ATOS_TRY(cudaMallocHost((void**)&s.h_insts, sizeof(Instance) * m));
+  ATOS_TRY(pool_malloc_host((void**)&s.h_insts, sizeof(Instance) * m));
   ATOS_TRY(dev_alloc(&s.d_qctl, m));
   ATOS_TRY(dev_alloc(&s.d_ring, (size_t)cap * m));
   ATOS_TRY(dev_alloc(&s.d_stats, (size_t)kNumStats * m));
-  ATOS_TRY(cudaMallocHost((void**)&s.h_stats, sizeof(unsigned long long) * kNumStats * m));
+  ATOS_TRY(pool_malloc_host((void**)&s.h_stats, sizeof(unsigned long long) * kNumStats * m));
   s.ninst = m;
   s.cap = cap;
   // fresh rings hold garbage: mark dirty so the next prepare fills them with EMPTY
@@ -200,10 +211,10 @@ int ensure_bsp(atos_graph_s* g, size_t bytes) {
   }
   if (g->bsp_bytes >= bytes) return ATOS_OK;
   cudaDeviceSynchronize();
-  cudaFree(g->d_bsp);
+  pool_free(g->d_bsp);
   g->d_bsp = nullptr;
   g->bsp_bytes = 0;
-  ATOS_TRY(cudaMalloc(&g->d_bsp, bytes));
+  ATOS_TRY(pool_malloc(&g->d_bsp, bytes));
   g->bsp_bytes = bytes;
   return ATOS_OK;
 }
@@ -507,9 +518,10 @@ int atos_graph_create(const int32_t* row_ptr, const int32_t* col, int32_t n, int
 int atos_graph_destroy(atos_graph_t g) {
   if (!g) return ATOS_OK;
   cudaDeviceSynchronize();
-  if (g->owned) cudaFree(g->row_ptr), cudaFree(g->col);
-  cudaFree(g->d_res), cudaFree(g->d_qbits), cudaFree(g->d_bsp), cudaFree(g->d_cert);
-  cudaFree(g->sp_row_ptr), cudaFree(g->sp_col), cudaFree(g->sp_out);
+  if (g->owned) pool_free(g->row_ptr), pool_free(g->col);
+  pool_free(g->d_res), pool_free(g->d_qbits), pool_free(g->d_bsp), pool_free(g->d_cert);
+  pool_free(g->sp_row_ptr), pool_free(g->sp_col), pool_free(g->sp_out), pool_free(g->sp_perm), pool_free(g->sp_bsums);
+  if (g->sp_ready) cudaEventDestroy(g->sp_ready);
   g->s.release();
   delete g;
   return ATOS_OK;

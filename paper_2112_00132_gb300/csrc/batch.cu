@@ -202,11 +202,11 @@ struct atos_batch_s {
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
-    cudaFree(d_insts), cudaFree(d_qctl), cudaFree(d_ring), cudaFree(d_stats), cudaFreeHost(h_stats);
-    cudaFree(d_ctl), cudaFreeHost(h_ctl), cudaFree(d_res), cudaFree(d_qbits), cudaFree(d_results);
-    cudaFree(d_pr_idx), cudaFree(d_cert_y), cudaFree(d_cert), cudaFreeHost(h_cert);
-    cudaFree(d_sp_out), cudaFree(d_jobs);
-    cudaFreeHost(h_results);
+    pool_free(d_insts), pool_free(d_qctl), pool_free(d_ring), pool_free(d_stats), pool_free_host(h_stats);
+    pool_free(d_ctl), pool_free_host(h_ctl), pool_free(d_res), pool_free(d_qbits), pool_free(d_results);
+    pool_free(d_pr_idx), pool_free(d_cert_y), pool_free(d_cert), pool_free_host(h_cert);
+    pool_free(d_sp_out), pool_free(d_jobs);
+    pool_free_host(h_results);
   }
 };
 
@@ -346,15 +346,15 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
     }
     footprint += (inst[i].app == ATOS_APP_PAGERANK ? 8.0 : 4.0) * n;
   }
-  if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_insts, sizeof(Instance) * ninst));
-  if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_qctl, sizeof(QueueCtl) * ninst));
-  if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_ring, sizeof(unsigned long long) * ring_total));
-  if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_stats, sizeof(unsigned long long) * kNumStats * ninst));
-  if (!rc) rc = cuda_rc(cudaMallocHost((void**)&b->h_stats, sizeof(unsigned long long) * kNumStats * ninst));
-  if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_ctl, sizeof(DevCtl)));
-  if (!rc) rc = cuda_rc(cudaMallocHost((void**)&b->h_ctl, sizeof(DevCtl)));
-  if (!rc && res_total) rc = cuda_rc(cudaMalloc((void**)&b->d_res, sizeof(float) * res_total));
-  if (!rc && bits_total) rc = cuda_rc(cudaMalloc((void**)&b->d_qbits, sizeof(uint32_t) * bits_total));
+  if (!rc) rc = cuda_rc(pool_malloc((void**)&b->d_insts, sizeof(Instance) * ninst));
+  if (!rc) rc = cuda_rc(pool_malloc((void**)&b->d_qctl, sizeof(QueueCtl) * ninst));
+  if (!rc) rc = cuda_rc(pool_malloc((void**)&b->d_ring, sizeof(unsigned long long) * ring_total));
+  if (!rc) rc = cuda_rc(pool_malloc((void**)&b->d_stats, sizeof(unsigned long long) * kNumStats * ninst));
+  if (!rc) rc = cuda_rc(pool_malloc_host((void**)&b->h_stats, sizeof(unsigned long long) * kNumStats * ninst));
+  if (!rc) rc = cuda_rc(pool_malloc((void**)&b->d_ctl, sizeof(DevCtl)));
+  if (!rc) rc = cuda_rc(pool_malloc_host((void**)&b->h_ctl, sizeof(DevCtl)));
+  if (!rc && res_total) rc = cuda_rc(pool_malloc((void**)&b->d_res, sizeof(float) * res_total));
+  if (!rc && bits_total) rc = cuda_rc(pool_malloc((void**)&b->d_qbits, sizeof(uint32_t) * bits_total));
   const bool spread = (cfg.flags & ATOS_FLAG_SPREAD_IDS) != 0;
   std::vector<uint64_t> sp_off(ninst, 0);
   uint64_t sp_total = 0;
@@ -366,16 +366,16 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
         b->njobs++;
         b->max_n_jobs = std::max(b->max_n_jobs, gn[inst[i].graph]);
       }
-  if (!rc && sp_total) rc = cuda_rc(cudaMalloc((void**)&b->d_sp_out, sizeof(int32_t) * sp_total));
-  if (!rc && b->njobs) rc = cuda_rc(cudaMalloc((void**)&b->d_jobs, sizeof(SpreadJob) * b->njobs));
+  if (!rc && sp_total) rc = cuda_rc(pool_malloc((void**)&b->d_sp_out, sizeof(int32_t) * sp_total));
+  if (!rc && b->njobs) rc = cuda_rc(pool_malloc((void**)&b->d_jobs, sizeof(SpreadJob) * b->njobs));
   if (!rc && b->n_pr) {
-    rc = cuda_rc(cudaMalloc((void**)&b->d_cert_y, sizeof(double) * res_total));  // same row offsets as res
-    if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_pr_idx, sizeof(int) * b->n_pr));
-    if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_cert, sizeof(double) * b->n_pr));
-    if (!rc) rc = cuda_rc(cudaMallocHost((void**)&b->h_cert, sizeof(double) * b->n_pr));
+    rc = cuda_rc(pool_malloc((void**)&b->d_cert_y, sizeof(double) * res_total));  // same row offsets as res
+    if (!rc) rc = cuda_rc(pool_malloc((void**)&b->d_pr_idx, sizeof(int) * b->n_pr));
+    if (!rc) rc = cuda_rc(pool_malloc((void**)&b->d_cert, sizeof(double) * b->n_pr));
+    if (!rc) rc = cuda_rc(pool_malloc_host((void**)&b->h_cert, sizeof(double) * b->n_pr));
   }
-  if (!rc) rc = cuda_rc(cudaMalloc((void**)&b->d_results, sizeof(InstResult) * ninst));
-  if (!rc) rc = cuda_rc(cudaMallocHost((void**)&b->h_results, sizeof(InstResult) * ninst));
+  if (!rc) rc = cuda_rc(pool_malloc((void**)&b->d_results, sizeof(InstResult) * ninst));
+  if (!rc) rc = cuda_rc(pool_malloc_host((void**)&b->h_results, sizeof(InstResult) * ninst));
   if (!rc) rc = cuda_rc(cudaEventCreate(&b->ev0));
   if (!rc) rc = cuda_rc(cudaEventCreate(&b->ev1));
   if (rc) {

@@ -47,6 +47,13 @@ inline int resident_blocks(const void* fn, int threads) {
   return per_sm * sms;
 }
 
+// The library's caching allocator (pool.cu): blocks are reused by later requests of the same size
+// class instead of going back to the driver.  Free only blocks the device no longer uses.
+cudaError_t pool_malloc(void** p, size_t bytes);
+cudaError_t pool_malloc_host(void** p, size_t bytes);
+void pool_free(void* p);
+void pool_free_host(void* p);
+
 // Kernels this library has launched (all launch sites add to it; read by atos_kernel_launches).
 void count_launches(unsigned n);
 void uncount_launches(unsigned n);  // launches recorded into a CUDA graph, not run

@@ -27,22 +27,27 @@ __device__ __forceinline__ int32_t spread_id(uint32_t v, uint64_t a, uint64_t c,
   return (int32_t)((a * v + c) % n);
 }
 
-__global__ void spread_degrees_kernel(const int32_t* __restrict__ rp, int32_t n, uint64_t a, uint64_t c,
-                                      int32_t* __restrict__ new_rp) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    new_rp[spread_id((uint32_t)v, a, c, (uint32_t)n)] = __ldg(rp + v + 1) - __ldg(rp + v);
+// perm[v] = pi(v) for every v (the one place the 64-bit product and remainder are computed), and
+// the degrees of the copy's rows.
+__global__ void spread_perm_kernel(const int32_t* __restrict__ rp, int32_t n, uint64_t a, uint64_t c,
+                                   int32_t* __restrict__ perm, int32_t* __restrict__ new_rp) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t p = spread_id((uint32_t)v, a, c, (uint32_t)n);
+    perm[v] = p;
+    new_rp[p] = __ldg(rp + v + 1) - __ldg(rp + v);
+  }
 }
 
-// One warp per row of the original graph; lanes stride the row.
+// One warp per row of the original graph; lanes stride the row and rename through perm.
 __global__ void spread_cols_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, int32_t n,
-                                   uint64_t a, uint64_t c, const int32_t* __restrict__ new_rp,
+                                   const int32_t* __restrict__ perm, const int32_t* __restrict__ new_rp,
                                    int32_t* __restrict__ new_col) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     const int s = __ldg(rp + v), e = __ldg(rp + v + 1);
-    const int d = __ldg(new_rp + spread_id((uint32_t)v, a, c, (uint32_t)n));
-    for (int k = s + lane; k < e; k += 32) new_col[d + (k - s)] = spread_id((uint32_t)__ldg(col + k), a, c, (uint32_t)n);
+    const int d = __ldg(new_rp + __ldg(perm + v));
+    for (int k = s + lane; k < e; k += 32) new_col[d + (k - s)] = __ldg(perm + __ldg(col + k));
   }
 }
 
@@ -68,17 +73,17 @@ uint64_t spread_multiplier(int32_t n) {
   return a % (uint64_t)n;
 }
 
-// Builds the spread copy: new_rp (n + 1 entries) and new_col (nnz entries); bsums needs
-// n / 1024 + 2 entries of scratch.
-cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, uint64_t a, uint64_t c, int32_t* new_rp,
-                         int32_t* new_col, int32_t* bsums, cudaStream_t s) {
+// Builds the spread copy: perm (n entries, v -> pi(v)), new_rp (n + 1 entries) and new_col (nnz
+// entries); bsums needs n / 1024 + 2 entries of scratch.
+cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, uint64_t a, uint64_t c, int32_t* perm,
+                         int32_t* new_rp, int32_t* new_col, int32_t* bsums, cudaStream_t s) {
   count_launches(2);
-  spread_degrees_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(rp, n, a, c, new_rp);
+  spread_perm_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(rp, n, a, c, perm, new_rp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = bsp::scan_inplace(new_rp, n, bsums, s);  // exclusive scan; new_rp[n] = nnz
   if (e != cudaSuccess) return e;
-  spread_cols_kernel<<<grid_for((int64_t)n * 32, 256, 8192), 256, 0, s>>>(rp, col, n, a, c, new_rp, new_col);
+  spread_cols_kernel<<<grid_for((int64_t)n * 32, 256, 8192), 256, 0, s>>>(rp, col, n, perm, new_rp, new_col);
   return cudaGetLastError();
 }
 

@@ -190,12 +190,12 @@ struct atos_server_s {
 
   ~atos_server_s() {
     cudaDeviceSynchronize();
-    cudaFree(d_arena), cudaFree(d_slots), cudaFreeHost(h_slots), cudaFree(d_active), cudaFreeHost(h_active);
-    cudaFree(d_qctl);
-    cudaFree(d_stats), cudaFreeHost(h_stats), cudaFree(d_ctl), cudaFreeHost(h_ctl), cudaFree(d_fin);
-    cudaFreeHost(h_fin), cudaFree(d_results), cudaFreeHost(h_results);
-    cudaFree(d_cert_idx), cudaFreeHost(h_cert_idx), cudaFree(d_cert), cudaFreeHost(h_cert);
-    cudaFree(d_jobs), cudaFreeHost(h_jobs);
+    pool_free(d_arena), pool_free(d_slots), pool_free_host(h_slots), pool_free(d_active), pool_free_host(h_active);
+    pool_free(d_qctl);
+    pool_free(d_stats), pool_free_host(h_stats), pool_free(d_ctl), pool_free_host(h_ctl), pool_free(d_fin);
+    pool_free_host(h_fin), pool_free(d_results), pool_free_host(h_results);
+    pool_free(d_cert_idx), pool_free_host(h_cert_idx), pool_free(d_cert), pool_free_host(h_cert);
+    pool_free(d_jobs), pool_free_host(h_jobs);
     if (stream) cudaStreamDestroy(stream);
   }
 };
@@ -268,26 +268,26 @@ int atos_server_create(const atos_graph_t* graphs, int32_t ngraphs, int32_t max_
   s->orphan_cap = (uint32_t)(2 * s->nb * cfg.worker_size);
   int rc = s->nb > 0 ? ATOS_OK : ATOS_ERR_CUDA;
   if (!rc) rc = rc_of(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_arena, (size_t)budget_bytes));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_slots, sizeof(Instance) * max_slots));
-  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_slots, sizeof(Instance) * max_slots));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_active, sizeof(Instance) * max_slots));
-  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_active, sizeof(Instance) * max_slots));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_qctl, sizeof(QueueCtl) * max_slots));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_stats, sizeof(unsigned long long) * kNumStats * max_slots));
-  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_stats, sizeof(unsigned long long) * kNumStats * max_slots));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_ctl, sizeof(DevCtl)));
-  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_ctl, sizeof(DevCtl)));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_fin, sizeof(int) * max_slots));
-  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_fin, sizeof(int) * max_slots));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_results, batch_result_bytes() * max_slots));  // by active index
-  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_results, batch_result_bytes() * max_slots));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_cert_idx, sizeof(int) * max_slots));
-  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_cert_idx, sizeof(int) * max_slots));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_cert, sizeof(double) * max_slots));
-  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_cert, sizeof(double) * max_slots));
-  if (!rc) rc = rc_of(cudaMalloc((void**)&s->d_jobs, sizeof(SpreadJob) * max_slots));
-  if (!rc) rc = rc_of(cudaMallocHost((void**)&s->h_jobs, sizeof(SpreadJob) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_arena, (size_t)budget_bytes));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_slots, sizeof(Instance) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc_host((void**)&s->h_slots, sizeof(Instance) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_active, sizeof(Instance) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc_host((void**)&s->h_active, sizeof(Instance) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_qctl, sizeof(QueueCtl) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_stats, sizeof(unsigned long long) * kNumStats * max_slots));
+  if (!rc) rc = rc_of(pool_malloc_host((void**)&s->h_stats, sizeof(unsigned long long) * kNumStats * max_slots));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_ctl, sizeof(DevCtl)));
+  if (!rc) rc = rc_of(pool_malloc_host((void**)&s->h_ctl, sizeof(DevCtl)));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_fin, sizeof(int) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc_host((void**)&s->h_fin, sizeof(int) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_results, batch_result_bytes() * max_slots));  // by active index
+  if (!rc) rc = rc_of(pool_malloc_host((void**)&s->h_results, batch_result_bytes() * max_slots));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_cert_idx, sizeof(int) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc_host((void**)&s->h_cert_idx, sizeof(int) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_cert, sizeof(double) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc_host((void**)&s->h_cert, sizeof(double) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc((void**)&s->d_jobs, sizeof(SpreadJob) * max_slots));
+  if (!rc) rc = rc_of(pool_malloc_host((void**)&s->h_jobs, sizeof(SpreadJob) * max_slots));
   if (!rc) rc = rc_of(cudaMemsetAsync(s->d_ctl, 0, sizeof(DevCtl), s->stream));
   if (rc) {
     delete s;

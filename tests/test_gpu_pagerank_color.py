@@ -251,3 +251,24 @@ def test_spread_ids_full_size_rmat22(atos):
     assert st.status == 0 and bound <= PR_L1_TOL and st.error_bound <= PR_L1_TOL
     code, bad, kk = oracle.check_coloring(g, colors.cpu().numpy())
     assert st_c.status == 0 and code == 0 and k == kk
+
+
+def test_recreated_graphs_reuse_pooled_memory(atos):
+    """Graph objects created and destroyed in a loop (the end-to-end pattern) reuse the library's
+    cached blocks; results stay right, and trimming returns the cache to the driver."""
+    import ctypes
+    g = gg.rmat(12, 16, seed=1)
+    ref = pr_reference(g)
+    flags = atos.FLAG_SPREAD_IDS
+    for rep in range(3):
+        with atos.Graph.from_csr(g) as G:
+            rank, st = G.pagerank(ALPHA, EPS, cfg=atos.queue_config(flags=flags))
+            assert np.abs(rank.cpu().numpy() - ref).sum() <= PR_L1_TOL, f"rep {rep}"
+            colors, k, _ = G.color(cfg=atos.queue_config(flags=flags))
+            assert oracle.check_coloring(g, colors.cpu().numpy())[0] == 0
+            d, _ = G.bfs([0])
+            assert np.array_equal(d.cpu().numpy()[0], oracle.bfs(g, 0))
+    cached = ctypes.c_int64(-1)
+    assert atos.abi.lib().atos_pool_trim(ctypes.byref(cached)) == 0
+    assert cached.value > 0
+    assert atos.abi.lib().atos_pool_trim(ctypes.byref(cached)) == 0 and cached.value == 0
