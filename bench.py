@@ -370,6 +370,11 @@ def run_atos(args, rank: int, world: int):
         comparisons["pagerank_bsp_ms"] = round(timed(lambda: G.pagerank(ALPHA, EPS, rank_t, cfg=bsp, stream=stream,
                                                                          stats=False)), 3)
         comparisons["color_bsp_ms"] = round(timed(lambda: G.color(colors, cfg=bsp, stream=stream, stats=False)), 3)
+        # the quality option: assigns avoid only smaller neighbours' colours (ATOS_FLAG_GC_ORDERED)
+        ordered = atos.queue_config(worker_size=512, fetch_size=512, flags=atos.FLAG_GC_ORDERED)
+        _, k_ord, st_ord = G.color(colors, cfg=ordered, stream=stream)
+        comparisons["color_ordered"] = {"ms": round(st_ord.ms, 3), "colors": int(k_ord),
+                                        "tasks_per_vertex": round(st_ord.tasks / g.n, 3)}
         comparisons["step_bsp_ms"] = round(comparisons["bfs64_bsp_ms"] + comparisons["pagerank_bsp_ms"]
                                            + comparisons["color_bsp_ms"], 3)
         comparisons["bfs64_batched_ms"] = round(mean(bfs_ms), 3)

@@ -81,6 +81,13 @@ extern "C" {
                                      cached by atos_autotune for the graph's class (all fields),
                                      or this one without the flag when the class is not tuned */
 
+#define ATOS_FLAG_GC_ORDERED 16u   /* colouring: an assign task avoids only the colours of the vertex's
+                                     smaller-id neighbours (in the ids the run uses); the check tasks
+                                     are unchanged, so a conflict with a larger neighbour still makes
+                                     that neighbour recolour.  The result stays proper and follows
+                                     first fit in id order closely: fewer colours on scale-free
+                                     graphs (Algorithm 6's assign considers every neighbour) */
+
 typedef struct atos_config {
   int32_t worker_size;    /* 32 (warp worker) or a CTA worker of 64, 128, 256, 512 or 1024 threads */
   int32_t fetch_size;     /* tasks per pop, 1..1024; at most worker_size for CTA workers (FETCH_SIZE

@@ -243,7 +243,8 @@ int check_config(const atos_config& c) {
   if (c.fetch_policy < ATOS_FETCH_FIXED || c.fetch_policy > ATOS_FETCH_SPREAD) return ATOS_ERR_INVALID_ARG;
   if (c.num_blocks < 0 || c.check_size < 0 || c.window < 0 || c.queue_capacity < 0 || c.spin_limit_ns < 0)
     return ATOS_ERR_INVALID_ARG;
-  if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS | ATOS_FLAG_USE_TUNED))
+  if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS | ATOS_FLAG_USE_TUNED |
+                  ATOS_FLAG_GC_ORDERED))
     return ATOS_ERR_INVALID_ARG;
   return ATOS_OK;
 }
@@ -739,6 +740,7 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   }
   Instance I = base_instance(g, 0, kAppGc, cap, (uint32_t)n, -1);
   I.color = spread ? (int32_t*)g->sp_out : colors;
+  I.gc_ordered = (cfg.flags & ATOS_FLAG_GC_ORDERED) ? 1 : 0;
   if (spread) I.row_ptr = g->sp_row_ptr, I.col = g->sp_col;
   I.qbits = g->d_qbits;
   g->s.h_insts[0] = I;

@@ -441,6 +441,7 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
       I.prefix_len = (uint32_t)I.n;
       I.prefix_item = -1;
       I.color = job.src ? (int32_t*)job.src : (int32_t*)q.out;
+      I.gc_ordered = (cfg.flags & ATOS_FLAG_GC_ORDERED) ? 1 : 0;
       I.qbits = b->d_qbits + bits_off[i];
     }
     b->h_insts[i] = I;

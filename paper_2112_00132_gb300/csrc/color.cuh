@@ -95,7 +95,8 @@ struct GcBody {
             const int item = sm.aux[i];
             if (item >= 0) {
               const int rel = c[j] - base;
-              if (rel >= 0 && rel < kGcWindow) atomicOr(&sm.x.bits[2 * i + (rel >> 5)], 1u << (rel & 31));
+              if (rel >= 0 && rel < kGcWindow && (!I.gc_ordered || nb[j] < item))
+                atomicOr(&sm.x.bits[2 * i + (rel >> 5)], 1u << (rel & 31));
             } else if (c[j] == (int)sm.x.bits[2 * i] && nb[j] != ~item) {
               if (nb[j] < ~item) sm.x.bits[2 * i + 1] = 1u;   // v is the larger: v recolours
               else push_nb = gc_claim_assign(I, nb[j]);       // the neighbour is the larger
@@ -165,7 +166,9 @@ struct GcBody {
       for (int base = 0; colour < 0; base += kGcWindow) {
         unsigned lo = 0, hi = 0;
         for (int k = s + lane; k < e; k += 32) {
-          const int rel = __ldcg(I.color + ldg(I.col + k)) - base;
+          const int u = ldg(I.col + k);
+          if (I.gc_ordered && u > v) continue;
+          const int rel = __ldcg(I.color + u) - base;
           if (rel >= 0 && rel < 32) lo |= 1u << rel;
           else if (rel >= 32 && rel < 64) hi |= 1u << (rel - 32);
         }

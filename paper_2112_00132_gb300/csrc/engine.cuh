@@ -79,7 +79,7 @@ struct Instance {
   unsigned long long* stats;  // kNumStats counters
   unsigned* orphans[2];  // serving: pending tickets recorded at a pause, by epoch parity
   uint32_t orphan_cap;
-  int32_t _pad2;
+  int32_t gc_ordered;    // colouring: 1 = an assign avoids only the colours of smaller-id neighbours
   double* cert_y;        // PageRank in batches and serving: FP64 scratch (n) of the output certificate
   double exact_sum;      // PageRank: n - alpha * (isolated vertices), the fixed point's sum
 };

@@ -381,6 +381,7 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
     I.prefix_len = (uint32_t)n;
     I.prefix_item = -1;
     I.color = job.src ? (int32_t*)job.src : (int32_t*)q->out;
+    I.gc_ordered = (s->cfg.flags & ATOS_FLAG_GC_ORDERED) ? 1 : 0;
     I.qbits = (uint32_t*)take((size_t)(n + 31) / 32 * 4);
   }
   sl.state = kActive;
