@@ -349,17 +349,20 @@ def run_atos(args, rank: int, world: int):
             torch.cuda.synchronize()
             return a.elapsed_time(b)
         bsp = atos.queue_config("bsp")
+        # the BSP PageRank and colouring on the same layout as the persistent runs
+        bsp_pr = atos.queue_config("bsp", flags=cfg_pr.flags & atos.FLAG_SPREAD_IDS)
+        bsp_gc = atos.queue_config("bsp", flags=cfg_gc.flags & atos.FLAG_SPREAD_IDS)
         comparisons["bfs64_bsp_ms"] = round(timed(lambda: G.bfs(srcs, depths, cfg=bsp, stream=stream,
                                                                   stats=False)), 3)
         # work of the level-synchronous forms (neighbour entries read), for the workload ratio
         # of Table 4: persistent work / BSP work
         _, bsp_bfs = G.bfs(srcs, depths, cfg=bsp, stream=stream)
-        _, bsp_pr = G.pagerank(ALPHA, EPS, rank_t, cfg=bsp, stream=stream)
-        _, _, bsp_gc = G.color(colors, cfg=bsp, stream=stream)
+        _, bsp_pr_st = G.pagerank(ALPHA, EPS, rank_t, cfg=bsp_pr, stream=stream)
+        _, _, bsp_gc_st = G.color(colors, cfg=bsp_gc, stream=stream)
         comparisons["workload_ratio"] = {
             "bfs": round(bfs_stats.edges / max(1, bsp_bfs.edges), 3),
-            "pagerank": round(pr_edges / max(1, bsp_pr.edges), 3),
-            "color": round(gc_edges / max(1, bsp_gc.edges), 3),
+            "pagerank": round(pr_edges / max(1, bsp_pr_st.edges), 3),
+            "color": round(gc_edges / max(1, bsp_gc_st.edges), 3),
             "note": "neighbour entries read by the persistent path / by the BSP path (Table 4's ratio)"}
         one = torch.empty((1, g.n), dtype=torch.int32, device="cuda")
 
@@ -367,9 +370,11 @@ def run_atos(args, rank: int, world: int):
             for s0 in srcs:
                 G.bfs([int(s0)], one, cfg=cfg_bfs, stream=stream, stats=False)
         comparisons["bfs64_unbatched_ms"] = round(timed(unbatched), 3)
-        comparisons["pagerank_bsp_ms"] = round(timed(lambda: G.pagerank(ALPHA, EPS, rank_t, cfg=bsp, stream=stream,
+        comparisons["pagerank_bsp_ms"] = round(timed(lambda: G.pagerank(ALPHA, EPS, rank_t, cfg=bsp_pr, stream=stream,
                                                                          stats=False)), 3)
-        comparisons["color_bsp_ms"] = round(timed(lambda: G.color(colors, cfg=bsp, stream=stream, stats=False)), 3)
+        comparisons["color_bsp_ms"] = round(timed(lambda: G.color(colors, cfg=bsp_gc, stream=stream, stats=False)), 3)
+        comparisons["bsp_layout"] = {"pagerank": "spread" if bsp_pr.flags else "input",
+                                     "color": "spread" if bsp_gc.flags else "input"}
         # the quality option: assigns avoid only smaller neighbours' colours (ATOS_FLAG_GC_ORDERED)
         ordered = atos.queue_config(worker_size=512, fetch_size=512, flags=atos.FLAG_GC_ORDERED)
         _, k_ord, st_ord = G.color(colors, cfg=ordered, stream=stream)

@@ -75,7 +75,8 @@ extern "C" {
                                      hubs, so a warp's 32 state updates land in a few L2 slices;
                                      spread ids balance them over the slices.  Results come back in
                                      the caller's ids (one gather).  Batches and servers apply it to
-                                     their PageRank and colouring instances; BFS and BSP ignore it. */
+                                     their PageRank and colouring instances, and the BSP strategy to
+                                     its PageRank and colouring; BFS ignores it. */
 
 #define ATOS_FLAG_USE_TUNED 8u     /* atos_bfs / atos_pagerank / atos_color use the configuration
                                      cached by atos_autotune for the graph's class (all fields),

@@ -629,7 +629,7 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   if (rc) return rc;
   if (!g->d_res) ATOS_TRY(dev_alloc(&g->d_res, (size_t)n));
   if (!g->d_qbits) ATOS_TRY(dev_alloc(&g->d_qbits, (size_t)(n + 31) / 32));
-  const bool spread = (cfg.flags & ATOS_FLAG_SPREAD_IDS) && !bsp;
+  const bool spread = (cfg.flags & ATOS_FLAG_SPREAD_IDS) != 0;
   if (spread) {
     rc = ensure_spread(g, st);
     if (rc) return rc;
@@ -654,7 +654,7 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
     if (rc) return rc;
     ATOS_TRY(launch_prepare(g->s.d_insts, 1, n, g->s.d_ctl, 0u, 1u, st));
     ATOS_TRY(launch_pr_init(g->s.d_insts, 1, g->nnz, st));
-    rc = bsp_pagerank(g->row_ptr, g->col, n, alpha, eps, rank, g->d_res, g->d_bsp, g->bsp_bytes,
+    rc = bsp_pagerank(I.row_ptr, I.col, n, alpha, eps, I.rank, g->d_res, g->d_bsp, g->bsp_bytes,
                       (int32_t*)&g->s.h_ctl->maxgen, st, &iters, &bsp_edges, &bsp_tasks);
     if (rc) return rc;
   } else {
@@ -699,16 +699,23 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   if (cfg.strategy == ATOS_BSP) {
     rc = ensure_bsp(g, bsp_bytes_for(n));
     if (rc) return rc;
+    const bool spread_bsp = (cfg.flags & ATOS_FLAG_SPREAD_IDS) != 0;
+    if (spread_bsp) {
+      rc = ensure_spread(g, st);
+      if (rc) return rc;
+    }
+    int32_t* out = spread_bsp ? (int32_t*)g->sp_out : colors;
     ATOS_TRY(cudaEventRecord(g->s.ev0, st));
     int64_t iters = 0, edges = 0, tasks = 0;
-    rc = bsp_color(g->row_ptr, g->col, n, colors, g->d_bsp, g->bsp_bytes, (int32_t*)&g->s.h_ctl->maxgen, st, &iters,
-                   &edges, &tasks);
+    rc = bsp_color(spread_bsp ? g->sp_row_ptr : g->row_ptr, spread_bsp ? g->sp_col : g->col, n, out, g->d_bsp,
+                   g->bsp_bytes, (int32_t*)&g->s.h_ctl->maxgen, st, &iters, &edges, &tasks);
     if (rc) return rc;
     Instance I;
     memset(&I, 0, sizeof(I));
     I.n = n;
-    I.color = colors;
+    I.color = out;
     ATOS_TRY(gc_finish(&I, g->s.d_ctl, st));
+    if (spread_bsp) ATOS_TRY(unspread_i32(out, colors, n, g->sp_a, g->sp_c, st));
     ATOS_TRY(cudaEventRecord(g->s.ev1, st));
     if (stats || num_colors) {
       ATOS_TRY(cudaMemcpyAsync(g->s.h_ctl, g->s.d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));

@@ -74,7 +74,7 @@ std::vector<atos_config> candidates(int app, int nsrc) {
     // the same shapes on the spread-id copy of the graph
     const size_t k = out.size();
     for (size_t i = 0; i < k; ++i)
-      if (out[i].strategy != ATOS_BSP && !(out[i].flags & ATOS_FLAG_PR_CROSSING)) {
+      if (!(out[i].flags & ATOS_FLAG_PR_CROSSING)) {
         atos_config c = out[i];
         c.flags |= ATOS_FLAG_SPREAD_IDS;
         out.push_back(c);
