@@ -64,6 +64,12 @@ std::vector<atos_config> candidates(int app, int nsrc) {
         c.check_size = cs;
         out.push_back(c);
       }
+    for (int f : {128, 256, 512})  // greedy pops at 512 threads
+      for (int cs : {8, 16}) {
+        atos_config c = make(nullptr, 512, f, ATOS_FETCH_GREEDY);
+        c.check_size = cs;
+        out.push_back(c);
+      }
     for (int w : {256, 512, 1024}) {  // threshold-crossing enqueue instead of the Check_Size scan
       atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
       c.flags |= ATOS_FLAG_PR_CROSSING;
