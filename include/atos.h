@@ -89,6 +89,14 @@ extern "C" {
                                      first fit in id order closely: fewer colours on scale-free
                                      graphs (Algorithm 6's assign considers every neighbour) */
 
+#define ATOS_FLAG_BFS_EXPAND_ONCE 32u /* BFS (atos_bfs, persistent and discrete): a vertex queued
+                                     several times is expanded once per depth.  A task first
+                                     records its depth in a per-vertex marker (atomicMin) and skips
+                                     the expansion if a copy of the vertex popped after the same
+                                     improvement already expanded it.  Removes nearly all of the
+                                     asynchronous BFS's re-expansions on scale-free graphs, at one
+                                     atomic per task (n int32 per source of scratch). */
+
 typedef struct atos_config {
   int32_t worker_size;    /* 32 (warp worker) or a CTA worker of 64, 128, 256, 512 or 1024 threads */
   int32_t fetch_size;     /* tasks per pop, 1..1024; at most worker_size for CTA workers (FETCH_SIZE

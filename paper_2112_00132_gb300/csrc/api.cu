@@ -122,6 +122,8 @@ struct atos_graph_s {
   cudaEvent_t sp_ready = nullptr;  // recorded after the build
   void* sp_out = nullptr;
   uint64_t sp_a = 1, sp_c = 0;
+  int32_t* d_expanded = nullptr;  // BFS: per source, the smallest depth each vertex was expanded at
+  size_t expanded_rows = 0;
 };
 
 namespace {
@@ -244,7 +246,7 @@ int check_config(const atos_config& c) {
   if (c.num_blocks < 0 || c.check_size < 0 || c.window < 0 || c.queue_capacity < 0 || c.spin_limit_ns < 0)
     return ATOS_ERR_INVALID_ARG;
   if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS | ATOS_FLAG_USE_TUNED |
-                  ATOS_FLAG_GC_ORDERED))
+                  ATOS_FLAG_GC_ORDERED | ATOS_FLAG_BFS_EXPAND_ONCE))
     return ATOS_ERR_INVALID_ARG;
   return ATOS_OK;
 }
@@ -522,6 +524,7 @@ int atos_graph_destroy(atos_graph_t g) {
   if (g->owned) pool_free(g->row_ptr), pool_free(g->col);
   pool_free(g->d_res), pool_free(g->d_qbits), pool_free(g->d_bsp), pool_free(g->d_cert);
   pool_free(g->sp_row_ptr), pool_free(g->sp_col), pool_free(g->sp_out), pool_free(g->sp_perm), pool_free(g->sp_bsums);
+  pool_free(g->d_expanded);
   if (g->sp_ready) cudaEventDestroy(g->sp_ready);
   g->s.release();
   delete g;
@@ -579,9 +582,19 @@ int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* dept
   if (!cap) return ATOS_ERR_INVALID_ARG;
   rc = ensure_scratch(g, nsrc, cap);
   if (rc) return rc;
+  const bool marks = (cfg.flags & ATOS_FLAG_BFS_EXPAND_ONCE) != 0;
+  if (marks && (size_t)nsrc > g->expanded_rows) {  // expansion markers, one row of n per source
+    cudaDeviceSynchronize();               // the old rows may still be in use
+    pool_free(g->d_expanded);
+    g->d_expanded = nullptr;
+    g->expanded_rows = 0;
+    ATOS_TRY(dev_alloc(&g->d_expanded, (size_t)nsrc * (size_t)n));
+    g->expanded_rows = (size_t)nsrc;
+  }
   for (int32_t i = 0; i < nsrc; ++i) {
     Instance I = base_instance(g, i, kAppBfs, cap, 1, sources[i]);
     I.depth = depths + (size_t)i * n;
+    I.expanded = marks ? g->d_expanded + (size_t)i * n : nullptr;
     g->s.h_insts[i] = I;
   }
   if (cfg.window == 0) {

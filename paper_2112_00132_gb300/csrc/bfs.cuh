@@ -42,6 +42,9 @@ struct BfsBody {
       sm.start[threadIdx.x] = s;
       sm.aux[threadIdx.x] = d + 1;
       deg = d == kUnreached ? 0 : e - s;  // a queued vertex always has a depth; never relax from INT32_MAX
+      // a vertex queued twice is expanded once per depth: a task finding it already expanded at
+      // this depth or a better one (by a copy popped after the improvement) skips the expansion
+      if (deg && I.expanded && atomicMin(I.expanded + v, d) <= d) deg = 0;
     }
     int total;
     const int off = block_exclusive_scan<BLOCK>(deg, sm.tmp, total);
@@ -88,11 +91,15 @@ struct BfsBody {
   // Warp worker: the 32 lanes stride the neighbour list of one vertex.
   __device__ static void warp_item(WarpSmem& ws, const Instance& I, int v, const Launch& L, unsigned long long* st) {
     const int lane = threadIdx.x & 31;
-    int d = 0;
-    if (lane == 0) d = ld_relaxed(I.depth + v);
+    int d = 0, skip = 0;
+    if (lane == 0) {
+      d = ld_relaxed(I.depth + v);
+      skip = d == kUnreached || (I.expanded && atomicMin(I.expanded + v, d) <= d);  // see cta_batch
+    }
     d = __shfl_sync(0xffffffffu, d, 0);  // one read, so every lane relaxes with the same depth
+    skip = __shfl_sync(0xffffffffu, skip, 0);
     const int nd = d + 1;
-    const int s = ldg(I.row_ptr + v), e = d == kUnreached ? s : ldg(I.row_ptr + v + 1);
+    const int s = ldg(I.row_ptr + v), e = skip ? s : ldg(I.row_ptr + v + 1);
     for (int k = s; k < e; k += 32) {
       const int j = k + lane;
       bool want = false;

@@ -81,6 +81,7 @@ struct Instance {
   uint32_t orphan_cap;
   int32_t gc_ordered;    // colouring: 1 = an assign avoids only the colours of smaller-id neighbours
   double* cert_y;        // PageRank in batches and serving: FP64 scratch (n) of the output certificate
+  int32_t* expanded;     // BFS (optional): the smallest depth at which each vertex has been expanded
   double exact_sum;      // PageRank: n - alpha * (isolated vertices), the fixed point's sum
 };
 

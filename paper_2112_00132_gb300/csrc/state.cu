@@ -54,6 +54,8 @@ __global__ void prepare_kernel(Instance* insts, DevCtl* ctl, uint32_t flags, uns
   switch (I.app) {
     case kAppBfs:
       for (int v = tid; v < n; v += stride) I.depth[v] = v == I.prefix_item ? 0 : kUnreached;
+      if (I.expanded)
+        for (int v = tid; v < n; v += stride) I.expanded[v] = kUnreached;
       break;
     case kAppPr: {
       const float a = I.alpha, base = (1.0f - I.alpha) * I.alpha;

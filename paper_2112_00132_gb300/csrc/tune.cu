@@ -76,6 +76,16 @@ std::vector<atos_config> candidates(int app, int nsrc) {
       out.push_back(c);
     }
   }
+  if (app == ATOS_APP_BFS) {
+    // the same shapes with expansion markers
+    const size_t k = out.size();
+    for (size_t i = 0; i < k; ++i)
+      if (out[i].strategy != ATOS_BSP) {
+        atos_config c = out[i];
+        c.flags |= ATOS_FLAG_BFS_EXPAND_ONCE;
+        out.push_back(c);
+      }
+  }
   if (app == ATOS_APP_PAGERANK || app == ATOS_APP_COLOR) {
     // the same shapes on the spread-id copy of the graph
     const size_t k = out.size();

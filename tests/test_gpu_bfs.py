@@ -119,3 +119,15 @@ def test_bfs_full_size_rmat22_64_sources(atos):
         assert np.array_equal(d[i], oracle.bfs(g, srcs[i])), f"source {srcs[i]}"
     for i in range(0, 64, 4):
         assert oracle.bfs_certificate(g, srcs[i], d[i]) == (0, -1), f"source {srcs[i]}"
+
+
+def test_bfs_expand_once_all_configs(atos):
+    """ATOS_FLAG_BFS_EXPAND_ONCE: bit-exact depths for every configuration (BSP ignores the flag)."""
+    for g in (gg.rmat(12, 16, seed=1), gg.grid(97, 61, delete_frac=0.1, seed=3), gg.rmat(11, 16, seed=7, delete_frac=0.1)):
+        srcs = bfs_sources(g)
+        ref = np.stack([oracle.bfs(g, s) for s in srcs])
+        with atos.Graph.from_csr(g) as G:
+            for cname, cfg in configs(atos).items():
+                cfg.flags |= atos.FLAG_BFS_EXPAND_ONCE
+                d, st = G.bfs(srcs, cfg=cfg)
+                assert st.status == 0 and np.array_equal(d.cpu().numpy(), ref), cname
