@@ -76,6 +76,15 @@ std::vector<atos_config> candidates(int app, int nsrc) {
       out.push_back(c);
     }
   }
+  if (app == ATOS_APP_BFS && nsrc > 1) {
+    for (int w : {256, 512})
+      for (int win : {1, 2, 4, 8, 16, 32}) {
+        if (win >= nsrc) break;
+        atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
+        c.window = win;
+        out.push_back(c);
+      }
+  }
   if (app == ATOS_APP_BFS) {
     // the same shapes with expansion markers
     const size_t k = out.size();
@@ -93,15 +102,6 @@ std::vector<atos_config> candidates(int app, int nsrc) {
       if (!(out[i].flags & ATOS_FLAG_PR_CROSSING)) {
         atos_config c = out[i];
         c.flags |= ATOS_FLAG_SPREAD_IDS;
-        out.push_back(c);
-      }
-  }
-  if (app == ATOS_APP_BFS && nsrc > 1) {
-    for (int w : {256, 512})
-      for (int win : {1, 2, 4, 8, 16, 32}) {
-        if (win >= nsrc) break;
-        atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
-        c.window = win;
         out.push_back(c);
       }
   }
