@@ -5,6 +5,8 @@
 
 namespace atos {
 
+constexpr int kMarkMinDegree = 16;  // ATOS_FLAG_BFS_EXPAND_ONCE: rows this long or longer are marked
+
 struct BfsBody {
   using Extra = NoExtra;
   static constexpr int kResidentThreads = 1536;
@@ -43,8 +45,9 @@ struct BfsBody {
       sm.aux[threadIdx.x] = d + 1;
       deg = d == kUnreached ? 0 : e - s;  // a queued vertex always has a depth; never relax from INT32_MAX
       // a vertex queued twice is expanded once per depth: a task finding it already expanded at
-      // this depth or a better one (by a copy popped after the improvement) skips the expansion
-      if (deg && I.expanded && atomicMin(I.expanded + v, d) <= d) deg = 0;
+      // this depth or a better one (by a copy popped after the improvement) skips the expansion;
+      // rows shorter than kMarkMinDegree are cheaper to re-expand than to mark
+      if (deg >= kMarkMinDegree && I.expanded && atomicMin(I.expanded + v, d) <= d) deg = 0;
     }
     int total;
     const int off = block_exclusive_scan<BLOCK>(deg, sm.tmp, total);
@@ -94,7 +97,9 @@ struct BfsBody {
     int d = 0, skip = 0;
     if (lane == 0) {
       d = ld_relaxed(I.depth + v);
-      skip = d == kUnreached || (I.expanded && atomicMin(I.expanded + v, d) <= d);  // see cta_batch
+      skip = d == kUnreached;
+      if (!skip && I.expanded && ldg(I.row_ptr + v + 1) - ldg(I.row_ptr + v) >= kMarkMinDegree)
+        skip = atomicMin(I.expanded + v, d) <= d;  // see cta_batch
     }
     d = __shfl_sync(0xffffffffu, d, 0);  // one read, so every lane relaxes with the same depth
     skip = __shfl_sync(0xffffffffu, skip, 0);
