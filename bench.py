@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use --worker / --fetch")
     ap.add_argument("--check-size", type=int, default=32, help="with --no-tune: PageRank's Check_Size")
     ap.add_argument("--flags", type=int, default=0, help="with --no-tune: atos_config.flags of PageRank and colouring")
+    ap.add_argument("--policy", type=int, default=2, help="with --no-tune: PageRank's fetch policy (0 fixed, 1 greedy, 2 spread)")
     ap.add_argument("--no-compare", action="store_true", help="skip the BSP / unbatched comparisons")
     ap.add_argument("--workload", default="rmat22", choices=["rmat22", "batched"],
                     help="rmat22: the single-graph step (default); batched: 256 graphs x (4 BFS + 1 PageRank) "
@@ -172,11 +173,12 @@ def recorded_traffic(cfg_pr):
         h.update(open(os.path.join(ROOT, "paper_2112_00132_gb300", "csrc", f), "rb").read())
     if not digest or digest[0] != h.hexdigest():
         return None
+    key = (cfg_pr.worker_size, cfg_pr.fetch_size, cfg_pr.fetch_policy, cfg_pr.check_size, cfg_pr.flags)
     for ln in lines:
         if ln.startswith("entry: "):
-            w, cs, fl, traffic = ln.split()[1:5]
-            if (int(w), int(cs), int(fl)) == (cfg_pr.worker_size, cfg_pr.check_size, cfg_pr.flags):
-                return float(traffic)
+            fields = ln.split()[1:]
+            if tuple(int(x) for x in fields[:5]) == key:
+                return float(fields[5])
     return None
 
 
@@ -214,7 +216,7 @@ def run_atos(args, rank: int, world: int):
         cfg_bfs = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch)
         cfg_gc = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch, flags=args.flags)
         cfg_pr = atos.queue_config(worker_size=args.worker, fetch_size=args.fetch, check_size=args.check_size,
-                                   flags=args.flags)
+                                   flags=args.flags, fetch_policy=args.policy)
         tune_ms = {}
     else:
         cfg_bfs, t_b = G.autotune("bfs", srcs, repeats=1, stream=stream)
