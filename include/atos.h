@@ -209,6 +209,17 @@ int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint3
  * zero.  Either pointer may be NULL. */
 int atos_debug_scratch_check(atos_graph_t g, uint64_t* set_bits, uint64_t* busy_slots);
 
+/* Throughput timeline (tracing): the persistent and discrete calls on g that follow record, per
+ * bucket of bucket_ns nanoseconds from the start of the call, the tasks and neighbour entries of
+ * the worker batches that ended in it (the last bucket takes everything later).  nbuckets = 0
+ * turns it off.  It costs two global atomics per batch while on.  The BSP strategy records nothing.
+ * Synchronises the device. */
+int atos_timeline(atos_graph_t g, int64_t bucket_ns, int32_t nbuckets);
+
+/* The timeline of the last call on g: tasks[b] and edges[b] (HOST arrays of nbuckets, the
+ * configured count; either may be NULL).  Synchronises the device. */
+int atos_timeline_read(atos_graph_t g, int64_t* tasks, int64_t* edges, int32_t nbuckets);
+
 /* Ceilings of the task bodies' edge loops on g, with no scheduler: one pass over every CSR
  * entry in order, a coalesced read of col[e] and then
  *   ATOS_CEILING_SCATTER: red.add.f32 into state[col[e]] (PageRank's residue scatter), or

@@ -160,6 +160,10 @@ def lib() -> ctypes.CDLL:
         for name in ("atos_server_create", "atos_server_submit", "atos_server_step", "atos_server_poll",
                      "atos_server_info", "atos_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
+        L.atos_timeline.argtypes = [vp, i64, i32]
+        L.atos_timeline.restype = ctypes.c_int
+        L.atos_timeline_read.argtypes = [vp, vp, vp, i32]
+        L.atos_timeline_read.restype = ctypes.c_int
         L.atos_pool_trim.argtypes = [P(i64)]
         L.atos_pool_trim.restype = ctypes.c_int
         L.atos_edge_ceiling.argtypes = [vp, i32, i32, P(ctypes.c_double), vp]
@@ -326,6 +330,20 @@ class Graph:
         _check(lib().atos_autotune(self._h, code, src.ctypes.data, src.shape[0], scratch.data_ptr(), repeats,
                                    ctypes.byref(best), ctypes.byref(ms), _stream_handle(stream)), "atos_autotune")
         return best, ms.value
+
+    def timeline(self, bucket_us: float = 0.0, nbuckets: int = 0):
+        """Records the throughput timeline of the following calls (nbuckets buckets of bucket_us
+        microseconds from each call's start); timeline() turns it off."""
+        _check(lib().atos_timeline(self._h, int(bucket_us * 1000), int(nbuckets)), "atos_timeline")
+        self._tl_buckets = int(nbuckets)
+
+    def timeline_read(self):
+        """(tasks, edges) per bucket of the last call, as int64 numpy arrays."""
+        nb = getattr(self, "_tl_buckets", 0)
+        tasks = np.zeros(nb, np.int64)
+        edges = np.zeros(nb, np.int64)
+        _check(lib().atos_timeline_read(self._h, tasks.ctypes.data, edges.ctypes.data, nb), "atos_timeline_read")
+        return tasks, edges
 
     def edge_ceiling(self, kind: str = "scatter", repeats: int = 3, stream=None, spread_ids: bool = False) -> float:
         """Device ms of one ideal pass over every CSR entry ("scatter": red.add into state[col[e]],

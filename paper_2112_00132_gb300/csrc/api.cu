@@ -124,6 +124,9 @@ struct atos_graph_s {
   uint64_t sp_a = 1, sp_c = 0;
   int32_t* d_expanded = nullptr;  // BFS: per source, the smallest depth each vertex was expanded at
   size_t expanded_rows = 0;
+  unsigned long long* d_timeline = nullptr;  // throughput timeline (atos_timeline), 2 counters per bucket
+  int64_t tl_bucket_ns = 0;
+  int32_t tl_nbuckets = 0;
 };
 
 namespace {
@@ -296,6 +299,13 @@ int run_instances(atos_graph_s* g, int ninst, int max_n, const atos_config& cfg,
   L.fail_site = &s.d_ctl->fail_site;
   int rc = upload_instances(s, ninst, st);
   if (rc) return rc;
+  if (g->d_timeline && g->tl_nbuckets > 0) {
+    ATOS_TRY(cudaMemsetAsync(g->d_timeline, 0, sizeof(unsigned long long) * 2 * g->tl_nbuckets, st));
+    L.timeline = g->d_timeline;
+    L.t_origin = &s.d_ctl->t_origin;
+    L.bucket_ns = g->tl_bucket_ns;
+    L.nbuckets = g->tl_nbuckets;
+  }
   ATOS_TRY(launch_prepare(s.d_insts, ninst, max_n, s.d_ctl, cfg.flags, (unsigned)window, st));
   if (app == kAppPr) ATOS_TRY(launch_pr_init(s.d_insts, ninst, g->nnz, st));
   int64_t iters = 0;
@@ -525,6 +535,7 @@ int atos_graph_destroy(atos_graph_t g) {
   pool_free(g->d_res), pool_free(g->d_qbits), pool_free(g->d_bsp), pool_free(g->d_cert);
   pool_free(g->sp_row_ptr), pool_free(g->sp_col), pool_free(g->sp_out), pool_free(g->sp_perm), pool_free(g->sp_bsums);
   pool_free(g->d_expanded);
+  pool_free(g->d_timeline);
   if (g->sp_ready) cudaEventDestroy(g->sp_ready);
   g->s.release();
   delete g;
@@ -782,6 +793,32 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
     out->num_colors = g->s.h_ctl->num_colors;
     if (num_colors) *num_colors = g->s.h_ctl->num_colors;
     return out->status;
+  }
+  return ATOS_OK;
+}
+
+int atos_timeline(atos_graph_t g, int64_t bucket_ns, int32_t nbuckets) {
+  if (!g || nbuckets < 0 || nbuckets > (1 << 20) || (nbuckets > 0 && bucket_ns < 1)) return ATOS_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();  // a running call may still count into the old buffer
+  pool_free(g->d_timeline);
+  g->d_timeline = nullptr;
+  g->tl_nbuckets = 0;
+  if (nbuckets == 0) return ATOS_OK;
+  ATOS_TRY(dev_alloc(&g->d_timeline, (size_t)2 * nbuckets));
+  ATOS_TRY(cudaMemset(g->d_timeline, 0, sizeof(unsigned long long) * 2 * nbuckets));
+  g->tl_bucket_ns = bucket_ns;
+  g->tl_nbuckets = nbuckets;
+  return ATOS_OK;
+}
+
+int atos_timeline_read(atos_graph_t g, int64_t* tasks, int64_t* edges, int32_t nbuckets) {
+  if (!g || nbuckets != g->tl_nbuckets || nbuckets < 1) return ATOS_ERR_INVALID_ARG;
+  std::vector<unsigned long long> h((size_t)2 * nbuckets);
+  ATOS_TRY(cudaDeviceSynchronize());
+  ATOS_TRY(cudaMemcpy(h.data(), g->d_timeline, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost));
+  for (int32_t b = 0; b < nbuckets; ++b) {
+    if (tasks) tasks[b] = (int64_t)h[2 * b];
+    if (edges) edges[b] = (int64_t)h[2 * b + 1];
   }
   return ATOS_OK;
 }

@@ -100,6 +100,12 @@ struct Launch {
   int* fail_site;           // which wait gave up first (diagnostics)
   long long slice_ns;       // serving: a worker pauses at its next safe point after this long (0 = never)
   unsigned epoch;           // serving: epoch number (its parity selects the orphan buffers)
+  // throughput timeline (optional): per bucket of bucket_ns after *t_origin, tasks and neighbour
+  // entries of the batches that ended in it (timeline[2 b], timeline[2 b + 1])
+  unsigned long long* timeline;
+  const unsigned long long* t_origin;
+  long long bucket_ns;
+  int32_t nbuckets;
 };
 
 // ------------------------------------------------------------------------------------ PTX
@@ -398,6 +404,14 @@ __device__ __forceinline__ void lbs_round(const S& sm, const int32_t* __restrict
   }
 }
 
+// Adds a finished batch to the throughput timeline (one thread per worker).
+__device__ __forceinline__ void timeline_add(const Launch& L, unsigned long long tasks, unsigned long long edges) {
+  const long long dt = (long long)(globaltimer() - *L.t_origin);
+  int b = dt < 0 ? 0 : (int)min(dt / L.bucket_ns, (long long)L.nbuckets - 1);
+  atomicAdd(L.timeline + 2 * b, tasks);
+  atomicAdd(L.timeline + 2 * b + 1, edges);
+}
+
 // After a batch: stop if the launch failed or this worker has outlived the launch budget.
 __device__ __forceinline__ bool must_stop(const Launch& L, unsigned long long t0) {
   if (ld_relaxed(L.status) != 0) return true;
@@ -529,8 +543,10 @@ __device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const 
       if (got) sm.items[pos] = item;
       const int still = __syncthreads_count(pending);
       if (total > 0) {
-        if (threadIdx.x == 0) st[kStatBatches]++;
+        unsigned long long edges0 = 0;
+        if (threadIdx.x == 0) st[kStatBatches]++, edges0 = st[kStatEdges];
         Body::template cta_batch<BLOCK>(sm, total, L, st);
+        if (threadIdx.x == 0 && L.timeline) timeline_add(L, (unsigned long long)total, st[kStatEdges] - edges0);
         wait.reset();
         if (threadIdx.x == 0) sm.flag = must_stop(L, t0) ? 1 : (slice_over(L, t0) ? 2 : 0);
         __syncthreads();
@@ -631,6 +647,7 @@ __global__ void __launch_bounds__(BLOCK) cta_discrete_kernel(Launch L) {
   if (item != kEmpty) sm.items[pos] = item;
   __syncthreads();
   if (cnt > 0) Body::template cta_batch<BLOCK>(sm, cnt, L, st);
+  if (threadIdx.x == 0 && cnt > 0 && L.timeline) timeline_add(L, (unsigned long long)cnt, st[kStatEdges]);
   if (threadIdx.x == 0) st[kStatBatches] += cnt > 0, flush_stats(I, st);
 }
 
@@ -711,6 +728,7 @@ __device__ void warp_run_instance(WarpSmem& ws, const Instance& I, const Launch&
       const unsigned still = __ballot_sync(0xffffffffu, pending);
       if (got) {
         const int cnt = __popc(got);
+        const unsigned long long edges0 = st[kStatEdges];
         while (got) {
           const int src = __ffs(got) - 1;
           got &= got - 1;
@@ -718,6 +736,7 @@ __device__ void warp_run_instance(WarpSmem& ws, const Instance& I, const Launch&
           Body::warp_item(ws, I, it, L, st);
         }
         if (lane == 0) st[kStatTasks] += cnt, st[kStatBatches]++;
+        if (lane == 0 && L.timeline) timeline_add(L, (unsigned long long)cnt, st[kStatEdges] - edges0);
         warp_flush(ws, I, cnt, L, st);
         wait.reset();
         int stop = 0;
@@ -796,6 +815,7 @@ __global__ void __launch_bounds__(kWarpBlock) warp_discrete_kernel(Launch L) {
     Body::warp_item(ws, I, __shfl_sync(0xffffffffu, item, src), L, st);
   }
   if (lane == 0) st[kStatTasks] += cnt, st[kStatBatches] += cnt > 0;
+  if (lane == 0 && cnt > 0 && L.timeline) timeline_add(L, (unsigned long long)cnt, st[kStatEdges]);
   warp_flush(ws, I, cnt, L, st);
   if (lane == 0) flush_stats(I, st);
 }

@@ -28,6 +28,7 @@ __global__ void prepare_kernel(Instance* insts, DevCtl* ctl, uint32_t flags, uns
   const int stride = gridDim.x * blockDim.x;
   if (ctl->dirty)
     for (uint32_t k = tid; k < I.cap; k += stride) I.ring[k] = kFreeSlot;
+  if (tid == 0 && blockIdx.y == 0) ctl->t_origin = globaltimer();
   if (tid == 0) {
     QueueCtl* c = I.ctl;
     const unsigned phantom = (flags & ATOS_FLAG_PHANTOM_TASK) ? 1u : 0u;

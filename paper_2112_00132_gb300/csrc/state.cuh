@@ -20,7 +20,7 @@ struct alignas(128) DevCtl {
   double sum_rank;     // PageRank: FP64 sum of the ranks
   double sum_res;      // PageRank: FP64 sum of the residues left
   double cert_l1;      // PageRank: FP64 ||(1 - alpha) 1 + alpha P x - x||_1 on the exact scale
-  double pad2[1];
+  unsigned long long t_origin;  // %globaltimer when the run's state was prepared (timeline origin)
 };
 
 cudaError_t launch_prepare(Instance* d_insts, int ninst, int max_n, DevCtl* d_ctl, uint32_t flags, unsigned window,

@@ -290,3 +290,20 @@ def test_color_ordered_all_configs(atos, graphs, gname):
                 assert st.status == 0 and code == 0 and k == kk, f"{gname}/{cname}/{extra}: code {code} vertex {bad}"
                 if gname == "rmat12" and not extra and cname != "bsp":
                     assert k <= greedy + 4, f"{cname}: {k} colours, serial greedy {greedy}"
+
+
+def test_throughput_timeline(atos):
+    """atos_timeline: the per-bucket tasks and neighbour entries of a run add up to its counters,
+    for the persistent and the discrete strategy; turning it off stops the recording."""
+    g = gg.rmat(12, 16, seed=1)
+    with atos.Graph.from_csr(g) as G:
+        G.timeline(bucket_us=50.0, nbuckets=64)
+        for cfg in (atos.queue_config(), atos.queue_config("discrete-cta"), atos.queue_config("persist-warp")):
+            _, st = G.pagerank(ALPHA, EPS, cfg=cfg)
+            tasks, edges = G.timeline_read()
+            assert tasks.sum() == st.tasks and edges.sum() == st.edges and tasks.sum() > 0
+            _, st = G.bfs([0, 1], cfg=cfg)
+            tasks, edges = G.timeline_read()
+            assert tasks.sum() == st.tasks and edges.sum() == st.edges
+        G.timeline()
+        G.pagerank(ALPHA, EPS)
