@@ -310,6 +310,16 @@ def run_atos(args, rank: int, world: int):
                 "algorithmic_bytes": dom_bytes, "launch_ms": round(dom_ms, 3)}
     # the edge-loop ceilings on this graph (library probe, no scheduler): the rate the bodies'
     # inner loops could reach; the kernels are bound by L2 atomics and gather latency, not HBM
+    # throughput over one PageRank run (the paper's throughput-vs-time view), outside the timed steps
+    nb = 24
+    bucket_us = max(1.0, mean(pr_ms) * 1e3 / (nb - 4))
+    G.timeline(bucket_us=bucket_us, nbuckets=nb)
+    G.pagerank(ALPHA, EPS, rank_t, cfg=cfg_pr, stream=stream, stats=False)
+    tl_tasks, tl_edges = G.timeline_read()
+    G.timeline()
+    pagerank_timeline = {"bucket_ms": round(bucket_us / 1e3, 3),
+                         "g_edge_pushes_per_s": [round(float(e) / (bucket_us * 1e-6) / 1e9, 1) for e in tl_edges],
+                         "tasks": [int(t) for t in tl_tasks]}
     # each on the layout the application ran on (spread ids when its configuration says so)
     def ceiling(kind, spread):
         return g.nnz / G.edge_ceiling(kind, repeats=3, stream=stream, spread_ids=spread) / 1e6
@@ -399,6 +409,7 @@ def run_atos(args, rank: int, world: int):
         "comparisons": comparisons,
         "roofline": roofline,
         "edge_ceiling": edge_ceiling,
+        "pagerank_timeline": pagerank_timeline,
         "gpu_launches": launches,
         "breakdown": {
             "bfs_ms": round(mean(bfs_ms), 3), "pagerank_ms": round(mean(pr_ms), 3), "color_ms": round(mean(gc_ms), 3),
