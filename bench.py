@@ -158,19 +158,23 @@ def replica_throughput(work_per_replica: float, total_ms: float, steps: int, wor
     return ms_step, world * work_per_replica / (ms_step * 1e-3) / 1e9
 
 
-def recorded_traffic(cfg_pr):
+TRAFFIC_SOURCES = ("engine.cuh", "pagerank.cuh", "pagerank.cu", "relabel.cu")
+
+
+def recorded_traffic(cfg_pr, path=None, src_dir=None):
     """DRAM bytes per launch of the PageRank kernel from the committed ncu record, or None when
     the kernel's sources changed since it was taken or the configuration differs."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "pagerank_traffic_rmat22.txt")
+    path = path or os.path.join(ROOT, "profiles", "pagerank_traffic_rmat22.txt")
+    src_dir = src_dir or os.path.join(ROOT, "paper_2112_00132_gb300", "csrc")
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
     digest = [ln.split(": ", 1)[1].strip() for ln in lines if ln.startswith("kernel_sources_sha256: ")]
     h = hashlib.sha256()
-    for f in ("engine.cuh", "pagerank.cuh", "pagerank.cu", "relabel.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2112_00132_gb300", "csrc", f), "rb").read())
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(src_dir, f), "rb").read())
     if not digest or digest[0] != h.hexdigest():
         return None
     key = (cfg_pr.worker_size, cfg_pr.fetch_size, cfg_pr.fetch_policy, cfg_pr.check_size, cfg_pr.flags)

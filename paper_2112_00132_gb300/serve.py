@@ -60,22 +60,27 @@ def make_arrivals(rate: float, duration: float, mix, ngraphs: int, seed: int = 1
 
 def serve(csrs, rate=2000.0, duration=10.0, warmup=1.0, mix=(0.6, 0.3, 0.1), slice_ns=1_000_000, max_slots=64,
           budget_bytes=None, alpha=0.85, eps=1e-9, seed=1, drain_s=30.0, keep=0, cfg=None, graphs=None,
-          large_n=1 << 21, max_large=1):
+          large_n=1 << 21, max_large=1, server_factory=None):
     """Runs the serving loop; returns a summary dict (and up to `keep` finished requests with their
     outputs under "kept", for checking).  `graphs`: resident abi.Graph objects of `csrs` to reuse
-    (created here, and closed at the end, when None)."""
-    import torch
+    (created here, and closed at the end, when None).  `server_factory(graphs, max_slots,
+    budget_bytes, cfg)` builds the server (default: abi.Server); the loop only calls its submit,
+    step, poll, info and close."""
     own_graphs = graphs is None
     if own_graphs:
         graphs = [abi.Graph.from_csr(g) for g in csrs]
     sources = [gg.sources(g, 4096, seed=seed + 11 * k) if g.nnz else np.zeros(1, np.int32)
                for k, g in enumerate(csrs)]
     if budget_bytes is None:
+        import torch
         free, _ = torch.cuda.mem_get_info()
         budget_bytes = int(min(free * 0.5, 64 << 30))
     if cfg is None:  # PageRank and colouring on the graphs' spread-id copies (faster on every graph measured)
         cfg = abi.queue_config(flags=abi.FLAG_SPREAD_IDS)
-    server = abi.Server(graphs, max_slots=max_slots, budget_bytes=budget_bytes, cfg=cfg)
+    if server_factory is None:
+        server = abi.Server(graphs, max_slots=max_slots, budget_bytes=budget_bytes, cfg=cfg)
+    else:
+        server = server_factory(graphs, max_slots, budget_bytes, cfg)
     arrivals = make_arrivals(rate, duration, mix, len(graphs), seed)
     backlog, backlog_large = [], []
     large_active = 0

@@ -26,3 +26,30 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_recorded_traffic_lookup(tmp_path):
+    """roofline.traffic: the entry for the run's PageRank shape, and only while the kernel sources
+    hash to the recorded value."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "csrc"
+    src.mkdir()
+    for f in bench.TRAFFIC_SOURCES:
+        (src / f).write_text(f"// {f}\n")
+    h = hashlib.sha256()
+    for f in bench.TRAFFIC_SOURCES:
+        h.update((src / f).read_bytes())
+    rec = tmp_path / "traffic.txt"
+    rec.write_text("# header\nentry: 512 256 1 8 4 62810000000\nentry: 1024 1024 2 16 4 67650000000\n"
+                   f"kernel_sources_sha256: {h.hexdigest()}\n")
+
+    class Cfg:
+        worker_size, fetch_size, fetch_policy, check_size, flags = 512, 256, 1, 8, 4
+    assert bench.recorded_traffic(Cfg, path=str(rec), src_dir=str(src)) == 62810000000.0
+    Cfg.check_size = 16
+    assert bench.recorded_traffic(Cfg, path=str(rec), src_dir=str(src)) is None  # no such shape
+    Cfg.check_size = 8
+    (src / "pagerank.cuh").write_text("// changed\n")
+    assert bench.recorded_traffic(Cfg, path=str(rec), src_dir=str(src)) is None  # kernel changed
