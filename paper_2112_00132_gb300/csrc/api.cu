@@ -276,6 +276,13 @@ int upload_instances(Scratch& s, int ninst, cudaStream_t st) {
   return ATOS_OK;
 }
 
+// The BSP strategy records no timeline: clear it, so a read after such a call shows nothing.
+int clear_timeline(atos_graph_s* g, cudaStream_t st) {
+  if (g->d_timeline && g->tl_nbuckets > 0)
+    ATOS_TRY(cudaMemsetAsync(g->d_timeline, 0, sizeof(unsigned long long) * 2 * g->tl_nbuckets, st));
+  return ATOS_OK;
+}
+
 // Runs the scheduling loop over the instances in s.h_insts[0, ninst).  The caller has filled the
 // table; `kp` / `kd` are the body's persistent / discrete kernels.
 int run_instances(atos_graph_s* g, int ninst, int max_n, const atos_config& cfg, const void* (*kp)(int),
@@ -566,6 +573,8 @@ int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* dept
   if (cfg.strategy == ATOS_BSP) {
     rc = ensure_bsp(g, bsp_bytes_for(g->n));
     if (rc) return rc;
+    rc = clear_timeline(g, st);
+    if (rc) return rc;
     ATOS_TRY(cudaEventRecord(g->s.ev0, st));
     int64_t iters = 0, edges = 0;
     for (int32_t i = 0; i < nsrc; ++i) {
@@ -674,6 +683,8 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   int64_t iters = 0, bsp_edges = 0, bsp_tasks = 0;
   if (bsp) {
     // Algorithm 3: same initial state (prepare + initial residue), then level-synchronous sweeps
+    rc = clear_timeline(g, st);
+    if (rc) return rc;
     rc = upload_instances(g->s, 1, st);
     if (rc) return rc;
     ATOS_TRY(launch_prepare(g->s.d_insts, 1, n, g->s.d_ctl, 0u, 1u, st));
@@ -729,6 +740,8 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
       if (rc) return rc;
     }
     int32_t* out = spread_bsp ? (int32_t*)g->sp_out : colors;
+    rc = clear_timeline(g, st);
+    if (rc) return rc;
     ATOS_TRY(cudaEventRecord(g->s.ev0, st));
     int64_t iters = 0, edges = 0, tasks = 0;
     rc = bsp_color(spread_bsp ? g->sp_row_ptr : g->row_ptr, spread_bsp ? g->sp_col : g->col, n, out, g->d_bsp,

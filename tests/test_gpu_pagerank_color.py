@@ -305,5 +305,8 @@ def test_throughput_timeline(atos):
             _, st = G.bfs([0, 1], cfg=cfg)
             tasks, edges = G.timeline_read()
             assert tasks.sum() == st.tasks and edges.sum() == st.edges
+        G.pagerank(ALPHA, EPS, cfg=atos.queue_config("bsp"))  # BSP records nothing
+        tasks, edges = G.timeline_read()
+        assert tasks.sum() == 0 and edges.sum() == 0
         G.timeline()
         G.pagerank(ALPHA, EPS)
