@@ -48,6 +48,9 @@ extern "C" {
 
 /* ------------------------------------------------------------------ configuration */
 #define ATOS_WORKER_WARP 32 /* worker_size == 32: one warp per worker (persist-32) */
+#define ATOS_WORKER_THREAD 1 /* worker_size == 1: one thread per worker, scheduled per warp (the
+                                warp pops up to fetch_size <= 32 tasks, each lane expands one);
+                                BFS through atos_bfs only (ATOS_ERR_UNSUPPORTED elsewhere) */
 
 #define ATOS_PERSISTENT 0 /* one launch; workers loop on the queue until it drains (Section 3.4) */
 #define ATOS_DISCRETE 1   /* one launch per queue generation; the host reads the next size */
@@ -98,9 +101,10 @@ extern "C" {
                                      atomic per task (n int32 per source of scratch). */
 
 typedef struct atos_config {
-  int32_t worker_size;    /* 32 (warp worker) or a CTA worker of 64, 128, 256, 512 or 1024 threads */
+  int32_t worker_size;    /* 1 (thread worker, BFS only), 32 (warp worker) or a CTA worker of 64,
+                             128, 256, 512 or 1024 threads */
   int32_t fetch_size;     /* tasks per pop, 1..1024; at most worker_size for CTA workers (FETCH_SIZE
-                             of Section 4); at most 32 for the warp worker */
+                             of Section 4); at most 32 for thread and warp workers */
   int32_t strategy;       /* ATOS_PERSISTENT, ATOS_DISCRETE or ATOS_BSP */
   int32_t fetch_policy;   /* ATOS_FETCH_FIXED, _GREEDY or _SPREAD (persistent strategy only) */
   int32_t num_blocks;     /* persistent grid size; 0 = all CTAs that fit at once (occupancy x SMs) */
@@ -352,7 +356,8 @@ int atos_server_destroy(atos_server_t s);
 #define ATOS_TUNE_PR_MAX_ERROR 1e-4
 
 /* Times candidate configurations of `app` (ATOS_APP_*) on g and returns the fastest in *best
- * (its device time in *best_ms): CTA workers of 128..1024 threads and warp workers, fixed /
+ * (its device time in *best_ms): CTA workers of 128..1024 threads, warp workers and (BFS) thread
+ * workers, fixed /
  * greedy / spread fetch policies, persistent, discrete and BSP strategies, plus the instance
  * window for multi-source BFS, and Check_Size and the threshold-crossing enqueue for PageRank
  * (Figure 4's worker-size x FETCH_SIZE sweep with the kernel strategy of Section 3.4).  Each

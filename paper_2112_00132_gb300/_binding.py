@@ -29,6 +29,7 @@ ERR_UNSUPPORTED = -7
 ERR_BUSY = -8
 
 WORKER_WARP = 32
+WORKER_THREAD = 1
 PERSISTENT, DISCRETE, BSP = 0, 1, 2
 FETCH_FIXED, FETCH_GREEDY, FETCH_SPREAD = 0, 1, 2
 FLAG_PHANTOM_TASK = 1

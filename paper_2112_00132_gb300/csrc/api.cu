@@ -243,7 +243,7 @@ void apply_tuned(atos_graph_t g, int32_t app, atos_config* cfg) {
 int check_config(const atos_config& c) {
   if (!worker_supported(c.worker_size)) return ATOS_ERR_UNSUPPORTED;
   if (c.fetch_size < 1 || c.fetch_size > 1024) return ATOS_ERR_INVALID_ARG;
-  if (c.worker_size != 32 && c.fetch_size > c.worker_size) return ATOS_ERR_INVALID_ARG;
+  if (c.fetch_size > (warp_hosted(c.worker_size) ? 32 : c.worker_size)) return ATOS_ERR_INVALID_ARG;
   if (c.strategy < ATOS_PERSISTENT || c.strategy > ATOS_BSP) return ATOS_ERR_INVALID_ARG;
   if (c.fetch_policy < ATOS_FETCH_FIXED || c.fetch_policy > ATOS_FETCH_SPREAD) return ATOS_ERR_INVALID_ARG;
   if (c.num_blocks < 0 || c.check_size < 0 || c.window < 0 || c.queue_capacity < 0 || c.spin_limit_ns < 0)
@@ -321,14 +321,14 @@ int run_instances(atos_graph_s* g, int ninst, int max_n, const atos_config& cfg,
     if (!fn) return ATOS_ERR_UNSUPPORTED;
     int nb = cfg.num_blocks > 0 ? cfg.num_blocks : resident_blocks(fn, threads);
     if (nb <= 0) return ATOS_ERR_CUDA;
-    const int workers_per_block = worker == 32 ? kWarpBlock / 32 : 1;
+    const int workers_per_block = warp_hosted(worker) ? kWarpBlock / 32 : 1;
     L.nworkers = std::max(1, nb * workers_per_block / window);
     ATOS_TRY(launch_kernel(fn, dim3(nb), threads, L, st));
     iters = 1;
   } else {
     const void* fn = kd(worker);
     if (!fn) return ATOS_ERR_UNSUPPORTED;
-    const int per_block = worker == 32 ? std::min(cfg.fetch_size, 32) * (kWarpBlock / 32) : cfg.fetch_size;
+    const int per_block = warp_hosted(worker) ? std::min(cfg.fetch_size, 32) * (kWarpBlock / 32) : cfg.fetch_size;
     unsigned gen = 0;
     for (int i = 0; i < ninst; ++i) gen = std::max(gen, s.h_insts[i].prefix_len);
     ATOS_TRY(discrete_loop(fn, threads, per_block, L, s.d_insts, ninst, max_n, gen, app == kAppPr, s.d_ctl, s.h_ctl,

@@ -12,7 +12,12 @@
 
 namespace atos {
 
-const void* bfs_persistent_kernel(int worker) { return persistent_kernel_ptr<BfsBody>(worker); }
-const void* bfs_discrete_kernel(int worker) { return discrete_kernel_ptr<BfsBody>(worker); }
+// worker 1: thread workers (each lane of a warp expands its own vertex, BfsBody::lane_items)
+const void* bfs_persistent_kernel(int worker) {
+  return worker == 1 ? (const void*)warp_persistent_kernel<BfsBody, true> : persistent_kernel_ptr<BfsBody>(worker);
+}
+const void* bfs_discrete_kernel(int worker) {
+  return worker == 1 ? (const void*)warp_discrete_kernel<BfsBody, true> : discrete_kernel_ptr<BfsBody>(worker);
+}
 
 }  // namespace atos

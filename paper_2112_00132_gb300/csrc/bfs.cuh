@@ -119,6 +119,38 @@ struct BfsBody {
     if (lane == 0) st[kStatEdges] += e - s;
   }
 
+  // Thread worker (worker_size 1, Section 3.2's smallest worker): each lane expands its own
+  // vertex v (kEmpty: none), walking its row one entry per step; the warp steps together until
+  // every lane's row is done, and pushes through the warp's buffer.  Suits rows of a few entries
+  // (meshes); one long row holds its whole warp.
+  __device__ static void lane_items(WarpSmem& ws, const Instance& I, int v, const Launch& L, unsigned long long* st) {
+    int k = 0, e = 0, nd = 0;
+    if (v != kEmpty) {
+      const int d = ld_relaxed(I.depth + v);
+      if (d != kUnreached) {
+        k = ldg(I.row_ptr + v);
+        e = ldg(I.row_ptr + v + 1);
+        nd = d + 1;
+        if (I.expanded && e - k >= kMarkMinDegree && atomicMin(I.expanded + v, d) <= d) e = k;  // see cta_batch
+      }
+    }
+    unsigned long long edges = (unsigned long long)(e - k);
+    while (__any_sync(0xffffffffu, k < e)) {
+      bool want = false;
+      int nb = 0;
+      if (k < e) {
+        nb = ldg(I.col + k);
+        if (nd < __ldcg(I.depth + nb)) want = nd < atomicMin(I.depth + nb, nd);
+        ++k;
+      }
+      warp_push(ws, want, nb);
+      warp_maybe_flush(ws, I, L, st);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) edges += __shfl_xor_sync(0xffffffffu, edges, o);
+    if ((threadIdx.x & 31) == 0) st[kStatEdges] += edges;
+  }
+
   __device__ static int warp_idle(WarpSmem&, const Instance& I, const Launch&, unsigned long long*) {
     return (threadIdx.x & 31) == 0 ? (instance_quiescent(I) ? 1 : 0) : 0;
   }

@@ -702,7 +702,9 @@ __device__ __forceinline__ void warp_maybe_flush(WarpSmem& ws, const Instance& I
   if (ws.npush > kWarpPushCap - 32) warp_flush(ws, I, 0, L, st);
 }
 
-template <class Body>
+// kLanes: thread workers (worker_size 1) -- the warp pops up to 32 tasks as one, and each lane
+// processes its own task (Body::lane_items) instead of the 32 lanes sharing each task in turn.
+template <class Body, bool kLanes = false>
 __device__ void warp_run_instance(WarpSmem& ws, const Instance& I, const Launch& L, unsigned long long* st,
                                   unsigned long long t0) {
   const int lane = threadIdx.x & 31;
@@ -729,11 +731,15 @@ __device__ void warp_run_instance(WarpSmem& ws, const Instance& I, const Launch&
       if (got) {
         const int cnt = __popc(got);
         const unsigned long long edges0 = st[kStatEdges];
-        while (got) {
-          const int src = __ffs(got) - 1;
-          got &= got - 1;
-          const int it = __shfl_sync(0xffffffffu, item, src);
-          Body::warp_item(ws, I, it, L, st);
+        if constexpr (kLanes) {
+          Body::lane_items(ws, I, item, L, st);
+        } else {
+          while (got) {
+            const int src = __ffs(got) - 1;
+            got &= got - 1;
+            const int it = __shfl_sync(0xffffffffu, item, src);
+            Body::warp_item(ws, I, it, L, st);
+          }
         }
         if (lane == 0) st[kStatTasks] += cnt, st[kStatBatches]++;
         if (lane == 0 && L.timeline) timeline_add(L, (unsigned long long)cnt, st[kStatEdges] - edges0);
@@ -763,7 +769,7 @@ __device__ void warp_run_instance(WarpSmem& ws, const Instance& I, const Launch&
 
 constexpr int kWarpBlock = 256;
 
-template <class Body>
+template <class Body, bool kLanes = false>
 __global__ void __launch_bounds__(kWarpBlock) warp_persistent_kernel(Launch L) {
   __shared__ WarpSmem wsm[kWarpBlock / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -778,7 +784,7 @@ __global__ void __launch_bounds__(kWarpBlock) warp_persistent_kernel(Launch L) {
     const Instance I = L.insts[inst];
     int fin = 0;
     if (lane == 0) fin = ld_relaxed(&I.ctl->finished);  // one lane decides for the warp
-    if (!__shfl_sync(0xffffffffu, fin, 0)) warp_run_instance<Body>(ws, I, L, st, t0);
+    if (!__shfl_sync(0xffffffffu, fin, 0)) warp_run_instance<Body, kLanes>(ws, I, L, st, t0);
     int next = -1;
     if (lane == 0) {
       flush_stats(I, st);
@@ -792,7 +798,7 @@ __global__ void __launch_bounds__(kWarpBlock) warp_persistent_kernel(Launch L) {
 }
 
 // Discrete warp strategy: warp w of the grid processes up to `fetch` items of the generation.
-template <class Body>
+template <class Body, bool kLanes = false>
 __global__ void __launch_bounds__(kWarpBlock) warp_discrete_kernel(Launch L) {
   __shared__ WarpSmem wsm[kWarpBlock / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -809,10 +815,14 @@ __global__ void __launch_bounds__(kWarpBlock) warp_discrete_kernel(Launch L) {
   const int item = lane < span ? take_ticket(I, lo + lane) : kEmpty;
   unsigned got = __ballot_sync(0xffffffffu, item != kEmpty);  // EMPTY only after a failed push
   const int cnt = __popc(got);
-  while (got) {
-    const int src = __ffs(got) - 1;
-    got &= got - 1;
-    Body::warp_item(ws, I, __shfl_sync(0xffffffffu, item, src), L, st);
+  if constexpr (kLanes) {
+    Body::lane_items(ws, I, item, L, st);
+  } else {
+    while (got) {
+      const int src = __ffs(got) - 1;
+      got &= got - 1;
+      Body::warp_item(ws, I, __shfl_sync(0xffffffffu, item, src), L, st);
+    }
   }
   if (lane == 0) st[kStatTasks] += cnt, st[kStatBatches] += cnt > 0;
   if (lane == 0 && cnt > 0 && L.timeline) timeline_add(L, (unsigned long long)cnt, st[kStatEdges]);

@@ -7,8 +7,13 @@
 
 namespace atos {
 
-// Worker shapes that are compiled: the warp worker (32) and CTA workers of 64 .. 1024 threads.
-inline bool worker_supported(int w) { return w == 32 || w == 64 || w == 128 || w == 256 || w == 512 || w == 1024; }
+// Worker shapes that are compiled: thread workers (1, BFS only), the warp worker (32) and CTA
+// workers of 64 .. 1024 threads.
+inline bool worker_supported(int w) {
+  return w == 1 || w == 32 || w == 64 || w == 128 || w == 256 || w == 512 || w == 1024;
+}
+// Workers that a warp hosts (thread and warp workers are scheduled per warp).
+inline bool warp_hosted(int w) { return w == 1 || w == 32; }
 
 template <class Body>
 const void* persistent_kernel_ptr(int worker) {
@@ -36,7 +41,7 @@ const void* discrete_kernel_ptr(int worker) {
   return nullptr;
 }
 
-inline int block_threads(int worker) { return worker == 32 ? kWarpBlock : worker; }
+inline int block_threads(int worker) { return warp_hosted(worker) ? kWarpBlock : worker; }
 
 // CTAs of this kernel that fit on the whole GPU at once (the persistent grid of Section 3.4).
 inline int resident_blocks(const void* fn, int threads) {

@@ -237,7 +237,7 @@ int atos_server_create(const atos_graph_t* graphs, int32_t ngraphs, int32_t max_
   atos_config cfg;
   if (cfg_in) cfg = *cfg_in;
   else atos_queue_config(&cfg, nullptr);
-  if (cfg.strategy != ATOS_PERSISTENT || cfg.worker_size == 32 || !worker_supported(cfg.worker_size))
+  if (cfg.strategy != ATOS_PERSISTENT || warp_hosted(cfg.worker_size) || !worker_supported(cfg.worker_size))
     return ATOS_ERR_UNSUPPORTED;  // serving pauses CTA workers only
   if (cfg.fetch_size < 1 || cfg.fetch_size > cfg.worker_size) return ATOS_ERR_INVALID_ARG;
   atos_server_s* s = new (std::nothrow) atos_server_s();

@@ -131,3 +131,66 @@ def test_bfs_expand_once_all_configs(atos):
                 cfg.flags |= atos.FLAG_BFS_EXPAND_ONCE
                 d, st = G.bfs(srcs, cfg=cfg)
                 assert st.status == 0 and np.array_equal(d.cpu().numpy(), ref), cname
+
+
+def thread_worker_configs(atos):
+    """Thread workers (worker_size 1): a warp pops up to 32 tasks and each lane expands one."""
+    q = atos.queue_config
+    return {
+        "persist-thread-f32": q(worker_size=1, fetch_size=32, fetch_policy=atos.FETCH_SPREAD),
+        "persist-thread-f7-fixed": q(worker_size=1, fetch_size=7, fetch_policy=atos.FETCH_FIXED),
+        "persist-thread-greedy-4blocks": q(worker_size=1, fetch_size=32, fetch_policy=atos.FETCH_GREEDY, num_blocks=4),
+        "discrete-thread-f32": q("discrete-warp", worker_size=1, fetch_size=32),
+        "discrete-thread-f5": q("discrete-warp", worker_size=1, fetch_size=5),
+    }
+
+
+@pytest.mark.parametrize("gname", list(small_graphs().keys()))
+def test_bfs_thread_workers_bit_exact(atos, graphs, gname):
+    """Thread workers reach the same exact depths, with and without expansion markers."""
+    g = graphs[gname]
+    srcs = bfs_sources(g)
+    ref = np.stack([oracle.bfs(g, s) for s in srcs])
+    with atos.Graph.from_csr(g) as G:
+        for cname, cfg in thread_worker_configs(atos).items():
+            for marks in (False, True):
+                if marks:
+                    cfg.flags |= atos.FLAG_BFS_EXPAND_ONCE
+                d, st = G.bfs(srcs, cfg=cfg)
+                assert st.status == 0, (cname, marks, st.status)
+                assert np.array_equal(d.cpu().numpy(), ref), (gname, cname, marks)
+                assert st.tasks >= int((ref != oracle.UNREACHED).sum()), (cname, marks)
+
+
+def test_bfs_thread_workers_windows_and_grid(atos):
+    """Thread workers with instance windows over 40 sources, and on the 2048 x 2048 grid."""
+    g = gg.rmat(12, 16, seed=1)
+    srcs = [int(x) for x in gg.sources(g, 40, seed=2)]
+    refs = np.stack([oracle.bfs(g, s) for s in srcs])
+    with atos.Graph.from_csr(g) as G:
+        for window in (1, 16):
+            cfg = atos.queue_config(worker_size=1, fetch_size=32, window=window)
+            d, st = G.bfs(srcs, cfg=cfg)
+            assert st.status == 0 and np.array_equal(d.cpu().numpy(), refs), window
+    g = gg.grid(2048, delete_frac=0.1, seed=1)
+    ref = oracle.bfs(g, 0)
+    with atos.Graph.from_csr(g) as G:
+        d, st = G.bfs([0], cfg=atos.queue_config(worker_size=1, fetch_size=32))
+        assert st.status == 0 and np.array_equal(d.cpu().numpy()[0], ref)
+
+
+def test_thread_workers_rejected_outside_bfs(atos):
+    """Thread workers are built for BFS only: the other entry points answer UNSUPPORTED, and a
+    fetch size above 32 is an invalid argument."""
+    g = gg.rmat(10, 8, seed=3)
+    cfg = atos.queue_config(worker_size=1, fetch_size=32)
+    with atos.Graph.from_csr(g) as G:
+        for call in (lambda: G.pagerank(0.85, 1e-6, cfg=cfg), lambda: G.color(cfg=cfg)):
+            with pytest.raises(atos.AtosError) as e:
+                call()
+            assert e.value.status == atos.abi.ERR_UNSUPPORTED
+        with pytest.raises(atos.AtosError) as e:
+            G.bfs([0], cfg=atos.queue_config(worker_size=1, fetch_size=64))
+        assert e.value.status == atos.abi.ERR_INVALID_ARG
+        d, st = G.bfs([0], cfg=cfg)  # the graph still works afterwards
+        assert np.array_equal(d.cpu().numpy()[0], oracle.bfs(g, 0))

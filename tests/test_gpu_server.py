@@ -117,6 +117,16 @@ def test_server_admission_by_footprint(atos, graphs):
     G.close()
 
 
+def test_server_rejects_warp_hosted_workers(atos, graphs):
+    """Serving pauses CTA workers between epochs; warp and thread workers are not offered."""
+    G = atos.Graph.from_csr(graphs[0])
+    for w in (1, 32):
+        with pytest.raises(atos.AtosError) as e:
+            atos.Server([G], max_slots=4, budget_bytes=8 << 20, cfg=atos.queue_config(worker_size=w, fetch_size=32))
+        assert e.value.status == atos.abi.ERR_UNSUPPORTED
+    G.close()
+
+
 def test_serving_loop_short_run(atos, graphs):
     """The Poisson serving loop: every request completes, latencies are reported, and sampled
     results are correct."""
