@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--flags", type=int, default=0, help="with --no-tune: atos_config.flags of PageRank and colouring")
     ap.add_argument("--policy", type=int, default=2, help="with --no-tune: PageRank's fetch policy (0 fixed, 1 greedy, 2 spread)")
     ap.add_argument("--no-compare", action="store_true", help="skip the BSP / unbatched comparisons")
+    ap.add_argument("--study", default=None, choices=["color-ids"],
+                    help="color-ids: colouring on the input ids, the spread ids and a random relabelling, for "
+                         "several worker shapes and BSP (Section 5.3's permutation experiment); prints one JSON "
+                         "line instead of the bench line")
     ap.add_argument("--workload", default="rmat22", choices=["rmat22", "batched"],
                     help="rmat22: the single-graph step (default); batched: 256 graphs x (4 BFS + 1 PageRank) "
                          "in one batched launch")
@@ -437,6 +441,45 @@ def run_atos(args, rank: int, world: int):
     return result
 
 
+def run_color_ids_study(args):
+    """Colouring time, recolouring work and colour count on three vertex-id layouts of the same
+    graph: the generator's ids (neighbours have close ids), the library's spread ids
+    (ATOS_FLAG_SPREAD_IDS) and a seeded uniform random relabelling.  Section 5.3 attributes the
+    colouring overwork to neighbours sitting next to each other in the initial queue and removes it
+    with a random permutation; this measures the same on the RMAT 22 bench graph and the 2048 x 2048
+    grid.  Work is colour assignments per vertex (1.0: nobody recoloured)."""
+    import torch
+
+    import paper_2112_00132_gb300 as atos
+
+    atos.build()
+    atos.lib()
+    q = atos.queue_config
+    impls = {"discrete-warp": ("discrete-warp", {}), "persist-warp": ("persist-warp", {}),
+             "persist-cta512": (None, {"worker_size": 512, "fetch_size": 512}), "bsp": ("bsp", {})}
+    out = {"study": "color_id_layout", "unit": "ms", "runs": 3, "graphs": {}}
+    for gname, g in (("rmat22", workload(args.scale)[0]), ("grid2048_del0.1", gg.grid(2048, delete_frac=0.1, seed=1))):
+        rel, _ = gg.relabel(g, seed=1)
+        res = {"n": g.n, "nnz": g.nnz}
+        for layout, graph, flags in (("input", g, 0), ("spread", g, atos.FLAG_SPREAD_IDS), ("random", rel, 0)):
+            G = atos.Graph.from_csr(graph)
+            colors = torch.empty(g.n, dtype=torch.int32, device="cuda")
+            row = {}
+            for iname, (preset, kw) in impls.items():
+                cfg = q(preset, flags=flags, **kw)
+                G.color(colors, cfg=cfg)  # warm-up
+                runs = [G.color(colors, cfg=cfg) for _ in range(3)]
+                ms = sorted(r[2].ms for r in runs)
+                k, st = runs[-1][1], runs[-1][2]
+                assign = st.tasks / g.n if iname == "bsp" else st.tasks / (2 * g.n)
+                row[iname] = {"ms": round(ms[1], 3), "assign_per_vertex": round(assign, 4), "colors": int(k)}
+            res[layout] = row
+            G.close()
+            torch.cuda.synchronize()
+        out["graphs"][gname] = res
+    return out
+
+
 def run_e2e(args, g, srcs, cfgs, work, world):
     """The same step through the public API from pinned host buffers: upload the CSR, run the
     three calls, read the results back, destroy the graph."""
@@ -741,6 +784,35 @@ def cpu_baseline(g, srcs):
             "seconds": round(dt, 2), "host_cores": os.cpu_count(), **info}
 
 
+def cpu_parallel(g, srcs):
+    """The whole step on every host core with the OpenMP baseline (not the oracle): BFS from all
+    sources, PageRank by Jacobi sweeps to the same per-vertex epsilon, speculative colouring.
+    Work counted as in the metric (component edges per BFS, nnz per sweep, entries read by the
+    colouring); `step_seconds` is the wall time of the three."""
+    try:
+        from oracle import parallel
+        parallel.build()
+        threads = os.cpu_count() or 1
+        deg = np.diff(g.row_ptr)
+        t0 = time.perf_counter()
+        d, _ = parallel.bfs(g, srcs, nthreads=threads)
+        t1 = time.perf_counter()
+        _, sweeps = parallel.pagerank(g, ALPHA, EPS, nthreads=threads)
+        t2 = time.perf_counter()
+        _, k, rounds, gc_edges = parallel.color(g, nthreads=threads)
+        t3 = time.perf_counter()
+        bfs_edges = sum(float(deg[row != np.iinfo(np.int32).max].sum()) / 2 for row in d)
+        work = bfs_edges + sweeps * g.nnz + gc_edges
+        return {"value": round(work / (t3 - t0) / 1e9, 4), "unit": UNIT, "cores": threads, "kind": "openmp",
+                "sample": f"the whole step: BFS from all {len(srcs)} sources (one serial search per thread), "
+                          f"FP64 Jacobi PageRank until a sweep changes L1 by <= {EPS:g} n, speculative greedy "
+                          "colouring in rounds",
+                "step_seconds": round(t3 - t0, 3), "bfs_s": round(t1 - t0, 3), "pagerank_s": round(t2 - t1, 3),
+                "color_s": round(t3 - t2, 3), "pagerank_sweeps": sweeps, "colors": k, "color_rounds": rounds}
+    except (OSError, RuntimeError, ValueError, subprocess.CalledProcessError) as e:
+        return {"unavailable": f"OpenMP baseline: {type(e).__name__}: {e}"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -793,7 +865,9 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    if args.impl == "reference":
+    if args.study == "color-ids":
+        res = run_color_ids_study(args) if rank == 0 else None
+    elif args.impl == "reference":
         res = run_reference(args, rank, world)
     elif args.workload == "batched":
         res = run_batched(args, rank, world)
@@ -810,6 +884,7 @@ def main():
             g, srcs = workload(args.scale)
             res["cpu_baseline"] = cpu_baseline(g, srcs)
             res["breakdown"]["colors_serial_greedy"] = res["cpu_baseline"].get("serial_greedy_colors")
+            res["cpu_parallel"] = cpu_parallel(g, srcs)
     if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -59,6 +59,7 @@ def _load():
             lib.gg_copy_out.argtypes = [vp, vp, vp]
             lib.gg_sources.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, vp]
             lib.gg_stream_u64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+            lib.gg_relabel.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int, vp, P(vp)]
             lib.gg_stream_u64.restype = ctypes.c_uint64
             _lib = lib
     return _lib
@@ -150,6 +151,19 @@ def sources(g: CSR, k: int, seed: int = 1) -> np.ndarray:
     if rc != 0:
         raise ValueError(f"gg_sources failed with code {rc}")
     return out
+
+
+def relabel(g: CSR, seed: int = 1, nthreads: int | None = None):
+    """Copy of g with vertex v renamed perm[v] for a seeded uniform random permutation perm, rows
+    sorted; returns (copy, perm).  Section 5.3 runs colouring on randomly relabelled ids."""
+    lib = _load()
+    perm = np.empty(g.n, dtype=np.int32)
+    h = ctypes.c_void_p()
+    rc = lib.gg_relabel(g.row_ptr.ctypes.data, g.col.ctypes.data if g.nnz else None, g.n, seed, _threads(nthreads),
+                        perm.ctypes.data if g.n else None, ctypes.byref(h))
+    if rc != 0:
+        raise ValueError(f"gg_relabel failed with code {rc}")
+    return _take(h, f"{g.name}_relabel{seed}"), perm
 
 
 def stream_u64(seed: int, stream: int, i: int) -> int:

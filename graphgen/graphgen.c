@@ -7,7 +7,8 @@
  *   - 2-D 4-neighbour grids in row-major vertex order,
  *   - optional uniform deletion of a fraction of the undirected edges (seeded partial
  *     Fisher-Yates over the canonical edge list),
- *   - int32 CSR assembly: symmetrised, self-loops and duplicates removed, rows sorted.
+ *   - int32 CSR assembly: symmetrised, self-loops and duplicates removed, rows sorted,
+ *   - a copy of a graph under a seeded uniform random relabelling of its vertices.
  *
  * Randomness is counter-based: value i of stream s under seed k is SplitMix64 (Steele, Lea and
  * Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014) applied to a per-stream
@@ -49,7 +50,7 @@ static inline uint64_t below(uint64_t r, uint64_t range) {
   return (uint64_t)(((unsigned __int128)r * range) >> 64);
 }
 
-enum { STREAM_RMAT = 1, STREAM_DELETE = 2, STREAM_SOURCES = 3 };
+enum { STREAM_RMAT = 1, STREAM_DELETE = 2, STREAM_SOURCES = 3, STREAM_RELABEL = 4 };
 
 /* ---------------------------------------------------------------- parallel for */
 
@@ -433,3 +434,71 @@ int gg_sources(const int32_t* row_ptr, int32_t n, int32_t k, uint64_t seed, int3
 /* Raw access to the counter-based stream, for inputs drawn on the Python side (graph sizes of a
  * batched mix, arrival times of a request stream). */
 uint64_t gg_stream_u64(uint64_t seed, uint64_t stream, uint64_t i) { return stream_at(stream_base(seed, stream), i); }
+
+/* ---------------------------------------------------------------- random relabelling */
+
+typedef struct {
+  const int32_t* rp;
+  const int32_t* col;
+  const int32_t* perm;
+  const int32_t* newrp;
+  int32_t* newcol;
+} relabel_ctx;
+
+static void relabel_rows(void* p, int64_t lo, int64_t hi) {
+  relabel_ctx* c = (relabel_ctx*)p;
+  for (int64_t v = lo; v < hi; ++v) {
+    int32_t* dst = c->newcol + c->newrp[c->perm[v]];
+    for (int64_t k = c->rp[v]; k < c->rp[v + 1]; ++k) *dst++ = c->perm[c->col[k]];
+  }
+}
+
+/* Copy of the CSR (row_ptr, col) in which vertex v is renamed perm[v], perm a uniform random
+ * permutation of 0..n-1 (Fisher-Yates driven by the counter-based stream), rows sorted again.
+ * perm_out (n entries, may be NULL) receives the permutation. */
+int gg_relabel(const int32_t* row_ptr, const int32_t* col, int32_t n, uint64_t seed, int nthreads, int32_t* perm_out,
+               gg_graph** out) {
+  if (!row_ptr || !out || n < 0 || row_ptr[0] != 0) return GG_ERR_ARG;
+  const int64_t nnz = row_ptr[n];
+  if (nnz > 0 && !col) return GG_ERR_ARG;
+  int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+  gg_graph* g = (gg_graph*)calloc(1, sizeof(gg_graph));
+  if (g) {
+    g->row_ptr = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    g->col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz ? nnz : 1));
+  }
+  if (!perm || !g || !g->row_ptr || !g->col) {
+    free(perm);
+    gg_destroy(g);
+    return GG_ERR_OOM;
+  }
+  g->n = n;
+  g->nnz = nnz;
+  for (int32_t v = 0; v < n; ++v) perm[v] = v;
+  const uint64_t base = stream_base(seed, STREAM_RELABEL);
+  for (int64_t i = (int64_t)n - 1; i > 0; --i) {
+    const int64_t j = (int64_t)below(stream_at(base, (uint64_t)i), (uint64_t)i + 1);
+    const int32_t t = perm[i];
+    perm[i] = perm[j];
+    perm[j] = t;
+  }
+  /* new row perm[v] has the length of old row v */
+  for (int32_t v = 0; v < n; ++v) g->row_ptr[perm[v] + 1] = row_ptr[v + 1] - row_ptr[v];
+  g->row_ptr[0] = 0;
+  for (int32_t v = 0; v < n; ++v) g->row_ptr[v + 1] += g->row_ptr[v];
+  relabel_ctx rc = {row_ptr, col, perm, g->row_ptr, g->col};
+  parallel_for(nthreads, n, 4096, relabel_rows, &rc);
+  int32_t* deg = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+  if (!deg) {
+    free(perm);
+    gg_destroy(g);
+    return GG_ERR_OOM;
+  }
+  sortdedup_ctx sc = {g->row_ptr, g->col, deg};
+  parallel_for(nthreads, n, 4096, sortdedup_rows, &sc);  /* no duplicates: only sorts */
+  free(deg);
+  if (perm_out) memcpy(perm_out, perm, sizeof(int32_t) * (size_t)n);
+  free(perm);
+  *out = g;
+  return GG_OK;
+}

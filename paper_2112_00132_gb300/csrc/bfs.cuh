@@ -121,17 +121,26 @@ struct BfsBody {
 
   // Thread worker (worker_size 1, Section 3.2's smallest worker): each lane expands its own
   // vertex v (kEmpty: none), walking its row one entry per step; the warp steps together until
-  // every lane's row is done, and pushes through the warp's buffer.  Suits rows of a few entries
-  // (meshes); one long row holds its whole warp.
+  // every lane's row is done, and pushes through the warp's buffer.  A row longer than
+  // kLaneRowMax would hold the whole warp for its length, so those vertices are expanded after
+  // the short rows by the warp worker's path, 32 entries per step (the thread/warp split of
+  // load-balanced graph frameworks).
+  static constexpr int kLaneRowMax = 32;
   __device__ static void lane_items(WarpSmem& ws, const Instance& I, int v, const Launch& L, unsigned long long* st) {
     int k = 0, e = 0, nd = 0;
+    bool longrow = false;
     if (v != kEmpty) {
       const int d = ld_relaxed(I.depth + v);
       if (d != kUnreached) {
         k = ldg(I.row_ptr + v);
         e = ldg(I.row_ptr + v + 1);
         nd = d + 1;
-        if (I.expanded && e - k >= kMarkMinDegree && atomicMin(I.expanded + v, d) <= d) e = k;  // see cta_batch
+        if (e - k > kLaneRowMax) {
+          longrow = true;
+          e = k;
+        } else if (I.expanded && e - k >= kMarkMinDegree && atomicMin(I.expanded + v, d) <= d) {
+          e = k;  // see cta_batch
+        }
       }
     }
     unsigned long long edges = (unsigned long long)(e - k);
@@ -149,6 +158,8 @@ struct BfsBody {
 #pragma unroll
     for (int o = 16; o; o >>= 1) edges += __shfl_xor_sync(0xffffffffu, edges, o);
     if ((threadIdx.x & 31) == 0) st[kStatEdges] += edges;
+    for (unsigned big = __ballot_sync(0xffffffffu, longrow); big; big &= big - 1)
+      warp_item(ws, I, __shfl_sync(0xffffffffu, v, __ffs(big) - 1), L, st);
   }
 
   __device__ static int warp_idle(WarpSmem&, const Instance& I, const Launch&, unsigned long long*) {

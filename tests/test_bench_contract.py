@@ -53,3 +53,12 @@ def test_recorded_traffic_lookup(tmp_path):
     Cfg.check_size = 8
     (src / "pagerank.cuh").write_text("// changed\n")
     assert bench.recorded_traffic(Cfg, path=str(rec), src_dir=str(src)) is None  # kernel changed
+
+
+def test_cpu_parallel_leg_shape():
+    """The OpenMP comparison leg: the whole step on every host core, labelled as such."""
+    import bench
+    g, srcs = bench.workload(12)
+    r = bench.cpu_parallel(g, srcs)
+    assert r["kind"] == "openmp" and r["unit"] == bench.UNIT and r["cores"] >= 1
+    assert r["value"] > 0 and r["step_seconds"] > 0 and r["pagerank_sweeps"] > 0 and r["colors"] >= 2

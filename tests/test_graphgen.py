@@ -88,3 +88,22 @@ def test_batched_mix_recipe():
     assert all(10 <= s <= 18 for k, s, _ in mix if k == "rmat")
     assert all(64 <= s <= 1024 for k, s, _ in mix if k == "grid")
     assert mix == gg.batched_mix()
+
+
+def test_relabel_is_an_isomorphic_copy():
+    g = gg.rmat(11, 8, seed=5)
+    h, perm = gg.relabel(g, seed=3)
+    assert np.array_equal(np.sort(perm), np.arange(g.n))  # a permutation
+    assert not np.array_equal(perm, np.arange(g.n))
+    assert h.n == g.n and h.nnz == g.nnz
+    assert np.array_equal(h.degrees[perm], g.degrees)
+    rows = np.repeat(np.arange(g.n), g.degrees)
+    old = set(zip(perm[rows].tolist(), perm[g.col].tolist()))
+    hrows = np.repeat(np.arange(h.n), h.degrees)
+    assert old == set(zip(hrows.tolist(), h.col.tolist()))
+    for v in range(h.n):  # rows sorted
+        r = h.col[h.row_ptr[v]:h.row_ptr[v + 1]]
+        assert np.all(np.diff(r) > 0)
+    h2, perm2 = gg.relabel(g, seed=3, nthreads=1)  # the same for any thread count
+    assert np.array_equal(perm, perm2) and np.array_equal(h.col, h2.col)
+    assert not np.array_equal(perm, gg.relabel(g, seed=4)[1])

@@ -313,3 +313,19 @@ def test_pr_rounding_floor_stop():
     centre = (1 + ALPHA * k) / (1 + ALPHA)
     assert x[0] == pytest.approx(centre, rel=1e-12)
     assert np.allclose(x[1:], (1 - ALPHA) + ALPHA * centre / k, rtol=1e-12)
+
+
+def test_relabelling_invariance():
+    """Renaming the vertices renames the results: BFS depths and the PageRank fixed point follow
+    the permutation; greedy colouring in the renamed order is still proper and equals greedy on the
+    original graph in the order perm^-1 (first fit depends only on the visiting order)."""
+    g = gg.rmat(10, 8, seed=9)
+    h, perm = gg.relabel(g, seed=2)
+    s = int(gg.sources(g, 1, seed=4)[0])
+    assert np.array_equal(oracle.bfs(h, int(perm[s]))[perm], oracle.bfs(g, s))
+    assert np.allclose(oracle.pagerank(h)[0][perm], oracle.pagerank(g)[0], rtol=0, atol=1e-10)
+    ch, kh = oracle.greedy_color(h)
+    assert oracle.check_coloring(h, ch)[0] == 0
+    inv = np.argsort(perm)  # vertex of g visited at step i of h's id order
+    cg, kg = oracle.greedy_color(g, order=inv)
+    assert kg == kh and np.array_equal(ch[perm], cg)
