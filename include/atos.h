@@ -100,15 +100,6 @@ extern "C" {
                                      asynchronous BFS's re-expansions on scale-free graphs, at one
                                      atomic per task (n int32 per source of scratch). */
 
-#define ATOS_FLAG_EAGER_HANDOVER 64u /* launches over several instances (multi-source BFS, batches)
-                                     with CTA workers, persistent strategy: once an instance has
-                                     completed n/2 tasks, a CTA that finds its queue empty and holds
-                                     no reserved ticket may leave it (one CTA always stays) to join
-                                     or start a later instance, instead of waiting for the instance
-                                     to finish.  Overlaps the drain of one window with the ramp-up of
-                                     the next when the instances have the same shape.  Ignored
-                                     elsewhere (warp and thread workers, serving). */
-
 typedef struct atos_config {
   int32_t worker_size;    /* 1 (thread worker, BFS only), 32 (warp worker) or a CTA worker of 64,
                              128, 256, 512 or 1024 threads */

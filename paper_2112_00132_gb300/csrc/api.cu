@@ -249,7 +249,7 @@ int check_config(const atos_config& c) {
   if (c.num_blocks < 0 || c.check_size < 0 || c.window < 0 || c.queue_capacity < 0 || c.spin_limit_ns < 0)
     return ATOS_ERR_INVALID_ARG;
   if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS | ATOS_FLAG_USE_TUNED |
-                  ATOS_FLAG_GC_ORDERED | ATOS_FLAG_BFS_EXPAND_ONCE | ATOS_FLAG_EAGER_HANDOVER))
+                  ATOS_FLAG_GC_ORDERED | ATOS_FLAG_BFS_EXPAND_ONCE))
     return ATOS_ERR_INVALID_ARG;
   return ATOS_OK;
 }

@@ -51,8 +51,7 @@ struct alignas(128) QueueCtl {
   unsigned int gen_end;
   unsigned int orphan_count[2];  // serving: pop tickets left pending by paused workers, per epoch parity
   unsigned int orphan_head;      // serving: orphans of the previous epoch handed out so far
-  int workers;                   // batched launch with eager hand-over: CTAs bound to the instance
-  char pad3[80];
+  char pad3[84];
 };
 static_assert(sizeof(QueueCtl) == 512, "QueueCtl layout");
 
@@ -248,15 +247,11 @@ __device__ __forceinline__ bool instance_quiescent(const Instance& I) {
   return (unsigned)(w >> 32) == (unsigned)w;
 }
 
-// Number of tickets a pop reserves under the fetch policy.  Normally at least one: a worker that
-// finds the queue empty waits on a ticket ahead of the tail.  `drain` (eager hand-over, below):
-// only tickets already pushed, possibly none, so that an idle worker holds nothing and may leave.
-__device__ __forceinline__ int pop_size(const Instance& I, const Launch& L, int fetch, bool drain = false) {
+// Number of tickets a pop reserves under the fetch policy.
+__device__ __forceinline__ int pop_size(const Instance& I, const Launch& L, int fetch) {
+  if (L.policy == ATOS_FETCH_FIXED) return fetch;
   unsigned long long w = ld_relaxed_u64(&I.ctl->word);
-  const int pushed = (int)((unsigned)(w >> 32) - ld_relaxed_u32(&I.ctl->head));
-  if (drain && pushed <= 0) return 0;
-  if (L.policy == ATOS_FETCH_FIXED) return drain ? min(fetch, pushed) : fetch;
-  int avail = pushed;
+  int avail = (int)((unsigned)(w >> 32) - ld_relaxed_u32(&I.ctl->head));
   if (L.policy == ATOS_FETCH_SPREAD) avail = avail / max(1, L.nworkers);
   return max(1, min(fetch, avail));
 }
@@ -332,7 +327,6 @@ struct CtaSmem {
   int h, n, flag, cnt;
   unsigned base;
   int inst_id;
-  int drain, idle_run;  // thread 0, eager hand-over: this CTA may leave; consecutive empty pops
   Instance I;
   Extra x;
 };
@@ -469,56 +463,6 @@ __device__ __forceinline__ int next_instance(int inst, const Launch& L) {
   return unfinished_instance(inst, L);
 }
 
-// Eager hand-over (ATOS_FLAG_EAGER_HANDOVER, CTA workers, batched launches).  Instances of one
-// window ramp up and drain at the same time when they have the same shape (many BFS sources on
-// one graph), so with hand-over on completion alone the GPU idles at every window boundary.
-// Instead, once an instance has completed n/2 tasks and unstarted instances remain, a CTA that
-// finds its queue empty while holding no tickets leaves it (one CTA always stays), and joins the
-// newest started instance until that one has its share of CTAs, else starts the next instance.
-constexpr int kEagerIdlePolls = 8;  // consecutive empty pops before a CTA leaves
-
-__device__ __forceinline__ bool eager_enabled(const Launch& L) { return (L.flags & ATOS_FLAG_EAGER_HANDOVER) != 0; }
-
-// Drain phase of instance I: eager hand-over may take CTAs away from it.
-__device__ __forceinline__ bool eager_drain(const Instance& I, const Launch& L) {
-  if (!eager_enabled(L)) return false;
-  const unsigned done = (unsigned)ld_relaxed_u64(&I.ctl->word);
-  return done >= (unsigned)(I.n / 2) && ld_relaxed_u32(L.next_inst) < (unsigned)L.ninst;
-}
-
-// Unbinds the calling CTA from I unless it is the last one there.
-__device__ __forceinline__ bool eager_try_leave(const Instance& I, const Launch& L) {
-  if (ld_relaxed_u32(L.next_inst) >= (unsigned)L.ninst) return false;
-  int w = ld_relaxed(&I.ctl->workers);
-  while (w > 1) {
-    const int o = atomicCAS(&I.ctl->workers, w, w - 1);
-    if (o == w) return true;
-    w = o;
-  }
-  return false;
-}
-
-// Instance the CTA binds to next (-1: none left).
-__device__ __forceinline__ int eager_join(int from, const Launch& L) {
-  const unsigned k = ld_relaxed_u32(L.next_inst);
-  if (k < (unsigned)L.ninst) {
-    const int newest = (int)k - 1;
-    if (newest >= 0 && newest != from && !ld_relaxed(&L.insts[newest].ctl->finished) &&
-        ld_relaxed(&L.insts[newest].ctl->workers) < L.nworkers) {
-      atomicAdd(&L.insts[newest].ctl->workers, 1);
-      return newest;
-    }
-    const unsigned c = atomicAdd(L.next_inst, 1u);
-    if (c < (unsigned)L.ninst) {
-      atomicAdd(&L.insts[c].ctl->workers, 1);
-      return (int)c;
-    }
-  }
-  const int u = unfinished_instance(from, L);
-  if (u >= 0) atomicAdd(&L.insts[u].ctl->workers, 1);
-  return u;
-}
-
 __device__ __forceinline__ void flush_stats(const Instance& I, unsigned long long* st) {
 #pragma unroll
   for (int k = 0; k < kNumStats; ++k)
@@ -554,19 +498,16 @@ __device__ __forceinline__ void cta_orphan_pending(S& sm, bool pending, const La
   }
 }
 
-// Returns 1 when the worker paused (serving slice over), 2 when it left a draining instance
-// (eager hand-over), 0 when the instance ended for it (terminated, or the launch failed).
+// Returns 1 when the worker paused (serving slice over), 0 when the instance ended for it
+// (terminated, or the launch failed).
 template <class Body, int BLOCK>
 __device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const Launch& L,
                                 unsigned long long* st, unsigned long long t0) {
   const Instance& I = sm.I;
   Waiter wait;
-  if (threadIdx.x == 0) sm.idle_run = 0;
   for (;;) {
     if (threadIdx.x == 0) {
-      const bool drain = eager_drain(I, L);
-      sm.drain = drain;
-      int n = pop_size(I, L, L.fetch, drain);
+      int n = pop_size(I, L, L.fetch);
       int from_orphans = 0;
       if (L.slice_ns > 0) {  // serving: the previous epoch's pending tickets come first
         const unsigned r = L.epoch & 1;
@@ -580,7 +521,7 @@ __device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const 
           }
         }
       }
-      if (!from_orphans) sm.h = n ? (int)atomicAdd(&I.ctl->head, (unsigned)n) : 0;
+      if (!from_orphans) sm.h = (int)atomicAdd(&I.ctl->head, (unsigned)n);
       sm.n = n;
       sm.cnt = from_orphans;
     }
@@ -603,7 +544,7 @@ __device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const 
       const int still = __syncthreads_count(pending);
       if (total > 0) {
         unsigned long long edges0 = 0;
-        if (threadIdx.x == 0) st[kStatBatches]++, edges0 = st[kStatEdges], sm.idle_run = 0;
+        if (threadIdx.x == 0) st[kStatBatches]++, edges0 = st[kStatEdges];
         Body::template cta_batch<BLOCK>(sm, total, L, st);
         if (threadIdx.x == 0 && L.timeline) timeline_add(L, (unsigned long long)total, st[kStatEdges] - edges0);
         wait.reset();
@@ -623,8 +564,6 @@ __device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const 
         int f = verdict;
         if (!f && ld_relaxed(L.status) != 0) f = 2;
         if (!f && slice_over(L, t0)) f = 3;
-        // eager hand-over: nothing reserved (still == 0), so leaving strands no ticket
-        if (!f && sm.drain && still == 0 && ++sm.idle_run >= kEagerIdlePolls && eager_try_leave(I, L)) f = 4;
         if (!f && !wait.step(L.spin_limit_ns)) {
           raise_timeout(L, kSiteCtaIdle);
           f = 2;
@@ -637,7 +576,6 @@ __device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const 
         cta_orphan_pending<BLOCK>(sm, pending, L);
         return 1;
       }
-      if (sm.flag == 4) return 2;
       if (sm.flag) return 0;
       if (still == 0) break;
     }
@@ -660,7 +598,6 @@ __global__ void __launch_bounds__(BLOCK, (MinBlocks<Body, BLOCK>::value)) cta_pe
   const unsigned long long t0 = globaltimer();
   int inst = (int)(blockIdx.x % (unsigned)min(L.window, L.ninst));
   if (threadIdx.x == 0) sm.npush = 0;
-  if (threadIdx.x == 0 && eager_enabled(L)) atomicAdd(&L.insts[inst].ctl->workers, 1);
   while (inst >= 0) {
     if (threadIdx.x == 0) {
       sm.I = L.insts[inst];
@@ -668,16 +605,14 @@ __global__ void __launch_bounds__(BLOCK, (MinBlocks<Body, BLOCK>::value)) cta_pe
       sm.flag = ld_relaxed(&sm.I.ctl->finished);  // one thread decides for the block
     }
     __syncthreads();
-    int r = 0;
-    if (!sm.flag) r = cta_run_instance<Body, BLOCK>(sm, L, st, t0);
+    int paused = 0;
+    if (!sm.flag) paused = cta_run_instance<Body, BLOCK>(sm, L, st, t0);
     if (threadIdx.x == 0) {
       flush_stats(sm.I, st);
       int next = -1;
-      if (r == 2 && ld_relaxed(L.status) == 0) {
-        next = eager_join(inst, L);  // left a draining instance that others finish
-      } else if (r == 0 && ld_relaxed(L.status) == 0) {
+      if (!paused && ld_relaxed(L.status) == 0) {
         atomicExch(&sm.I.ctl->finished, 1);
-        next = eager_enabled(L) ? eager_join(inst, L) : next_instance(inst, L);
+        next = next_instance(inst, L);
       }
       sm.flag = next;  // a paused worker leaves the launch (serving epochs end this way)
     }

@@ -83,10 +83,6 @@ std::vector<atos_config> candidates(int app, int nsrc) {
         atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
         c.window = win;
         out.push_back(c);
-        if (win >= 4 && win <= 16) {  // the same windows with eager hand-over
-          c.flags |= ATOS_FLAG_EAGER_HANDOVER;
-          out.push_back(c);
-        }
       }
   }
   if (app == ATOS_APP_BFS) out.push_back(make(nullptr, 1, 32, ATOS_FETCH_SPREAD));  // thread workers
@@ -170,9 +166,6 @@ int atos_batch_autotune(const atos_graph_t* graphs, int32_t ngraphs, const atos_
       atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
       c.window = win;
       cands.push_back(c);
-      atos_config e = c;  // eager hand-over between windowed instances
-      e.flags |= ATOS_FLAG_EAGER_HANDOVER;
-      cands.push_back(e);
       if (has_pr && win == 512)
         for (int cs : {8, 16}) {  // PageRank's Check_Size at the widest window
           atos_config d = c;

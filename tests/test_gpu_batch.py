@@ -64,25 +64,6 @@ def test_mixed_batch_matches_oracle(atos, graphs, worker, window):
         G.close()
 
 
-@pytest.mark.parametrize("worker,window", [(256, 1), (256, 3), (512, 2), (128, 5)])
-def test_mixed_batch_eager_handover(atos, graphs, worker, window):
-    """ATOS_FLAG_EAGER_HANDOVER: CTAs leave draining instances for later ones; every result equal
-    to the oracle, also under CUDA-graph replay."""
-    Gs = [atos.Graph.from_csr(g) for g in graphs]
-    specs = mixed_specs(graphs, per_graph_bfs=4)
-    cfg = atos.queue_config(worker_size=worker, fetch_size=worker, window=window, flags=atos.FLAG_EAGER_HANDOVER)
-    with atos.Batch(Gs, specs, cfg) as B:
-        for graph in (False, True, True):
-            for out in B.outputs:
-                out.fill_(-5)
-            B.run(graph=graph)
-            total, per = B.stats()
-            assert total.status == 0
-            check_results(graphs, specs, B.outputs, per)
-    for G in Gs:
-        G.close()
-
-
 def test_batch_cuda_graph_replay(atos, graphs):
     import torch
     Gs = [atos.Graph.from_csr(g) for g in graphs]

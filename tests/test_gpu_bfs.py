@@ -52,27 +52,6 @@ def test_bfs_many_sources_windows(atos):
                 assert np.array_equal(depths.cpu().numpy(), refs), (window, worker)
 
 
-def test_bfs_eager_handover_many_sources(atos):
-    """ATOS_FLAG_EAGER_HANDOVER with windows smaller than the source count: bit-exact depths for
-    every source, on a scale-free graph and on a grid, with and without expansion markers."""
-    for g, k in ((gg.rmat(14, 16, seed=2), 48), (gg.grid(200, 150, delete_frac=0.1, seed=5), 24)):
-        srcs = [int(x) for x in gg.sources(g, k, seed=7)]
-        refs = np.stack([oracle.bfs(g, s) for s in srcs])
-        with atos.Graph.from_csr(g) as G:
-            for worker, window in ((512, 4), (256, 8), (1024, 3), (128, 1)):
-                for marks in (0, atos.FLAG_BFS_EXPAND_ONCE):
-                    cfg = atos.queue_config(worker_size=worker, fetch_size=worker, window=window,
-                                            flags=atos.FLAG_EAGER_HANDOVER | marks)
-                    d, st = G.bfs(srcs, cfg=cfg)
-                    assert st.status == 0
-                    assert np.array_equal(d.cpu().numpy(), refs), (g.name, worker, window, marks)
-            # the flag is accepted and ignored by the other strategies and worker shapes
-            for cfg in (atos.queue_config("persist-warp", window=4, flags=atos.FLAG_EAGER_HANDOVER),
-                        atos.queue_config("discrete-cta", flags=atos.FLAG_EAGER_HANDOVER)):
-                d, st = G.bfs(srcs[:6], cfg=cfg)
-                assert np.array_equal(d.cpu().numpy(), refs[:6])
-
-
 def test_bfs_stats_consistent(atos):
     g = gg.grid(64, 64, delete_frac=0.1, seed=1)
     ref = oracle.bfs(g, 0)
