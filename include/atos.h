@@ -100,14 +100,6 @@ extern "C" {
                                      asynchronous BFS's re-expansions on scale-free graphs, at one
                                      atomic per task (n int32 per source of scratch). */
 
-#define ATOS_FLAG_BFS_PRUNE_LEAVES 64u /* BFS (every strategy, batches, serving): a vertex of degree 1
-                                     whose depth was improved is not queued.  Its only neighbour is
-                                     the vertex it was reached from, which is shallower, so its task
-                                     could relax nothing; depths are unchanged.  Costs a row_ptr
-                                     read per improvement and saves the task (on scale-free graphs
-                                     a large share of the vertices are leaves).  The level-
-                                     synchronous BFS leaves them out of its frontiers likewise. */
-
 typedef struct atos_config {
   int32_t worker_size;    /* 1 (thread worker, BFS only), 32 (warp worker) or a CTA worker of 64,
                              128, 256, 512 or 1024 threads */

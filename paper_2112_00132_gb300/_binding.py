@@ -38,7 +38,6 @@ FLAG_SPREAD_IDS = 4
 FLAG_USE_TUNED = 8
 FLAG_GC_ORDERED = 16
 FLAG_BFS_EXPAND_ONCE = 32
-FLAG_BFS_PRUNE_LEAVES = 64
 DEVICE_PTRS, BORROW, CHECK_SYMMETRIC, SKIP_VALIDATION = 1, 2, 4, 8
 UNREACHED = 2**31 - 1
 

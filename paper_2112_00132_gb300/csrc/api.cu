@@ -36,8 +36,7 @@ int bsp_color(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t* co
               size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges,
               int64_t* tasks);
 int bsp_bfs(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t src, int32_t* depth, void* scratch,
-            size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges,
-            bool prune_leaves);
+            size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges);
 }  // namespace atos
 
 using namespace atos;
@@ -250,7 +249,7 @@ int check_config(const atos_config& c) {
   if (c.num_blocks < 0 || c.check_size < 0 || c.window < 0 || c.queue_capacity < 0 || c.spin_limit_ns < 0)
     return ATOS_ERR_INVALID_ARG;
   if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS | ATOS_FLAG_USE_TUNED |
-                  ATOS_FLAG_GC_ORDERED | ATOS_FLAG_BFS_EXPAND_ONCE | ATOS_FLAG_BFS_PRUNE_LEAVES))
+                  ATOS_FLAG_GC_ORDERED | ATOS_FLAG_BFS_EXPAND_ONCE))
     return ATOS_ERR_INVALID_ARG;
   return ATOS_OK;
 }
@@ -581,7 +580,7 @@ int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* dept
     for (int32_t i = 0; i < nsrc; ++i) {
       int64_t it = 0, ed = 0;
       rc = bsp_bfs(g->row_ptr, g->col, g->n, sources[i], depths + (size_t)i * n, g->d_bsp, g->bsp_bytes,
-                   (int32_t*)&g->s.h_ctl->maxgen, st, &it, &ed, (cfg.flags & ATOS_FLAG_BFS_PRUNE_LEAVES) != 0);
+                   (int32_t*)&g->s.h_ctl->maxgen, st, &it, &ed);
       if (rc) return rc;
       iters += it;
       edges += ed;
@@ -616,7 +615,6 @@ int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* dept
     Instance I = base_instance(g, i, kAppBfs, cap, 1, sources[i]);
     I.depth = depths + (size_t)i * n;
     I.expanded = marks ? g->d_expanded + (size_t)i * n : nullptr;
-    I.bfs_prune = (cfg.flags & ATOS_FLAG_BFS_PRUNE_LEAVES) ? 1 : 0;
     g->s.h_insts[i] = I;
   }
   if (cfg.window == 0) {

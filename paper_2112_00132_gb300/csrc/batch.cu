@@ -421,7 +421,6 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
       I.prefix_len = 1;
       I.prefix_item = q.source;
       I.depth = (int32_t*)q.out;
-      I.bfs_prune = (cfg.flags & ATOS_FLAG_BFS_PRUNE_LEAVES) ? 1 : 0;
     } else if (q.app == ATOS_APP_PAGERANK) {
       I.app = kAppPr;
       I.prefix_len = (uint32_t)I.n;

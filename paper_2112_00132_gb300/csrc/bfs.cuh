@@ -7,13 +7,6 @@ namespace atos {
 
 constexpr int kMarkMinDegree = 16;  // ATOS_FLAG_BFS_EXPAND_ONCE: rows this long or longer are marked
 
-// ATOS_FLAG_BFS_PRUNE_LEAVES: a neighbour nb whose depth a task of u just improved is queued only
-// if it has another neighbour than u.  A vertex of degree 1 reached from its only neighbour u
-// would relax u alone, which is already shallower, so its task could change nothing.
-__device__ __forceinline__ bool bfs_worth_queuing(const Instance& I, int nb) {
-  return !I.bfs_prune || ldg(I.row_ptr + nb + 1) - ldg(I.row_ptr + nb) > 1;
-}
-
 struct BfsBody {
   using Extra = NoExtra;
   static constexpr int kResidentThreads = 1536;
@@ -23,7 +16,6 @@ struct BfsBody {
   template <int BLOCK, class S>
   __device__ static void relax_round(S& sm, int32_t* __restrict__ depth, const int (&item)[LbsRun<BLOCK>::R],
                                      const int (&nb)[LbsRun<BLOCK>::R]) {
-    const Instance& I = sm.I;
     constexpr int R = LbsRun<BLOCK>::R;
     int cur[R];
 #pragma unroll
@@ -33,7 +25,7 @@ struct BfsBody {
       bool want = false;
       if (item[j] >= 0) {
         const int nd = sm.aux[item[j]];
-        if (nd < cur[j]) want = nd < atomicMin(depth + nb[j], nd) && bfs_worth_queuing(I, nb[j]);
+        if (nd < cur[j]) want = nd < atomicMin(depth + nb[j], nd);
       }
       cta_push(sm, want, nb[j]);
     }
@@ -119,7 +111,7 @@ struct BfsBody {
       int nb = 0;
       if (j < e) {
         nb = ldg(I.col + j);
-        if (nd < __ldcg(I.depth + nb)) want = nd < atomicMin(I.depth + nb, nd) && bfs_worth_queuing(I, nb);
+        if (nd < __ldcg(I.depth + nb)) want = nd < atomicMin(I.depth + nb, nd);
       }
       warp_push(ws, want, nb);
       warp_maybe_flush(ws, I, L, st);
@@ -157,7 +149,7 @@ struct BfsBody {
       int nb = 0;
       if (k < e) {
         nb = ldg(I.col + k);
-        if (nd < __ldcg(I.depth + nb)) want = nd < atomicMin(I.depth + nb, nd) && bfs_worth_queuing(I, nb);
+        if (nd < __ldcg(I.depth + nb)) want = nd < atomicMin(I.depth + nb, nd);
         ++k;
       }
       warp_push(ws, want, nb);

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kBlock) bfs_advance(const int32_t* __restrict_
                                                       const int32_t* __restrict__ offs,
                                                       const int32_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col, int32_t* depth, int32_t nd,
-                                                      int32_t* __restrict__ out, int32_t* out_count, int prune) {
+                                                      int32_t* __restrict__ out, int32_t* out_count) {
   __shared__ int s_off[kChunk + 1];
   __shared__ int s_start[kChunk + 1];
   __shared__ int s_lo, s_cnt;
@@ -126,9 +126,6 @@ __global__ void __launch_bounds__(kBlock) bfs_advance(const int32_t* __restrict_
         }
         nb = __ldg(col + first + (e - o));
         if (nd < __ldcg(depth + nb)) want = nd < atomicMin(depth + nb, nd);
-        // ATOS_FLAG_BFS_PRUNE_LEAVES: a vertex of degree 1 joins no frontier (it could only relax
-        // the neighbour it was reached from)
-        if (want && prune) want = __ldg(row_ptr + nb + 1) - __ldg(row_ptr + nb) > 1;
       }
       const unsigned m = __ballot_sync(0xffffffffu, want);
       if (m) {
@@ -308,8 +305,7 @@ __global__ void fill_kernel(int32_t* a, int32_t n, int32_t value) {
 // Level-synchronous BFS from src.  scratch holds two frontiers of n entries, the scan offsets,
 // the chunk sums and a counter; `hcount` is pinned host memory receiving the next frontier size.
 int bsp_bfs(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t src, int32_t* depth, void* scratch,
-            size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges,
-            bool prune_leaves) {
+            size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges) {
   using namespace bsp;
   int32_t* fa = (int32_t*)scratch;
   int32_t* fb = fa + n;
@@ -332,7 +328,7 @@ int bsp_bfs(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t src, 
     }
     cudaMemsetAsync(count, 0, sizeof(int32_t), s);
     count_launches(1);
-    bfs_advance<<<sms * 8, kBlock, 0, s>>>(fa, F, offs, row_ptr, col, depth, level + 1, fb, count, prune_leaves ? 1 : 0);
+    bfs_advance<<<sms * 8, kBlock, 0, s>>>(fa, F, offs, row_ptr, col, depth, level + 1, fb, count);
     int32_t tot = 0;
     cudaMemcpyAsync(hcount, count, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&tot, offs + F, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

@@ -83,8 +83,6 @@ struct Instance {
   double* cert_y;        // PageRank in batches and serving: FP64 scratch (n) of the output certificate
   int32_t* expanded;     // BFS (optional): the smallest depth at which each vertex has been expanded
   double exact_sum;      // PageRank: n - alpha * (isolated vertices), the fixed point's sum
-  int32_t bfs_prune;     // BFS: 1 = a vertex of degree 1 is never queued (ATOS_FLAG_BFS_PRUNE_LEAVES)
-  int32_t _pad1;
 };
 
 struct Launch {

@@ -361,7 +361,6 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
     I.prefix_len = 1;
     I.prefix_item = q->source;
     I.depth = (int32_t*)q->out;
-    I.bfs_prune = (s->cfg.flags & ATOS_FLAG_BFS_PRUNE_LEAVES) ? 1 : 0;
   } else if (q->app == ATOS_APP_PAGERANK) {
     I.app = kAppPr;
     I.prefix_len = (uint32_t)n;

@@ -95,14 +95,6 @@ std::vector<atos_config> candidates(int app, int nsrc) {
         c.flags |= ATOS_FLAG_BFS_EXPAND_ONCE;
         out.push_back(c);
       }
-    // and with leaf pruning, on top of the markers (the BSP form as well)
-    const size_t m = out.size();
-    for (size_t i = 0; i < m; ++i)
-      if (out[i].strategy == ATOS_BSP || (out[i].flags & ATOS_FLAG_BFS_EXPAND_ONCE)) {
-        atos_config c = out[i];
-        c.flags |= ATOS_FLAG_BFS_PRUNE_LEAVES;
-        out.push_back(c);
-      }
   }
   if (app == ATOS_APP_PAGERANK || app == ATOS_APP_COLOR) {
     // the same shapes on the spread-id copy of the graph

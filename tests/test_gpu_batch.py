@@ -64,22 +64,6 @@ def test_mixed_batch_matches_oracle(atos, graphs, worker, window):
         G.close()
 
 
-@pytest.mark.parametrize("worker", [256, 32])
-def test_mixed_batch_prune_leaves(atos, graphs, worker):
-    """Leaf pruning in batched BFS instances: results equal to the oracle."""
-    Gs = [atos.Graph.from_csr(g) for g in graphs]
-    specs = mixed_specs(graphs)
-    cfg = atos.queue_config(worker_size=worker, fetch_size=32 if worker == 32 else worker, window=3,
-                            flags=atos.FLAG_BFS_PRUNE_LEAVES | atos.FLAG_BFS_EXPAND_ONCE)
-    with atos.Batch(Gs, specs, cfg) as B:
-        B.run()
-        total, per = B.stats()
-        assert total.status == 0
-        check_results(graphs, specs, B.outputs, per)
-    for G in Gs:
-        G.close()
-
-
 def test_batch_cuda_graph_replay(atos, graphs):
     import torch
     Gs = [atos.Graph.from_csr(g) for g in graphs]

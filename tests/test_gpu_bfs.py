@@ -68,45 +68,6 @@ def test_bfs_stats_consistent(atos):
         assert st.tasks == reached  # level-synchronous: no overwork
 
 
-def test_bfs_prune_leaves_stats(atos):
-    """ATOS_FLAG_BFS_PRUNE_LEAVES: depths unchanged; vertices of degree 1 are never queued, so the
-    level-synchronous forms process exactly the reached vertices of degree >= 2 (and the source)."""
-    g = gg.grid(64, 64, delete_frac=0.1, seed=1)
-    deg = g.degrees
-    for src in (0, int(np.flatnonzero(deg == 1)[0])):  # a corner, and a leaf as the source
-        ref = oracle.bfs(g, src)
-        reached = ref != oracle.UNREACHED
-        queued = reached & (deg != 1)
-        queued[src] = True
-        assert (reached & (deg == 1)).sum() > 0  # the graph has leaves to prune
-        with atos.Graph.from_csr(g) as G:
-            d, st = G.bfs([src], cfg=atos.queue_config(flags=atos.FLAG_BFS_PRUNE_LEAVES))
-            assert np.array_equal(d.cpu().numpy()[0], ref)
-            assert st.tasks >= int(queued.sum()) and st.pushes == st.tasks - 1
-            for preset in ("discrete-cta", "discrete-warp", "bsp"):
-                d, st = G.bfs([src], cfg=atos.queue_config(preset, flags=atos.FLAG_BFS_PRUNE_LEAVES))
-                assert np.array_equal(d.cpu().numpy()[0], ref), preset
-                assert st.iterations == ref[queued].max() + 1, preset  # one generation per queued level
-                if preset != "bsp":
-                    assert st.tasks == int(queued.sum()), preset
-
-
-def test_bfs_prune_leaves_all_configs(atos):
-    """Leaf pruning, alone and with expansion markers: bit-exact depths for every configuration,
-    thread workers included."""
-    for g in (gg.rmat(12, 16, seed=1), gg.grid(97, 61, delete_frac=0.1, seed=3), gg.star(1000), gg.path(300)):
-        srcs = bfs_sources(g)
-        ref = np.stack([oracle.bfs(g, s) for s in srcs])
-        with atos.Graph.from_csr(g) as G:
-            cfgs = dict(configs(atos))
-            cfgs.update(thread_worker_configs(atos))
-            for cname, cfg in cfgs.items():
-                for extra in (0, atos.FLAG_BFS_EXPAND_ONCE):
-                    cfg.flags = atos.FLAG_BFS_PRUNE_LEAVES | extra
-                    d, st = G.bfs(srcs, cfg=cfg)
-                    assert st.status == 0 and np.array_equal(d.cpu().numpy(), ref), (g.name, cname, extra)
-
-
 def test_bfs_device_csr_borrow(atos):
     import torch
     g = gg.rmat(10, 16, seed=5)
