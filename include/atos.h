@@ -161,7 +161,10 @@ int atos_csr_validate(const int32_t* row_ptr, const int32_t* col, int32_t n, int
 
 /* Uploads (or, with ATOS_DEVICE_PTRS | ATOS_BORROW, adopts) an undirected CSR graph of n
  * vertices and nnz entries (the CSR of Section 5's algorithms: vertex.neighbors /
- * neighborLen).  Host CSR is validated on the host; device CSR is validated by a kernel.
+ * neighborLen).  Host CSR is validated on the host.  Device CSR: row_ptr is copied to the host
+ * and checked there, every column index is range-checked by a kernel (which only compares it),
+ * and ATOS_CHECK_SYMMETRIC runs on a host copy of col.  ATOS_SKIP_VALIDATION keeps only the
+ * row_ptr[0] == 0 and row_ptr[n] == nnz checks: the caller then vouches for the CSR.
  * On success *out receives a handle owned by the caller until atos_graph_destroy.  n == 0 is
  * allowed (an empty graph). */
 int atos_graph_create(const int32_t* row_ptr, const int32_t* col, int32_t n, int64_t nnz, uint32_t flags,

@@ -406,6 +406,52 @@ int graph_device_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** co
 
 // ============================================================================ C ABI
 
+namespace {
+// Device CSR validation: sets *bad when a column index lies outside [0, n).  Reads col only.
+__global__ void csr_col_range_kernel(const int32_t* __restrict__ col, int64_t nnz, int32_t n, int* bad) {
+  bool out = false;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = col[k];
+    out |= c < 0 || c >= n;
+  }
+  if (__syncthreads_or(out) && threadIdx.x == 0) atomicExch(bad, 1);
+}
+
+// Validates a CSR held in device memory: row_ptr (already copied to the host, `hrp`) on the host,
+// the column range by a kernel, and symmetry (ATOS_CHECK_SYMMETRIC) on a host copy of col.
+int validate_device_csr(const int32_t* hrp, const int32_t* col, int32_t n, int64_t nnz, uint32_t flags,
+                        cudaStream_t st) {
+  if (hrp[0] != 0 || hrp[n] != nnz) return ATOS_ERR_BAD_CSR;
+  for (int32_t v = 0; v < n; ++v)
+    if (hrp[v + 1] < hrp[v]) return ATOS_ERR_BAD_CSR;
+  if (nnz == 0) return ATOS_OK;
+  if (flags & ATOS_CHECK_SYMMETRIC) {
+    std::vector<int32_t> hcol((size_t)nnz);
+    ATOS_TRY(cudaMemcpyAsync(hcol.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st));
+    ATOS_TRY(cudaStreamSynchronize(st));
+    return atos_csr_validate(hrp, hcol.data(), n, nnz, flags);
+  }
+  int* d_bad = nullptr;
+  ATOS_TRY(dev_alloc(&d_bad, 1));
+  int h_bad = 0;
+  cudaError_t e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t blocks = std::min<int64_t>((int64_t)sms * 8, (nnz + 255) / 256);
+    count_launches(1);
+    csr_col_range_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(col, nnz, n, d_bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  pool_free(d_bad);
+  if (e != cudaSuccess) return from_cuda(e);
+  return h_bad ? ATOS_ERR_BAD_CSR : ATOS_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char* atos_status_string(int status) {
@@ -501,9 +547,12 @@ int atos_graph_create(const int32_t* row_ptr, const int32_t* col, int32_t n, int
     ATOS_TRY(cudaMemcpyAsync(hrp.data(), row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, st));
     ATOS_TRY(cudaStreamSynchronize(st));
     rp_host = hrp.data();
-    if (rp_host[0] != 0 || rp_host[n] != nnz) return ATOS_ERR_BAD_CSR;
-    for (int32_t v = 0; v < n; ++v)
-      if (rp_host[v + 1] < rp_host[v]) return ATOS_ERR_BAD_CSR;
+    if (flags & ATOS_SKIP_VALIDATION) {
+      if (rp_host[0] != 0 || rp_host[n] != nnz) return ATOS_ERR_BAD_CSR;
+    } else {
+      const int rc = validate_device_csr(rp_host, col, n, nnz, flags, st);
+      if (rc) return rc;
+    }
   }
   atos_graph_s* g = new (std::nothrow) atos_graph_s();
   if (!g) return ATOS_ERR_OOM;

@@ -81,6 +81,41 @@ def test_bfs_device_csr_borrow(atos):
         assert np.array_equal(depths.cpu().numpy()[0], oracle.bfs(g, 3))
 
 
+def test_device_csr_validated(atos):
+    """A CSR in device memory is checked before any kernel uses it: row_ptr on the host, every
+    column index on the device, symmetry (when asked) on a host copy.  Out-of-range columns are
+    only compared, never dereferenced."""
+    import torch
+    g = gg.rmat(10, 16, seed=5)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    for bad_value in (g.n, -1, 2**31 - 1):
+        col = torch.from_numpy(g.col).cuda()
+        col[g.nnz // 2] = bad_value
+        for borrow in (False, True):
+            with pytest.raises(atos.AtosError) as e:
+                atos.Graph(rp, col, borrow=borrow)
+            assert e.value.status == atos.abi.ERR_BAD_CSR, (bad_value, borrow)
+    # a one-directional edge: accepted without the symmetry check, rejected with it
+    one_way = gg.from_edges(4, [(0, 1), (1, 2), (2, 3)])
+    col = torch.from_numpy(one_way.col.copy()).cuda()
+    col[0] = 2  # row 0 now holds (0, 2), whose mirror (2, 0) is missing
+    rp1 = torch.from_numpy(one_way.row_ptr).cuda()
+    with atos.Graph(rp1, col) as G:
+        assert G.n == 4
+    with pytest.raises(atos.AtosError) as e:
+        atos.Graph(rp1, col, check_symmetric=True)
+    assert e.value.status == atos.abi.ERR_BAD_CSR
+    with atos.Graph(rp1, torch.from_numpy(one_way.col).cuda(), check_symmetric=True) as G:
+        d, _ = G.bfs([0])
+        assert np.array_equal(d.cpu().numpy()[0], oracle.bfs(one_way, 0))
+    # a non-monotone row_ptr
+    rp_bad = rp.clone()
+    rp_bad[5] = rp_bad[7]
+    with pytest.raises(atos.AtosError) as e:
+        atos.Graph(rp_bad, torch.from_numpy(g.col).cuda())
+    assert e.value.status == atos.abi.ERR_BAD_CSR
+
+
 def test_bfs_invalid_arguments(atos):
     g = gg.path(10)
     with atos.Graph.from_csr(g) as G:
