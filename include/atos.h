@@ -143,7 +143,8 @@ typedef struct atos_graph_s* atos_graph_t;
 #define ATOS_BORROW 2u           /* with ATOS_DEVICE_PTRS: use the caller's buffers in place; the
                                     caller keeps them alive and unchanged until destroy */
 #define ATOS_CHECK_SYMMETRIC 4u  /* also verify that every entry (u, v) has its mirror (v, u) */
-#define ATOS_SKIP_VALIDATION 8u  /* trust the CSR (host pointers only) */
+#define ATOS_SKIP_VALIDATION 8u  /* trust the CSR: skip the monotonicity, column-range and symmetry
+                                    checks; row_ptr[0] == 0 and row_ptr[n] == nnz are still checked */
 
 /* ------------------------------------------------------------------ entry points */
 

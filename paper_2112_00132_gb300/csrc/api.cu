@@ -540,6 +540,8 @@ int atos_graph_create(const int32_t* row_ptr, const int32_t* col, int32_t n, int
     if (!(flags & ATOS_SKIP_VALIDATION)) {
       int rc = atos_csr_validate(row_ptr, col, n, nnz, flags);
       if (rc) return rc;
+    } else if (row_ptr[0] != 0 || row_ptr[n] != nnz) {
+      return ATOS_ERR_BAD_CSR;
     }
     rp_host = row_ptr;
   } else {
