@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the BSP / unbatched comparisons")
     ap.add_argument("--study", default=None, choices=["color-ids"],
                     help="color-ids: colouring on the input ids, the spread ids and a random relabelling, for "
-                         "several worker shapes and BSP (Section 5.3's permutation experiment); prints one JSON "
+                         "several worker shapes and BSP (Section 6.4's permutation experiment); prints one JSON "
                          "line instead of the bench line")
     ap.add_argument("--workload", default="rmat22", choices=["rmat22", "batched"],
                     help="rmat22: the single-graph step (default); batched: 256 graphs x (4 BFS + 1 PageRank) "
@@ -444,7 +444,7 @@ def run_atos(args, rank: int, world: int):
 def run_color_ids_study(args):
     """Colouring time, recolouring work and colour count on three vertex-id layouts of the same
     graph: the generator's ids (neighbours have close ids), the library's spread ids
-    (ATOS_FLAG_SPREAD_IDS) and a seeded uniform random relabelling.  Section 5.3 attributes the
+    (ATOS_FLAG_SPREAD_IDS) and a seeded uniform random relabelling.  Section 6.4 attributes the
     colouring overwork to neighbours sitting next to each other in the initial queue and removes it
     with a random permutation; this measures the same on the RMAT 22 bench graph and the 2048 x 2048
     grid.  Work is colour assignments per vertex (1.0: nobody recoloured)."""

@@ -1,7 +1,7 @@
 """Seeded synthetic input graphs, shared by the oracle and by the CUDA path.
 
 This module holds no arithmetic of the scheduling method or of BFS, PageRank or colouring.  It
-builds int32 CSR graphs shaped like the paper's workloads (Section 5, Table 2): RMAT graphs for
+builds int32 CSR graphs shaped like the paper's workloads (Section 6.2, Table 2): RMAT graphs for
 the scale-free inputs and 2-D grids with random edge deletion for the mesh-like ones.  All
 randomness comes from a counter-based SplitMix64 stream (see ``graphgen.c``), so a (recipe, seed)
 pair always gives the same graph on any machine and for any thread count.
@@ -155,7 +155,7 @@ def sources(g: CSR, k: int, seed: int = 1) -> np.ndarray:
 
 def relabel(g: CSR, seed: int = 1, nthreads: int | None = None):
     """Copy of g with vertex v renamed perm[v] for a seeded uniform random permutation perm, rows
-    sorted; returns (copy, perm).  Section 5.3 runs colouring on randomly relabelled ids."""
+    sorted; returns (copy, perm).  Section 6.4 runs colouring on randomly relabelled ids."""
     lib = _load()
     perm = np.empty(g.n, dtype=np.int32)
     h = ctypes.c_void_p()

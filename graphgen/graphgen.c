@@ -15,7 +15,7 @@
  * base plus i times the golden-ratio increment.  Every value depends only on (k, s, i), so the
  * output is identical for any thread count and on any host architecture.
  *
- * The workload shapes stand in for the paper's SuiteSparse inputs (Section 5, Table 2): RMAT for
+ * The workload shapes stand in for the paper's SuiteSparse inputs (Section 6.2, Table 2): RMAT for
  * the scale-free graphs, the grid with deletions for the mesh-like road networks.
  */
 #include <pthread.h>

@@ -217,11 +217,12 @@ int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint3
  * zero.  Either pointer may be NULL. */
 int atos_debug_scratch_check(atos_graph_t g, uint64_t* set_bits, uint64_t* busy_slots);
 
-/* Throughput timeline (tracing): the persistent and discrete calls on g that follow record, per
- * bucket of bucket_ns nanoseconds from the start of the call, the tasks and neighbour entries of
- * the worker batches that ended in it (the last bucket takes everything later).  nbuckets = 0
- * turns it off.  It costs two global atomics per batch while on.  The BSP strategy records nothing.
- * Synchronises the device. */
+/* Throughput timeline (tracing; the throughput-over-time view of Section 6.4, Figures 1-3): the
+ * persistent and discrete calls on g that follow record, per bucket of bucket_ns nanoseconds
+ * from the start of the call, the tasks and neighbour entries of the worker batches that ended
+ * in it (the last bucket takes everything later).  nbuckets = 0 turns it off.  It costs two
+ * global atomics per batch while on.  The BSP strategy records nothing.  Synchronises the
+ * device. */
 int atos_timeline(atos_graph_t g, int64_t bucket_ns, int32_t nbuckets);
 
 /* The timeline of the last call on g: tasks[b] and edges[b] (HOST arrays of nbuckets, the
@@ -235,7 +236,8 @@ int atos_timeline_read(atos_graph_t g, int64_t* tasks, int64_t* edges, int32_t n
  * into an n-float scratch the call allocates.  *ms_per_pass: mean device time of one pass over
  * `repeats` passes after a warm-up pass (stream-ordered on `stream`, which it synchronises).
  * nnz / ms_per_pass is the edge rate those loops can reach on this graph: the roofline of
- * the PageRank kernel (limited on scale-free graphs by same-address atomics at the hubs). */
+ * the PageRank kernel (on the input layout of an RMAT graph the sorted rows send a warp's
+ * updates to few L2 slices; ATOS_CEILING_SPREAD_IDS measures the spread layout). */
 #define ATOS_CEILING_SCATTER 0
 #define ATOS_CEILING_GATHER 1
 #define ATOS_CEILING_SPREAD_IDS 2 /* or-ed into kind: measure on the spread-id copy of the graph

@@ -1,7 +1,8 @@
 // tune.cu -- autotuner: picks worker size, fetch size, fetch policy, strategy and (BFS with many
 // sources) the instance window for one application on one graph by timing the candidates, the
-// sweep of Figure 4 (worker size x FETCH_SIZE, thread workers included for BFS) extended with the kernel strategy (Section 3.4) and,
-// for PageRank and colouring, the spread-id layout of the graph.
+// sweep of Figure 4 (worker size x FETCH_SIZE, thread workers included for BFS) extended with
+// the kernel strategy (Section 3.4) and, for PageRank and colouring, the spread-id layout of the
+// graph.
 //
 // Candidates are run on the caller's graph through the public entry points (each run is checked:
 // a candidate that fails, or a PageRank candidate whose FP64 error bound exceeds
