@@ -149,7 +149,7 @@ typedef struct atos_graph_s* atos_graph_t;
 /* ------------------------------------------------------------------ entry points */
 
 /* Fills *cfg with the preset named `preset`: NULL or "default" (persistent CTA worker of 256
- * threads, fetch 256), "persist-warp" (Section 5's persist-32), "persist-cta", "discrete-cta",
+ * threads, fetch 256), "persist-warp" (Section 6.2's persist-32), "persist-cta", "discrete-cta",
  * "discrete-warp", "bsp", or "autotune" (the defaults plus ATOS_FLAG_USE_TUNED: each call takes
  * the configuration atos_autotune cached for its graph's class and application, and the
  * defaults when there is none).  Returns ATOS_ERR_INVALID_ARG for an unknown name or NULL cfg. */

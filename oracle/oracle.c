@@ -8,11 +8,11 @@
  *
  * What it computes, and the passage each function follows:
  *
- *   oracle_bfs               Section 4.1 (Algorithms 1 and 2): the speculative BFS reaches the
+ *   oracle_bfs               Section 5.1 (Algorithms 1 and 2): the speculative BFS reaches the
  *                            exact hop distance from the source, i.e. what a textbook serial FIFO
  *                            breadth-first search computes.  That definition is written out here.
  *   oracle_bfs_certificate   the properties that characterise hop distances, checkable at any size.
- *   oracle_pagerank          Section 4.2 (Algorithms 3 and 4): push-residual PageRank converges to
+ *   oracle_pagerank          Section 5.2 (Algorithms 3 and 4): push-residual PageRank converges to
  *                            the fixed point of x = (1 - alpha) 1 + alpha P x, P = A D^-1 on the
  *                            paper's unnormalised scale (initial rank 1 - alpha).  Solved here by
  *                            plain FP64 Jacobi power iteration.
@@ -21,7 +21,7 @@
  *   oracle_pr_push_serial    the steps of Algorithm 3 run serially (initial residue, then push
  *                            exch / rank += / scatter while any residue exceeds epsilon), used for
  *                            workload statistics and to pin the reading of the initial residue.
- *   oracle_greedy_color      Section 4.3: serial greedy first-fit colouring in a given vertex order
+ *   oracle_greedy_color      Section 5.3: serial greedy first-fit colouring in a given vertex order
  *                            (the sequential algorithm the speculative colouring parallelises).
  *   oracle_check_coloring    proper-colouring check and the first-fit range 0 <= c(v) <= deg(v).
  *

@@ -6,12 +6,12 @@
  * NOT the parity reference (the serial oracle is); it is a reasonable parallel CPU program for the
  * same step, timed next to the GPU, and the tests check it against the serial oracle.
  *
- *   par_bfs       hop distances from each of nsrc sources (Section 4.1's result).  With at least
+ *   par_bfs       hop distances from each of nsrc sources (Section 5.1's result).  With at least
  *                 as many sources as threads, the sources run in parallel, one serial FIFO search
  *                 per thread; otherwise each source runs a level-synchronous parallel search
  *                 (Algorithm 1's structure: the frontier is split over threads, a vertex joins the
  *                 next frontier through a compare-and-swap on its depth).
- *   par_pagerank  the fixed point of x = (1 - alpha) 1 + alpha P x (Section 4.2's result) by
+ *   par_pagerank  the fixed point of x = (1 - alpha) 1 + alpha P x (Section 5.2's result) by
  *                 parallel FP64 Jacobi sweeps in pull form, until the L1 change of a sweep is at
  *                 most tol_per_vertex * n.
  *   par_color     speculative greedy colouring in rounds (Algorithm 5's structure): every vertex

@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(BLOCK) cta_discrete_kernel(Launch L) {
 
 // ----------------------------------------------------------------------- warp worker engine
 //
-// Each warp is an independent worker (persist-32 of Section 5): it pops up to 32 tickets, and
+// Each warp is an independent worker (persist-32 of Section 6.2): it pops up to 32 tickets, and
 // processes the items it got one after another, its 32 lanes striding each item's neighbours.
 // Body must provide:
 //   static void warp_item(WarpSmem&, const Instance&, int item, const Launch&, st)
