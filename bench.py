@@ -165,21 +165,31 @@ def replica_throughput(work_per_replica: float, total_ms: float, steps: int, wor
 TRAFFIC_SOURCES = ("engine.cuh", "pagerank.cuh", "pagerank.cu", "relabel.cu")
 
 
+def kernel_sources_digest(src_dir=None):
+    """sha256 of the PageRank kernel's sources with comments and whitespace removed, so that only a
+    change of the code itself voids the recorded traffic."""
+    import hashlib
+    import re
+    src_dir = src_dir or os.path.join(ROOT, "paper_2112_00132_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        text = open(os.path.join(src_dir, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)  # block comments
+        text = re.sub(r"//[^\n]*", " ", text)                # line comments
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()
+
+
 def recorded_traffic(cfg_pr, path=None, src_dir=None):
     """DRAM bytes per launch of the PageRank kernel from the committed ncu record, or None when
-    the kernel's sources changed since it was taken or the configuration differs."""
-    import hashlib
+    the kernel's code changed since it was taken or the configuration differs."""
     path = path or os.path.join(ROOT, "profiles", "pagerank_traffic_rmat22.txt")
-    src_dir = src_dir or os.path.join(ROOT, "paper_2112_00132_gb300", "csrc")
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
-    digest = [ln.split(": ", 1)[1].strip() for ln in lines if ln.startswith("kernel_sources_sha256: ")]
-    h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        h.update(open(os.path.join(src_dir, f), "rb").read())
-    if not digest or digest[0] != h.hexdigest():
+    digest = [ln.split(": ", 1)[1].strip() for ln in lines if ln.startswith("kernel_code_sha256: ")]
+    if not digest or digest[0] != kernel_sources_digest(src_dir):
         return None
     key = (cfg_pr.worker_size, cfg_pr.fetch_size, cfg_pr.fetch_policy, cfg_pr.check_size, cfg_pr.flags)
     for ln in lines:

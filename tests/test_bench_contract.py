@@ -31,19 +31,15 @@ def test_reference_arm_json_line():
 def test_recorded_traffic_lookup(tmp_path):
     """roofline.traffic: the entry for the run's PageRank shape, and only while the kernel sources
     hash to the recorded value."""
-    import hashlib
     sys.path.insert(0, ROOT)
     import bench
     src = tmp_path / "csrc"
     src.mkdir()
     for f in bench.TRAFFIC_SOURCES:
-        (src / f).write_text(f"// {f}\n")
-    h = hashlib.sha256()
-    for f in bench.TRAFFIC_SOURCES:
-        h.update((src / f).read_bytes())
+        (src / f).write_text(f"// {f}\nint x_{f.replace('.', '_')} = 1;\n")
     rec = tmp_path / "traffic.txt"
     rec.write_text("# header\nentry: 512 256 1 8 4 62810000000\nentry: 1024 1024 2 16 4 67650000000\n"
-                   f"kernel_sources_sha256: {h.hexdigest()}\n")
+                   f"kernel_code_sha256: {bench.kernel_sources_digest(str(src))}\n")
 
     class Cfg:
         worker_size, fetch_size, fetch_policy, check_size, flags = 512, 256, 1, 8, 4
@@ -51,8 +47,10 @@ def test_recorded_traffic_lookup(tmp_path):
     Cfg.check_size = 16
     assert bench.recorded_traffic(Cfg, path=str(rec), src_dir=str(src)) is None  # no such shape
     Cfg.check_size = 8
-    (src / "pagerank.cuh").write_text("// changed\n")
-    assert bench.recorded_traffic(Cfg, path=str(rec), src_dir=str(src)) is None  # kernel changed
+    (src / "pagerank.cuh").write_text("/* a comment\n   edited */ int x_pagerank_cuh   =  1;  // and here\n")
+    assert bench.recorded_traffic(Cfg, path=str(rec), src_dir=str(src)) == 62810000000.0  # comments only
+    (src / "pagerank.cuh").write_text("int x_pagerank_cuh = 2;\n")
+    assert bench.recorded_traffic(Cfg, path=str(rec), src_dir=str(src)) is None  # code changed
 
 
 def test_cpu_parallel_leg_shape():
