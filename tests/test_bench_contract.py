@@ -60,3 +60,16 @@ def test_cpu_parallel_leg_shape():
     r = bench.cpu_parallel(g, srcs)
     assert r["kind"] == "openmp" and r["unit"] == bench.UNIT and r["cores"] >= 1
     assert r["value"] > 0 and r["step_seconds"] > 0 and r["pagerank_sweeps"] > 0 and r["colors"] >= 2
+
+
+def test_cpu_parallel_batched_leg():
+    """The OpenMP leg of the batched workload on a small mix: every graph's sources and PageRank."""
+    import bench
+    import graphgen as gg
+    graphs = [gg.rmat(10, 8, seed=3), gg.grid(40, 30, delete_frac=0.1, seed=2)]
+    specs = []
+    for gi, g in enumerate(graphs):
+        specs += [("bfs", gi, int(s)) for s in gg.sources(g, 4, seed=gi + 1)]
+        specs.append(("pagerank", gi, 0.85, 1e-9))
+    r = bench.cpu_parallel_batched(graphs, specs)
+    assert r["kind"] == "openmp" and r["value"] > 0 and r["seconds"] > 0 and r["cores"] >= 1
