@@ -392,7 +392,8 @@ int atos_tuned_config(atos_graph_t g, int32_t app, atos_config* cfg);
 
 /* ------------------------------------------------------------------ allocation-free BFS */
 
-/* Largest graph atos_bfs_noalloc accepts (its fixed ring holds 2^19 slots). */
+/* Largest graph atos_bfs_noalloc accepts (its fixed ring holds 2^20 slots, the floor atos_bfs
+ * gives a single search). */
 #define ATOS_NOALLOC_MAX_VERTICES 262144
 
 /* Single-source BFS (same result as atos_bfs) that allocates no memory, for callers that must
@@ -402,15 +403,19 @@ int atos_tuned_config(atos_graph_t g, int32_t app, atos_config* cfg);
  *   row_ptr, col: DEVICE int32 CSR of an undirected graph (n + 1 and nnz entries), unchanged
  *   during the call; source in [0, n); depth: DEVICE int32[n] receiving the hop distances
  *   (INT32_MAX outside the source's component).
- * Scratch: one fixed array of about 4.1 MiB of device memory inside the library image, held by
+ * The CSR is checked on the device before the search reads it (row_ptr[0] == 0, row_ptr[n] ==
+ * nnz, rows non-decreasing, every column index in [0, n); symmetry is not checked), at the cost
+ * of one host round trip; a malformed CSR returns ATOS_ERR_BAD_CSR and the search does not run.
+ * Scratch: one fixed array of about 8.2 MiB of device memory inside the library image, held by
  * every GPU that loads the library until the process exits, and shared by all calls on that GPU.
- * The first call on a device obtains the array's device address (cudaGetSymbolAddress) and
- * initialises it; make that first call before any stream capture.  Calls that overlap on the
- * GPU (other streams, other host threads) race on the shared scratch and must be serialised by
- * the caller.  The call synchronises `stream` and returns the device status (ATOS_OK,
- * ATOS_ERR_TIMEOUT, ATOS_ERR_QUEUE_OVERFLOW) or ATOS_ERR_CUDA; it returns ATOS_ERR_INVALID_ARG
- * for NULL pointers, a source out of range, or n < 1 or n > ATOS_NOALLOC_MAX_VERTICES (checked
- * before any GPU work). */
+ * Each call looks up the array's device address (cudaGetSymbolAddress) on the current device; the
+ * first call on a device also initialises the array; make that first call before any stream
+ * capture.  Calls that overlap on the GPU (other streams, other host threads) race on the shared
+ * scratch and must be serialised by the caller.  The call synchronises `stream` and returns the
+ * device status (ATOS_OK, ATOS_ERR_TIMEOUT, ATOS_ERR_QUEUE_OVERFLOW), ATOS_ERR_BAD_CSR or
+ * ATOS_ERR_CUDA; it returns ATOS_ERR_INVALID_ARG for NULL pointers, a source out of range, nnz
+ * outside [0, INT32_MAX], or n < 1 or n > ATOS_NOALLOC_MAX_VERTICES (checked before any GPU
+ * work). */
 int atos_bfs_noalloc(const int32_t* row_ptr, const int32_t* col, int32_t n, int64_t nnz, int32_t source,
                      int32_t* depth, void* stream);
 
