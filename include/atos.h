@@ -71,15 +71,21 @@ extern "C" {
                                      ignored.  Persistent and discrete strategies; BSP ignores it. */
 
 #define ATOS_FLAG_SPREAD_IDS 4u   /* PageRank and colouring (persistent and discrete strategies) run on
-                                     an internal copy of the graph whose vertex ids are spread by the
-                                     bijection v -> (a v + c) mod n (a ~ 0.618 n, coprime to n), built
-                                     on the device at the first such call (4 (n + 1) + 4 nnz bytes).
-                                     On scale-free graphs sorted rows all begin with the few low-id
-                                     hubs, so a warp's 32 state updates land in a few L2 slices;
-                                     spread ids balance them over the slices.  Results come back in
-                                     the caller's ids (one gather).  Batches and servers apply it to
-                                     their PageRank and colouring instances, and the BSP strategy to
-                                     its PageRank and colouring; BFS ignores it. */
+                                     an internal copy of the graph with its vertices renamed, built on
+                                     the device at the first such call (4 (2 n + 1) + 4 nnz bytes; the
+                                     build synchronises the stream once).  The highest-degree vertices
+                                     (whole degree classes, at most 16384 and n / 32) take ids that
+                                     are multiples of 32 (one per 128-byte line), spread over the id
+                                     range; the rest are spread over the remaining ids by the
+                                     bijection r -> (a r + c) mod m (a ~ 0.618 m, coprime to m).  On
+                                     scale-free graphs sorted rows all begin with the few low-id hubs,
+                                     so a warp's 32 state updates land in a few L2 slices; spread ids
+                                     balance them over the slices, and PageRank's CTA workers add the
+                                     updates bound for the hubs in shared memory, sending each hub one
+                                     update per batch.  Results come back in the caller's ids (one
+                                     gather).  Batches and servers apply it to their PageRank and
+                                     colouring instances, and the BSP strategy to its PageRank and
+                                     colouring; BFS ignores it. */
 
 #define ATOS_FLAG_USE_TUNED 8u     /* atos_bfs / atos_pagerank / atos_color use the configuration
                                      cached by atos_autotune for the graph's class (all fields),
@@ -216,6 +222,16 @@ int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint3
  * (PageRank / colouring) and the occupied slots of its rings; after a successful run both are
  * zero.  Either pointer may be NULL. */
 int atos_debug_scratch_check(atos_graph_t g, uint64_t* set_bits, uint64_t* busy_slots);
+
+/* Diagnostics: the vertex layout of the spread-id copy of g (ATOS_FLAG_SPREAD_IDS), built first
+ * if needed (which synchronises `stream`).  perm: HOST int32 array of n entries receiving the
+ * copy's id of every vertex (may be NULL); *hubs (may be NULL) receives H, the number of hubs:
+ * the vertices of the largest degree classes (four classes per power of two), whole classes while
+ * they fit in min(16384, 2^k), 2^k the largest power of two <= n / 32, ranked by decreasing class
+ * and increasing vertex id within a class.  The hub of rank i has the id 32 ((mul i + add) mod
+ * 2^k) with mul odd: one hub per 128-byte line of a 4-byte state array, at most.  The other
+ * vertices take the remaining ids in spread order. */
+int atos_debug_spread_layout(atos_graph_t g, int32_t* perm, int32_t* hubs, void* stream);
 
 /* Throughput timeline (tracing; the throughput-over-time view of Section 6.4, Figures 1-3): the
  * persistent and discrete calls on g that follow record, per bucket of bucket_ns nanoseconds

@@ -177,6 +177,8 @@ def lib() -> ctypes.CDLL:
         L.atos_tuned_config.restype = ctypes.c_int
         L.atos_bfs_noalloc.argtypes = [vp, vp, i32, i64, i32, vp, vp]
         L.atos_bfs_noalloc.restype = ctypes.c_int
+        L.atos_debug_spread_layout.argtypes = [vp, vp, P(i32), vp]
+        L.atos_debug_spread_layout.restype = ctypes.c_int
         L.atos_debug_scratch_check.argtypes = [vp, P(ctypes.c_uint64), P(ctypes.c_uint64)]
         L.atos_debug_scratch_check.restype = ctypes.c_int
         L.atos_kernel_launches.argtypes = []
@@ -310,6 +312,17 @@ class Graph:
         _check(lib().atos_debug_queue_state(self._h, ninst, words.ctypes.data, heads.ctypes.data,
                                             ctypes.byref(site)), "atos_debug_queue_state")
         return [(int(w >> 32), int(w & 0xffffffff), int(h)) for w, h in zip(words, heads)], site.value
+
+    def spread_layout(self, stream=None):
+        """(perm, hubs) of the spread-id copy: perm[v] is the copy's id of v, ids [0, hubs) the hub
+        region."""
+        n = ctypes.c_int32()
+        lib().atos_graph_info(self._h, ctypes.byref(n), None, None)
+        perm = np.zeros(max(n.value, 1), dtype=np.int32)
+        hubs = ctypes.c_int32(0)
+        _check(lib().atos_debug_spread_layout(self._h, perm.ctypes.data, ctypes.byref(hubs), _stream_handle(stream)),
+               "atos_debug_spread_layout")
+        return perm[:n.value], hubs.value
 
     def scratch_check(self):
         """(set queued bits, occupied ring slots) after the last run; both 0 after a clean run."""

@@ -23,11 +23,12 @@ cudaError_t pr_verify_sweep(Instance* d_insts, int ninst, int max_n, DevCtl* d_c
 cudaError_t pr_finish(Instance* d_insts, int ninst, int n, int64_t nnz, DevCtl* d_ctl, double* certificate_y,
                       double exact_sum, cudaStream_t s);
 cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s);
-uint64_t spread_multiplier(int32_t n);
-cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, uint64_t a, uint64_t c, int32_t* perm,
-                         int32_t* new_rp, int32_t* new_col, int32_t* bsums, cudaStream_t s);
-cudaError_t unspread_f32(const float* src, float* dst, int32_t n, uint64_t a, uint64_t c, cudaStream_t s);
-cudaError_t unspread_i32(const int32_t* src, int32_t* dst, int32_t n, uint64_t a, uint64_t c, cudaStream_t s);
+size_t spread_build_scratch_bytes(int32_t n);
+cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, int32_t* perm, int32_t* new_rp,
+                         int32_t* new_col, int32_t* bsums, void* scratch, int32_t* h_hubs, HubMap* h_map,
+                         cudaStream_t s);
+cudaError_t unspread_f32(const float* src, float* dst, int32_t n, const int32_t* perm, cudaStream_t s);
+cudaError_t unspread_i32(const int32_t* src, int32_t* dst, int32_t n, const int32_t* perm, cudaStream_t s);
 unsigned long long launches_so_far();
 int bsp_pagerank(const int32_t* row_ptr, const int32_t* col, int32_t n, float alpha, float eps, float* rank,
                  float* res, void* scratch, size_t scratch_bytes, int32_t* hcount, cudaStream_t s,
@@ -113,15 +114,15 @@ struct atos_graph_s {
   double* d_cert = nullptr;  // PageRank FP64 certificate scratch (n entries)
   void* d_bsp = nullptr;  // BSP comparator frontiers and scan space
   size_t bsp_bytes = 0;
-  // the spread-id copy (ATOS_FLAG_SPREAD_IDS): CSR with vertex v renamed (sp_a v + sp_c) mod n,
-  // and an n-entry output buffer in the copy's ids
+  // the spread-id copy (ATOS_FLAG_SPREAD_IDS): CSR with vertex v renamed perm[v] (the
+  // highest-degree vertices first, the rest spread over the id range), and an n-entry output
+  // buffer in the copy's ids
   int32_t* sp_row_ptr = nullptr;
   int32_t* sp_col = nullptr;
-  int32_t* sp_perm = nullptr;  // v -> (sp_a v + sp_c) mod n
-  int32_t* sp_bsums = nullptr;
-  cudaEvent_t sp_ready = nullptr;  // recorded after the build
+  int32_t* sp_perm = nullptr;  // v -> the copy's id of v
   void* sp_out = nullptr;
-  uint64_t sp_a = 1, sp_c = 0;
+  int32_t sp_hubs = 0;         // hubs of the copy (its highest-degree vertices)
+  HubMap sp_hub = {0, 1, 1, 0};  // where they sit
   int32_t* d_expanded = nullptr;  // BFS: per source, the smallest depth each vertex was expanded at
   size_t expanded_rows = 0;
   unsigned long long* d_timeline = nullptr;  // throughput timeline (atos_timeline), 2 counters per bucket
@@ -131,34 +132,29 @@ struct atos_graph_s {
 
 namespace {
 
-// Builds the spread-id copy of g on `st` the first time it is needed.
+// Builds the spread-id copy of g on `st` the first time it is needed (the build synchronises
+// `st` once, to learn the size of the hub region).
 int ensure_spread(atos_graph_s* g, cudaStream_t st) {
-  if (g->sp_row_ptr) {
-    // built earlier, maybe on another stream: order this stream after the build
-    return from_cuda(cudaStreamWaitEvent(st, g->sp_ready, 0));
-  }
+  if (g->sp_row_ptr) return ATOS_OK;
   const int32_t n = g->n;
-  int32_t* bsums = nullptr;
-  int32_t *rp = nullptr, *col = nullptr, *perm = nullptr;
-  void* out = nullptr;
+  int32_t *bsums = nullptr, *rp = nullptr, *col = nullptr, *perm = nullptr;
+  void *out = nullptr, *tmp = nullptr;
   int rc = from_cuda(dev_alloc(&rp, (size_t)n + 1));
   if (!rc) rc = from_cuda(dev_alloc(&perm, (size_t)n));
   if (!rc) rc = from_cuda(dev_alloc(&col, (size_t)std::max<int64_t>(g->nnz, 1)));
   if (!rc) rc = from_cuda(dev_alloc(&bsums, (size_t)n / 1024 + 2));
-  if (!rc) rc = from_cuda(pool_malloc(&out, sizeof(int32_t) * (size_t)n));
-  const uint64_t sa = spread_multiplier(n), sc = (uint64_t)(n / 2);
-  if (!rc) rc = from_cuda(spread_build(g->row_ptr, g->col, n, sa, sc, perm, rp, col, bsums, st));
-  if (!rc && !g->sp_ready) rc = from_cuda(cudaEventCreateWithFlags(&g->sp_ready, cudaEventDisableTiming));
-  if (!rc) rc = from_cuda(cudaEventRecord(g->sp_ready, st));
+  if (!rc) rc = from_cuda(pool_malloc(&out, sizeof(int32_t) * std::max<size_t>((size_t)n, 1)));
+  if (!rc) rc = from_cuda(pool_malloc(&tmp, spread_build_scratch_bytes(n)));
+  int32_t hubs = 0;
+  HubMap hm = {0, 1, 1, 0};
+  if (!rc) rc = from_cuda(spread_build(g->row_ptr, g->col, n, perm, rp, col, bsums, tmp, &hubs, &hm, st));
+  cudaStreamSynchronize(st);  // the build's scratch goes back now; nothing of a failed build may still run
+  pool_free(tmp), pool_free(bsums);
   if (rc) {
-    cudaStreamSynchronize(st);  // nothing of a failed build may still run when its buffers go back
-    pool_free(rp), pool_free(col), pool_free(out), pool_free(perm), pool_free(bsums);
+    pool_free(rp), pool_free(col), pool_free(out), pool_free(perm);
     return rc;
   }
-  // stream-ordered: the build runs before the caller's kernels on `st`; the scan scratch stays
-  // with the graph (freed with it, after the device is idle)
-  g->sp_row_ptr = rp, g->sp_col = col, g->sp_out = out, g->sp_a = sa, g->sp_c = sc, g->sp_perm = perm;
-  g->sp_bsums = bsums;
+  g->sp_row_ptr = rp, g->sp_col = col, g->sp_out = out, g->sp_perm = perm, g->sp_hubs = hubs, g->sp_hub = hm;
   return ATOS_OK;
 }
 
@@ -383,15 +379,16 @@ Instance base_instance(atos_graph_s* g, int i, int app, uint32_t cap, uint32_t p
 
 namespace atos {
 // Device CSR of a graph, for the batch API.
-int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st, uint64_t* a,
-                     uint64_t* c) {
+int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st,
+                     const int32_t** perm, int32_t* hubs, HubMap* hub) {
   if (!g) return ATOS_ERR_INVALID_ARG;
   const int rc = ensure_spread(g, st);
   if (rc) return rc;
   *row_ptr = g->sp_row_ptr;
   *col = g->sp_col;
-  if (a) *a = g->sp_a;
-  if (c) *c = g->sp_c;
+  if (perm) *perm = g->sp_perm;
+  if (hubs) *hubs = g->sp_hubs;
+  if (hub) *hub = g->sp_hub;
   return ATOS_OK;
 }
 
@@ -591,10 +588,9 @@ int atos_graph_destroy(atos_graph_t g) {
   cudaDeviceSynchronize();
   if (g->owned) pool_free(g->row_ptr), pool_free(g->col);
   pool_free(g->d_res), pool_free(g->d_qbits), pool_free(g->d_bsp), pool_free(g->d_cert);
-  pool_free(g->sp_row_ptr), pool_free(g->sp_col), pool_free(g->sp_out), pool_free(g->sp_perm), pool_free(g->sp_bsums);
+  pool_free(g->sp_row_ptr), pool_free(g->sp_col), pool_free(g->sp_out), pool_free(g->sp_perm);
   pool_free(g->d_expanded);
   pool_free(g->d_timeline);
-  if (g->sp_ready) cudaEventDestroy(g->sp_ready);
   g->s.release();
   delete g;
   return ATOS_OK;
@@ -720,7 +716,7 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   }
   Instance I = base_instance(g, 0, kAppPr, cap, (uint32_t)n, -1);
   I.rank = spread ? (float*)g->sp_out : rank;
-  if (spread) I.row_ptr = g->sp_row_ptr, I.col = g->sp_col;
+  if (spread) I.row_ptr = g->sp_row_ptr, I.col = g->sp_col, I.hubs = g->sp_hubs, I.hub = g->sp_hub;
   I.res = g->d_res;
   I.qbits = g->d_qbits;
   I.alpha = alpha;
@@ -749,7 +745,7 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   }
   if (stats && !g->d_cert) ATOS_TRY(dev_alloc(&g->d_cert, (size_t)n));
   ATOS_TRY(pr_finish(g->s.d_insts, 1, n, g->nnz, g->s.d_ctl, stats ? g->d_cert : nullptr, exact_sum, st));
-  if (spread) ATOS_TRY(unspread_f32((const float*)g->sp_out, rank, n, g->sp_a, g->sp_c, st));
+  if (spread) ATOS_TRY(unspread_f32((const float*)g->sp_out, rank, n, g->sp_perm, st));
   ATOS_TRY(cudaEventRecord(g->s.ev1, st));
   if (stats) {
     rc = collect_stats(g, 1, st, stats);
@@ -803,7 +799,7 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
     I.n = n;
     I.color = out;
     ATOS_TRY(gc_finish(&I, g->s.d_ctl, st));
-    if (spread_bsp) ATOS_TRY(unspread_i32(out, colors, n, g->sp_a, g->sp_c, st));
+    if (spread_bsp) ATOS_TRY(unspread_i32(out, colors, n, g->sp_perm, st));
     ATOS_TRY(cudaEventRecord(g->s.ev1, st));
     if (stats || num_colors) {
       ATOS_TRY(cudaMemcpyAsync(g->s.h_ctl, g->s.d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
@@ -845,7 +841,7 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   rc = run_instances(g, 1, n, cfg, gc_persistent_kernel, gc_discrete_kernel, kAppGc, st, &iters);
   if (rc) return rc;
   ATOS_TRY(gc_finish(&I, g->s.d_ctl, st));
-  if (spread) ATOS_TRY(unspread_i32((const int32_t*)g->sp_out, colors, n, g->sp_a, g->sp_c, st));
+  if (spread) ATOS_TRY(unspread_i32((const int32_t*)g->sp_out, colors, n, g->sp_perm, st));
   ATOS_TRY(cudaEventRecord(g->s.ev1, st));
   if (stats || num_colors) {
     atos_stats local;
@@ -905,6 +901,23 @@ int atos_debug_queue_state(atos_graph_t g, int32_t ninst, uint64_t* words, uint3
 }
 
 uint64_t atos_kernel_launches(void) { return (uint64_t)launches_so_far(); }
+
+int atos_debug_spread_layout(atos_graph_t g, int32_t* perm, int32_t* hubs, void* stream) {
+  if (!g) return ATOS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (g->n == 0) {
+    if (hubs) *hubs = 0;
+    return ATOS_OK;
+  }
+  const int rc = ensure_spread(g, st);
+  if (rc) return rc;
+  if (perm) {
+    ATOS_TRY(cudaMemcpyAsync(perm, g->sp_perm, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, st));
+    ATOS_TRY(cudaStreamSynchronize(st));
+  }
+  if (hubs) *hubs = g->sp_hubs;
+  return ATOS_OK;
+}
 
 int atos_debug_scratch_check(atos_graph_t g, uint64_t* set_bits, uint64_t* busy_slots) {
   if (!g) return ATOS_ERR_INVALID_ARG;

@@ -26,9 +26,20 @@
 
 namespace atos {
 
+// Per-CTA shared state of the mixed body: a CTA runs one application's batch at a time, so the
+// colouring bitmaps and the PageRank hub accumulators share their space.
+template <int B>
+struct MixedExtra {
+  union {
+    unsigned bits[2 * B];
+    float hub[HubSlots<B>::value];
+  };
+};
+
 // Dispatches to the body of the instance's application (uniform across a CTA / warp).
 struct MixedBody {
-  using Extra = GcExtra;
+  template <int B>
+  using Extra = MixedExtra<B>;
   static constexpr int kResidentThreads = 1536;
 
   template <int BLOCK, class S>
@@ -275,8 +286,8 @@ int enqueue_run(atos_batch_s* b, cudaStream_t st) {
 extern "C" int atos_graph_info(atos_graph_t g, int32_t* n, int64_t* nnz, int32_t* max_degree);
 namespace atos {
 int graph_device_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, int32_t* n_isolated);
-int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st, uint64_t* a,
-                     uint64_t* c);
+int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st,
+                     const int32_t** perm, int32_t* hubs, HubMap* hub);
 }
 
 extern "C" {
@@ -396,9 +407,11 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
     graph_device_csr(graphs[q.graph], &rp, &col, &iso);
     SpreadJob job;
     memset(&job, 0, sizeof(job));
+    int32_t hubs = 0;
+    HubMap hub = {0, 1, 1, 0};
     if (spread && q.app != ATOS_APP_BFS) {
       // the spread-id copy of the graph (built on the legacy stream the first time; create is synchronous)
-      const int rc2 = graph_spread_csr(graphs[q.graph], &rp, &col, 0, &job.a, &job.c);
+      const int rc2 = graph_spread_csr(graphs[q.graph], &rp, &col, 0, &job.perm, &hubs, &hub);
       if (rc2) {
         delete b;
         return rc2;
@@ -426,6 +439,8 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
       I.prefix_len = (uint32_t)I.n;
       I.prefix_item = -1;
       I.rank = job.src ? (float*)job.src : (float*)q.out;
+      I.hubs = hubs;
+      I.hub = hub;
       I.res = b->d_res + res_off[i];
       I.qbits = b->d_qbits + bits_off[i];
       I.alpha = q.alpha;

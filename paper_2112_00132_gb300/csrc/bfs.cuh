@@ -8,6 +8,7 @@ namespace atos {
 constexpr int kMarkMinDegree = 16;  // ATOS_FLAG_BFS_EXPAND_ONCE: rows this long or longer are marked
 
 struct BfsBody {
+  template <int B>
   using Extra = NoExtra;
   static constexpr int kResidentThreads = 1536;
 

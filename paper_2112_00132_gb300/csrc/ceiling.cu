@@ -16,8 +16,8 @@
 
 namespace atos {
 int graph_device_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, int32_t* n_isolated);
-int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st, uint64_t* a,
-                     uint64_t* c);
+int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st,
+                     const int32_t** perm, int32_t* hubs, HubMap* hub);
 
 namespace {
 
@@ -54,7 +54,7 @@ extern "C" int atos_edge_ceiling(atos_graph_t g, int32_t kind, int32_t repeats, 
   int32_t iso = 0;
   cudaStream_t st = (cudaStream_t)stream;
   if (kind & ATOS_CEILING_SPREAD_IDS) {
-    const int rc0 = graph_spread_csr(g, &rp, &col, st, nullptr, nullptr);
+    const int rc0 = graph_spread_csr(g, &rp, &col, st, nullptr, nullptr, nullptr);
     if (rc0) return rc0;
   } else {
     graph_device_csr(g, &rp, &col, &iso);

@@ -25,10 +25,10 @@ namespace atos {
 
 constexpr int kGcWindow = 64;  // colours examined per pass: two 32-bit words per item
 
+template <int B>
 struct GcExtra {
-  unsigned bits[2 * 1024];  // per item: forbidden colours [base, base + 64) (assign) or
-                            // (own colour, conflict flag) (check)
-  int pass_base;
+  unsigned bits[2 * B];  // per item: forbidden colours [base, base + 64) (assign) or
+                         // (own colour, conflict flag) (check)
 };
 
 // Queues an assign task for u unless one is already queued.
@@ -38,7 +38,8 @@ __device__ __forceinline__ bool gc_claim_assign(const Instance& I, int u) {
 }
 
 struct GcBody {
-  using Extra = GcExtra;
+  template <int B>
+  using Extra = GcExtra<B>;
   static constexpr int kResidentThreads = 1536;
 
   template <int BLOCK, class S>

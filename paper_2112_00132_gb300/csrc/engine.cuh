@@ -33,6 +33,27 @@ constexpr unsigned long long kFreeSlot = ~0ull;  // a free ring slot (tag 0xffff
 constexpr int32_t kUnreached = INT32_MAX;
 
 enum : int32_t { kAppBfs = 0, kAppPr = 1, kAppGc = 2 };
+
+// Most hubs of the spread-id copy (the highest-degree vertices; PageRank CTAs combine their
+// batch's updates to them in shared memory).
+constexpr int kHubRegion = 16384;
+
+// Where the hubs of the spread-id copy sit: the hub of rank i has the id 32 line(i), the first
+// entry of a 128-byte line of every 4-byte state array, with line(i) = (mul i + add) mod 2^k
+// (mask = 2^k - 1, mul odd, inv = mul^-1 mod 2^32), so the hubs are spread over the first 2^k
+// lines and the rank of a line's hub is one multiplication away.
+struct HubMap {
+  uint32_t mask, mul, inv, add;
+  __host__ __device__ __forceinline__ int32_t id_of(uint32_t i) const { return (int32_t)(((mul * i + add) & mask) << 5); }
+  // Rank of the hub at id u, or a value >= 2^k (never a valid rank of fewer hubs) when no hub
+  // could sit at u.
+  __device__ __forceinline__ uint32_t rank_of(int32_t u) const {
+    const uint32_t l = (uint32_t)u >> 5;
+    if ((u & 31) || l > mask) return 0xffffffffu;
+    return (inv * (l - add)) & mask;
+  }
+};
+
 enum : int32_t { kStatTasks = 0, kStatEdges = 1, kStatPushes = 2, kStatIdle = 3, kStatBatches = 4, kNumStats = 5 };
 
 // Per-instance queue control block; each hot counter sits on its own 128-byte line.
@@ -65,7 +86,7 @@ struct Instance {
   uint32_t cap;          // ring slots (power of two)
   uint32_t prefix_len;   // items [0, prefix_len) are virtual
   int32_t prefix_item;   // >= 0: the single virtual item; < 0: virtual item i is vertex i
-  int32_t _pad0;
+  int32_t hubs;          // PageRank on the spread-id copy: hubs of rank < hubs sit where `hub` says
   QueueCtl* ctl;
   int32_t* depth;        // BFS
   float* rank;           // PageRank
@@ -83,6 +104,7 @@ struct Instance {
   double* cert_y;        // PageRank in batches and serving: FP64 scratch (n) of the output certificate
   int32_t* expanded;     // BFS (optional): the smallest depth at which each vertex has been expanded
   double exact_sum;      // PageRank: n - alpha * (isolated vertices), the fixed point's sum
+  HubMap hub;            // PageRank on the spread-id copy: the hubs' ids
 };
 
 struct Launch {
@@ -472,7 +494,7 @@ __device__ __forceinline__ void flush_stats(const Instance& I, unsigned long lon
 // ------------------------------------------------------------------------ CTA worker engine
 //
 // Body must provide:
-//   using Extra;                                  per-CTA shared state
+//   template <int B> using Extra;                 per-CTA shared state of a B-thread worker
 //   template <int B, class S> static void cta_batch(S& sm, int cnt, const Launch&, st);
 //       processes sm.items[0, cnt) of sm.I, pushes with cta_push / cta_maybe_flush and ends
 //       with cta_flush(sm, I, cnt, ...) so the batch is reported complete;
@@ -501,7 +523,7 @@ __device__ __forceinline__ void cta_orphan_pending(S& sm, bool pending, const La
 // Returns 1 when the worker paused (serving slice over), 0 when the instance ended for it
 // (terminated, or the launch failed).
 template <class Body, int BLOCK>
-__device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::Extra>& sm, const Launch& L,
+__device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::template Extra<BLOCK>>& sm, const Launch& L,
                                 unsigned long long* st, unsigned long long t0) {
   const Instance& I = sm.I;
   Waiter wait;
@@ -593,7 +615,7 @@ struct MinBlocks {
 
 template <class Body, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<Body, BLOCK>::value)) cta_persistent_kernel(Launch L) {
-  __shared__ CtaSmem<BLOCK, typename Body::Extra> sm;
+  __shared__ CtaSmem<BLOCK, typename Body::template Extra<BLOCK>> sm;
   unsigned long long st[kNumStats] = {};
   const unsigned long long t0 = globaltimer();
   int inst = (int)(blockIdx.x % (unsigned)min(L.window, L.ninst));
@@ -626,7 +648,7 @@ __global__ void __launch_bounds__(BLOCK, (MinBlocks<Body, BLOCK>::value)) cta_pe
 // blockIdx.y selects the instance, blockIdx.x a FETCH-sized slice.  Items are already written.
 template <class Body, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) cta_discrete_kernel(Launch L) {
-  __shared__ CtaSmem<BLOCK, typename Body::Extra> sm;
+  __shared__ CtaSmem<BLOCK, typename Body::template Extra<BLOCK>> sm;
   unsigned long long st[kNumStats] = {};
   const int inst = blockIdx.y;
   if (threadIdx.x == 0) {

@@ -29,8 +29,8 @@
 namespace atos {
 const void* mixed_persistent_kernel(int worker);
 int graph_device_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, int32_t* n_isolated);
-int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st, uint64_t* a,
-                     uint64_t* c);
+int graph_spread_csr(atos_graph_t g, const int32_t** row_ptr, const int32_t** col, cudaStream_t st,
+                     const int32_t** perm, int32_t* hubs, HubMap* hub);
 cudaError_t batch_finish_terminated(const Instance* d_insts, int ninst, int max_n, void* d_results, cudaStream_t s);
 size_t batch_result_bytes();
 void batch_result_read(const void* h_result, double* sum_rank, double* sum_res, int* num_colors);
@@ -330,9 +330,11 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
   graph_device_csr(s->graphs[q->graph], &rp, &col, &iso);
   SpreadJob job;
   memset(&job, 0, sizeof(job));
+  int32_t hubs = 0;
+  HubMap hub = {0, 1, 1, 0};
   if (q->app != ATOS_APP_BFS && (s->cfg.flags & ATOS_FLAG_SPREAD_IDS)) {
     // the graph's spread-id copy (built the first time, synchronising the server stream)
-    const int rc2 = graph_spread_csr(s->graphs[q->graph], &rp, &col, s->stream, &job.a, &job.c);
+    const int rc2 = graph_spread_csr(s->graphs[q->graph], &rp, &col, s->stream, &job.perm, &hubs, &hub);
     if (rc2) {
       s->arena.release(off, bytes);
       return rc2;
@@ -366,6 +368,8 @@ int atos_server_submit(atos_server_t s, const atos_instance* q, int64_t* id) {
     I.prefix_len = (uint32_t)n;
     I.prefix_item = -1;
     I.rank = job.src ? (float*)job.src : (float*)q->out;
+    I.hubs = hubs;
+    I.hub = hub;
     I.res = (float*)take((size_t)n * 4);
     I.cert_y = (double*)take((size_t)n * 8);
     I.exact_sum = (double)n - (double)q->alpha * iso;

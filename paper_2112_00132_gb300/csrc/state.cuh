@@ -30,13 +30,13 @@ cudaError_t launch_next_generation(Instance* d_insts, int ninst, DevCtl* d_ctl, 
 cudaError_t launch_finalize(const Instance* d_insts, int ninst, DevCtl* d_ctl, cudaStream_t s);
 
 // Results computed on the spread-id copy of a graph, to be returned in the caller's ids:
-// dst[v] = src[(a v + c) mod n] for 4-byte elements.
+// dst[v] = src[perm[v]] for 4-byte elements (perm: the copy's id of each vertex).
 struct SpreadJob {
   const void* src;
   void* dst;
   int32_t n;
   int32_t pad;
-  uint64_t a, c;
+  const int32_t* perm;
 };
 cudaError_t unspread_jobs(const SpreadJob* d_jobs, int njobs, int max_n, cudaStream_t s);
 

@@ -240,6 +240,78 @@ def test_spread_ids_all_configs(atos, graphs, gname):
                 assert G.scratch_check() == (0, 0), f"{gname}/{cname}: {G.scratch_check()}"
 
 
+def _degree_class(d):
+    """Four classes per power of two: 0 for isolated vertices, else 1 + 4 floor(log2 d) + the two
+    bits below d's leading one."""
+    if d <= 0:
+        return 0
+    lg = int(d).bit_length() - 1
+    sub = (d >> (lg - 2)) & 3 if lg >= 2 else (d << (2 - lg)) & 3
+    return 1 + 4 * lg + sub
+
+
+@pytest.mark.parametrize("maker", [lambda: gg.rmat(12, 16, seed=1), lambda: gg.rmat(16, 16, seed=2),
+                                   lambda: gg.rmat(11, 16, seed=7, delete_frac=0.1),
+                                   lambda: gg.grid(97, 61, delete_frac=0.1, seed=3), lambda: gg.star(1000),
+                                   lambda: gg.from_edges(70, [(0, 1)], "edge_and_isolated")])
+def test_spread_layout_hub_region(atos, maker):
+    """The spread-id copy's layout: a bijection; the H hubs are the largest degree classes, whole,
+    as many as fit in min(16384, 2^k) (2^k the largest power of two <= n / 32), and the hub of
+    rank i (largest class first, ids increasing within a class) has the id 32 ((mul i + add) mod
+    2^k) for one odd mul: at most one hub per 128-byte line."""
+    g = maker()
+    with atos.Graph.from_csr(g) as G:
+        perm, H = G.spread_layout()
+    assert np.array_equal(np.sort(perm), np.arange(g.n)), "not a permutation"
+    lines = 0
+    if g.n >= 32:
+        lines = 1
+        while lines * 2 <= g.n // 32:
+            lines *= 2
+    cap = min(16384, lines)
+    assert 0 <= H <= cap
+    cls = np.array([_degree_class(int(d)) for d in g.degrees])
+    # the hubs by rank, from the degree classes alone
+    order = sorted((v for v in range(g.n) if cls[v] > 0), key=lambda v: (-cls[v], v))
+    hv = np.array(order[:H], dtype=np.int64)
+    if H:
+        bmin = cls[hv].min()
+        assert H == np.count_nonzero(cls >= bmin), "hubs are not whole degree classes"
+    rest = cls[(cls > 0)]
+    if H < rest.size:  # the next class down did not fit
+        nxt = cls[order[H]]
+        assert H + np.count_nonzero(cls == nxt) > cap
+    ids = perm[hv]
+    assert np.all(ids % 32 == 0) and np.all(ids < 32 * max(lines, 1))
+    if H >= 2:
+        add = ids[0] // 32
+        mul = (ids[1] // 32 - add) % lines
+        assert mul % 2 == 1
+        want = 32 * ((mul * np.arange(H, dtype=np.int64) + add) % lines)
+        assert np.array_equal(ids, want), "hub ids do not follow one odd multiplier"
+    # no other vertex shares a line with a hub at its first entry
+    assert len(set((ids // 32).tolist())) == H
+
+
+@pytest.mark.parametrize("worker", [64, 256, 512, 1024])
+def test_pagerank_hub_combining_rmat16(atos, worker):
+    """RMAT 16 on the spread layout: its hubs (up to 2048) outnumber the shared-memory accumulators
+    of the 64-thread CTA worker and fit those of the larger ones; the result matches the oracle
+    either way."""
+    g = gg.rmat(16, 16, seed=2)
+    ref = pr_reference(g)
+    cfg = atos.queue_config(worker_size=worker, fetch_size=worker, check_size=8, flags=atos.FLAG_SPREAD_IDS)
+    with atos.Graph.from_csr(g) as G:
+        _, H = G.spread_layout()
+        assert H > 512
+        rank, st = G.pagerank(ALPHA, EPS, cfg=cfg)
+        assert G.scratch_check() == (0, 0)
+    q = rank.cpu().numpy().astype(np.float64)
+    l1 = np.abs(q - ref).sum()
+    assert st.status == 0 and l1 <= PR_L1_TOL, f"L1 {l1}"
+    assert l1 <= st.error_bound * 1.0001 + 1e-12
+
+
 def test_spread_ids_full_size_rmat22(atos):
     g = gg.rmat(22, 16, seed=1)
     cfg = atos.queue_config(worker_size=1024, fetch_size=1024, check_size=8, flags=atos.FLAG_SPREAD_IDS)
