@@ -106,6 +106,16 @@ extern "C" {
                                      asynchronous BFS's re-expansions on scale-free graphs, at one
                                      atomic per task (n int32 per source of scratch). */
 
+#define ATOS_FLAG_BSP_DEVICE_LOOP 64u /* ATOS_BSP: the level loop runs on the device: each level's
+                                     kernels are the body of a CUDA graph whose conditional WHILE node
+                                     repeats them until the next frontier is empty (one graph launch
+                                     per call, no host synchronisation per level).  Without it the host
+                                     reads the next frontier's size after every level. */
+
+#define ATOS_FLAG_BSP_PER_SOURCE 128u /* ATOS_BSP BFS: one source after another.  Without it the
+                                     frontiers of all sources advance together, one launch of each
+                                     level kernel per level for all of them. */
+
 typedef struct atos_config {
   int32_t worker_size;    /* 1 (thread worker, BFS only), 32 (warp worker) or a CTA worker of 64,
                              128, 256, 512 or 1024 threads */
@@ -185,7 +195,8 @@ int atos_graph_destroy(atos_graph_t g);
 int atos_graph_info(atos_graph_t g, int32_t* n, int64_t* nnz, int32_t* max_degree);
 
 /* Breadth-first search from each of nsrc sources (Section 5.1; Algorithm 2 when the strategy is
- * persistent or discrete, Algorithm 1 for ATOS_BSP).  sources: HOST array of nsrc vertex ids in
+ * persistent or discrete, Algorithm 1 for ATOS_BSP, whose levels cover every source's frontier
+ * at once unless ATOS_FLAG_BSP_PER_SOURCE).  sources: HOST array of nsrc vertex ids in
  * [0, n).  depths: DEVICE int32 array of nsrc * n entries, row s = hop distances from
  * sources[s], INT32_MAX for vertices outside the source's component.  All nsrc searches run in
  * one launch with one worklist each (cfg->window of them active at a time).  Errors:

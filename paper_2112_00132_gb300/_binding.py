@@ -38,6 +38,8 @@ FLAG_SPREAD_IDS = 4
 FLAG_USE_TUNED = 8
 FLAG_GC_ORDERED = 16
 FLAG_BFS_EXPAND_ONCE = 32
+FLAG_BSP_DEVICE_LOOP = 64
+FLAG_BSP_PER_SOURCE = 128
 DEVICE_PTRS, BORROW, CHECK_SYMMETRIC, SKIP_VALIDATION = 1, 2, 4, 8
 UNREACHED = 2**31 - 1
 

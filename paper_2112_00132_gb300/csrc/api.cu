@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "atos.h"
+#include "bsp.cuh"
 #include "engine.cuh"
 #include "launch.cuh"
 #include "state.cuh"
@@ -30,14 +31,6 @@ cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, int32
 cudaError_t unspread_f32(const float* src, float* dst, int32_t n, const int32_t* perm, cudaStream_t s);
 cudaError_t unspread_i32(const int32_t* src, int32_t* dst, int32_t n, const int32_t* perm, cudaStream_t s);
 unsigned long long launches_so_far();
-int bsp_pagerank(const int32_t* row_ptr, const int32_t* col, int32_t n, float alpha, float eps, float* rank,
-                 float* res, void* scratch, size_t scratch_bytes, int32_t* hcount, cudaStream_t s,
-                 int64_t* iterations, int64_t* edges, int64_t* tasks);
-int bsp_color(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t* color, void* scratch,
-              size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges,
-              int64_t* tasks);
-int bsp_bfs(const int32_t* row_ptr, const int32_t* col, int32_t n, int32_t src, int32_t* depth, void* scratch,
-            size_t scratch_bytes, int32_t* hcount, cudaStream_t s, int64_t* iterations, int64_t* edges);
 }  // namespace atos
 
 using namespace atos;
@@ -112,8 +105,10 @@ struct atos_graph_s {
   float* d_res = nullptr;
   uint32_t* d_qbits = nullptr;
   double* d_cert = nullptr;  // PageRank FP64 certificate scratch (n entries)
-  void* d_bsp = nullptr;  // BSP comparator frontiers and scan space
+  void* d_bsp = nullptr;  // BSP comparator frontiers, scan space and control block
   size_t bsp_bytes = 0;
+  void* h_bsp = nullptr;  // pinned: the BSP control block's upload image and read-back
+  BspGraphs bsp_graphs;   // the device-loop graphs of the BSP comparator
   // the spread-id copy (ATOS_FLAG_SPREAD_IDS): CSR with vertex v renamed perm[v] (the
   // highest-degree vertices first, the rest spread over the id range), and an n-entry output
   // buffer in the copy's ids
@@ -204,14 +199,16 @@ int ensure_scratch(atos_graph_s* g, int ninst, uint32_t cap) {
 // Ring slots per instance.  Besides the tasks in flight the ring must cover the span between the
 // oldest ticket a busy worker has not taken yet and the tail, so small graphs get a floor of 2^20
 // slots (8 MiB); large ones 1.5 n plus the virtual prefix.
-// BSP comparator scratch: frontiers, scan offsets and per-item values, grown on demand.
+// BSP comparator scratch: frontiers, scan offsets, control block, grown on demand.
 int ensure_bsp(atos_graph_s* g, size_t bytes) {
   if (!g->s.ev0) {
     int rc = ensure_scratch(g, 1, 1024);
     if (rc) return rc;
   }
+  if (!g->h_bsp) ATOS_TRY(pool_malloc_host(&g->h_bsp, bsp_host_bytes()));
   if (g->bsp_bytes >= bytes) return ATOS_OK;
   cudaDeviceSynchronize();
+  g->bsp_graphs.release();  // the graphs name the old control block
   pool_free(g->d_bsp);
   g->d_bsp = nullptr;
   g->bsp_bytes = 0;
@@ -220,7 +217,19 @@ int ensure_bsp(atos_graph_s* g, size_t bytes) {
   return ATOS_OK;
 }
 
-size_t bsp_bytes_for(int32_t n) { return sizeof(int32_t) * (4 * (size_t)n + (size_t)n / 1024 + 4096); }
+// One BSP run on g's comparator scratch; accumulates into *acc.
+int run_bsp(atos_graph_s* g, const BspRun& r, cudaStream_t st, BspResult* acc) {
+  int rc = ensure_bsp(g, bsp_scratch_bytes(r.app, r.n, r.nsrc));
+  if (rc) return rc;
+  BspResult one = {};
+  rc = bsp_run(r, g->d_bsp, g->bsp_bytes, g->h_bsp, &g->bsp_graphs, st, acc ? &one : nullptr);
+  if (rc) return rc;
+  if (acc) {
+    acc->iters += one.iters, acc->edges += one.edges, acc->tasks += one.tasks;
+    if (!acc->status) acc->status = one.status;
+  }
+  return ATOS_OK;
+}
 
 uint32_t ring_capacity(const atos_config& cfg, int32_t n, uint32_t prefix) {
   if (cfg.queue_capacity > 0) return next_pow2(std::max<uint64_t>((uint64_t)cfg.queue_capacity, 1024));
@@ -245,7 +254,8 @@ int check_config(const atos_config& c) {
   if (c.num_blocks < 0 || c.check_size < 0 || c.window < 0 || c.queue_capacity < 0 || c.spin_limit_ns < 0)
     return ATOS_ERR_INVALID_ARG;
   if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS | ATOS_FLAG_USE_TUNED |
-                  ATOS_FLAG_GC_ORDERED | ATOS_FLAG_BFS_EXPAND_ONCE))
+                  ATOS_FLAG_GC_ORDERED | ATOS_FLAG_BFS_EXPAND_ONCE | ATOS_FLAG_BSP_DEVICE_LOOP |
+                  ATOS_FLAG_BSP_PER_SOURCE))
     return ATOS_ERR_INVALID_ARG;
   return ATOS_OK;
 }
@@ -587,7 +597,9 @@ int atos_graph_destroy(atos_graph_t g) {
   if (!g) return ATOS_OK;
   cudaDeviceSynchronize();
   if (g->owned) pool_free(g->row_ptr), pool_free(g->col);
+  g->bsp_graphs.release();
   pool_free(g->d_res), pool_free(g->d_qbits), pool_free(g->d_bsp), pool_free(g->d_cert);
+  pool_free_host(g->h_bsp);
   pool_free(g->sp_row_ptr), pool_free(g->sp_col), pool_free(g->sp_out), pool_free(g->sp_perm);
   pool_free(g->d_expanded);
   pool_free(g->d_timeline);
@@ -618,19 +630,25 @@ int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* dept
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = g->n;
   if (cfg.strategy == ATOS_BSP) {
-    rc = ensure_bsp(g, bsp_bytes_for(g->n));
-    if (rc) return rc;
+    // Algorithm 1: every source's frontier advances in the same launches, one level at a time
+    // (or one source after another with ATOS_FLAG_BSP_PER_SOURCE)
     rc = clear_timeline(g, st);
     if (rc) return rc;
+    const bool per_source = (cfg.flags & ATOS_FLAG_BSP_PER_SOURCE) != 0;
+    BspRun r = {};
+    r.app = kAppBfs;
+    r.row_ptr = g->row_ptr, r.col = g->col, r.n = g->n;
+    r.device_loop = (cfg.flags & ATOS_FLAG_BSP_DEVICE_LOOP) != 0;
+    rc = ensure_bsp(g, bsp_scratch_bytes(kAppBfs, g->n, per_source ? 1 : nsrc));
+    if (rc) return rc;
     ATOS_TRY(cudaEventRecord(g->s.ev0, st));
-    int64_t iters = 0, edges = 0;
-    for (int32_t i = 0; i < nsrc; ++i) {
-      int64_t it = 0, ed = 0;
-      rc = bsp_bfs(g->row_ptr, g->col, g->n, sources[i], depths + (size_t)i * n, g->d_bsp, g->bsp_bytes,
-                   (int32_t*)&g->s.h_ctl->maxgen, st, &it, &ed);
+    BspResult acc = {};
+    for (int32_t i = 0; i < nsrc; i += per_source ? 1 : nsrc) {
+      r.sources = sources + i;
+      r.nsrc = per_source ? 1 : nsrc;
+      r.depth = depths + (size_t)i * n;
+      rc = run_bsp(g, r, st, stats ? &acc : nullptr);
       if (rc) return rc;
-      iters += it;
-      edges += ed;
     }
     ATOS_TRY(cudaEventRecord(g->s.ev1, st));
     if (stats) {
@@ -639,9 +657,12 @@ int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* dept
       float ms = 0.f;
       cudaEventElapsedTime(&ms, g->s.ev0, g->s.ev1);
       stats->ms = ms;
-      stats->iterations = iters;
-      stats->edges = edges;
-      stats->status = ATOS_OK;
+      stats->iterations = acc.iters;
+      stats->edges = acc.edges;
+      stats->tasks = acc.tasks;
+      stats->pushes = acc.tasks;
+      stats->status = acc.status;
+      return acc.status;
     }
     return ATOS_OK;
   }
@@ -700,7 +721,7 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   const bool bsp = cfg.strategy == ATOS_BSP;
   if (bsp) {
     cfg.strategy = ATOS_PERSISTENT;  // the prepare step below is shared; the loop is not run
-    rc = ensure_bsp(g, bsp_bytes_for(n));
+    rc = ensure_bsp(g, bsp_scratch_bytes(kAppPr, n, 1));
     if (rc) return rc;
   }
   const uint32_t cap = ring_capacity(cfg, n, (uint32_t)n);
@@ -727,7 +748,8 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   cfg.window = 1;
   const double exact_sum = (double)n - (double)alpha * (double)g->n_isolated;
   ATOS_TRY(cudaEventRecord(g->s.ev0, st));
-  int64_t iters = 0, bsp_edges = 0, bsp_tasks = 0;
+  int64_t iters = 0;
+  BspResult bsp_acc = {};
   if (bsp) {
     // Algorithm 3: same initial state (prepare + initial residue), then level-synchronous sweeps
     rc = clear_timeline(g, st);
@@ -736,9 +758,14 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
     if (rc) return rc;
     ATOS_TRY(launch_prepare(g->s.d_insts, 1, n, g->s.d_ctl, 0u, 1u, st));
     ATOS_TRY(launch_pr_init(g->s.d_insts, 1, g->nnz, st));
-    rc = bsp_pagerank(I.row_ptr, I.col, n, alpha, eps, I.rank, g->d_res, g->d_bsp, g->bsp_bytes,
-                      (int32_t*)&g->s.h_ctl->maxgen, st, &iters, &bsp_edges, &bsp_tasks);
+    BspRun r = {};
+    r.app = kAppPr;
+    r.row_ptr = I.row_ptr, r.col = I.col, r.n = n;
+    r.rank = I.rank, r.res = g->d_res, r.alpha = alpha, r.eps = eps;
+    r.device_loop = (cfg.flags & ATOS_FLAG_BSP_DEVICE_LOOP) != 0;
+    rc = run_bsp(g, r, st, stats ? &bsp_acc : nullptr);
     if (rc) return rc;
+    iters = bsp_acc.iters;
   } else {
     rc = run_instances(g, 1, n, cfg, pr_persistent_kernel, pr_discrete_kernel, kAppPr, st, &iters);
     if (rc) return rc;
@@ -752,9 +779,10 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
     if (rc) return rc;
     stats->iterations = iters;
     if (bsp) {
-      stats->tasks = bsp_tasks;
-      stats->edges = bsp_edges;
-      stats->pushes = bsp_tasks;
+      stats->tasks = bsp_acc.tasks;
+      stats->edges = bsp_acc.edges;
+      stats->pushes = bsp_acc.tasks;
+      if (!stats->status) stats->status = bsp_acc.status;
     }
     stats->residual_l1 = g->s.h_ctl->sum_res;
     const double denom = (1.0 - (double)alpha) * exact_sum;
@@ -779,7 +807,7 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   cudaStream_t st = (cudaStream_t)stream;
   const int32_t n = g->n;
   if (cfg.strategy == ATOS_BSP) {
-    rc = ensure_bsp(g, bsp_bytes_for(n));
+    rc = ensure_bsp(g, bsp_scratch_bytes(kAppGc, n, 1));
     if (rc) return rc;
     const bool spread_bsp = (cfg.flags & ATOS_FLAG_SPREAD_IDS) != 0;
     if (spread_bsp) {
@@ -790,9 +818,13 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
     rc = clear_timeline(g, st);
     if (rc) return rc;
     ATOS_TRY(cudaEventRecord(g->s.ev0, st));
-    int64_t iters = 0, edges = 0, tasks = 0;
-    rc = bsp_color(spread_bsp ? g->sp_row_ptr : g->row_ptr, spread_bsp ? g->sp_col : g->col, n, out, g->d_bsp,
-                   g->bsp_bytes, (int32_t*)&g->s.h_ctl->maxgen, st, &iters, &edges, &tasks);
+    BspRun r = {};
+    r.app = kAppGc;
+    r.row_ptr = spread_bsp ? g->sp_row_ptr : g->row_ptr, r.col = spread_bsp ? g->sp_col : g->col, r.n = n;
+    r.color = out;
+    r.device_loop = (cfg.flags & ATOS_FLAG_BSP_DEVICE_LOOP) != 0;
+    BspResult acc = {};
+    rc = run_bsp(g, r, st, (stats || num_colors) ? &acc : nullptr);
     if (rc) return rc;
     Instance I;
     memset(&I, 0, sizeof(I));
@@ -809,12 +841,12 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
         float ms = 0.f;
         cudaEventElapsedTime(&ms, g->s.ev0, g->s.ev1);
         stats->ms = ms;
-        stats->iterations = iters;
-        stats->edges = edges;
-        stats->tasks = tasks;
-        stats->pushes = tasks;
+        stats->iterations = acc.iters;
+        stats->edges = acc.edges;
+        stats->tasks = acc.tasks;
+        stats->pushes = acc.tasks;
         stats->num_colors = g->s.h_ctl->num_colors;
-        stats->status = ATOS_OK;
+        stats->status = acc.status;
       }
     }
     return ATOS_OK;

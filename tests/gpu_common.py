@@ -59,4 +59,6 @@ def configs(atos):
         "discrete-cta64": q("discrete-cta", worker_size=64, fetch_size=32),
         "discrete-warp": q("discrete-warp"),
         "bsp": q("bsp"),
+        "bsp-device-loop": q("bsp", flags=atos.FLAG_BSP_DEVICE_LOOP),
+        "bsp-per-source": q("bsp", flags=atos.FLAG_BSP_PER_SOURCE),
     }

@@ -156,6 +156,54 @@ def test_bfs_full_size_rmat22_64_sources(atos):
         assert oracle.bfs_certificate(g, srcs[i], d[i]) == (0, -1), f"source {srcs[i]}"
 
 
+@pytest.mark.parametrize("flags", ["host", "device_loop", "per_source", "per_source_device_loop"])
+def test_bfs_bsp_forms_many_sources(atos, flags):
+    """The level-synchronous comparator (Algorithm 1) over 40 sources: every source's frontier in
+    one launch per level (or one source after another), levels driven by the host or by a CUDA
+    graph's conditional loop; bit-exact, with no overwork (each reached vertex expanded once per
+    source) and one level per depth."""
+    f = {"host": 0, "device_loop": atos.FLAG_BSP_DEVICE_LOOP, "per_source": atos.FLAG_BSP_PER_SOURCE,
+         "per_source_device_loop": atos.FLAG_BSP_PER_SOURCE | atos.FLAG_BSP_DEVICE_LOOP}[flags]
+    g = gg.rmat(12, 16, seed=1, delete_frac=0.1)
+    srcs = [int(x) for x in gg.sources(g, 40, seed=2)] + [0]
+    refs = np.stack([oracle.bfs(g, s) for s in srcs])
+    reached = (refs != oracle.UNREACHED)
+    ecc = np.where(reached, refs, 0).max(axis=1)
+    with atos.Graph.from_csr(g) as G:
+        for _ in range(2):  # a second run reuses the scratch (and the graph of the device loop)
+            depths, st = G.bfs(srcs, cfg=atos.queue_config("bsp", flags=f))
+            assert st.status == 0
+            assert np.array_equal(depths.cpu().numpy(), refs)
+            assert st.tasks == int(reached.sum())
+            levels = int((ecc + 1).sum()) if f & atos.FLAG_BSP_PER_SOURCE else int(ecc.max() + 1)
+            assert st.iterations == levels
+
+
+def test_bfs_bsp_full_size(atos):
+    """Full-size level-synchronous BFS: the 2048 x 2048 grid from the corner (thousands of
+    levels, host-driven and in the device loop) bit-exact, and RMAT 22 with all 64 sources in one
+    device-loop run (levels of more than 2^31 edges), sampled sources bit-exact and every fourth by
+    the hop-distance certificate."""
+    g = gg.grid(2048, delete_frac=0.1, seed=1)
+    ref = oracle.bfs(g, 0)
+    ecc = int(ref[ref != oracle.UNREACHED].max())
+    with atos.Graph.from_csr(g) as G:
+        for f in (0, atos.FLAG_BSP_DEVICE_LOOP):
+            depths, st = G.bfs([0], cfg=atos.queue_config("bsp", flags=f))
+            assert st.status == 0 and st.iterations == ecc + 1
+            assert np.array_equal(depths.cpu().numpy()[0], ref)
+    g = gg.rmat(22, 16, seed=1)
+    srcs = [int(x) for x in gg.sources(g, 64, seed=1)]
+    with atos.Graph.from_csr(g) as G:
+        depths, st = G.bfs(srcs, cfg=atos.queue_config("bsp", flags=atos.FLAG_BSP_DEVICE_LOOP))
+        assert st.status == 0
+        d = depths.cpu().numpy()
+    for i in (0, 37, 63):
+        assert np.array_equal(d[i], oracle.bfs(g, srcs[i])), f"source {srcs[i]}"
+    for i in range(0, 64, 4):
+        assert oracle.bfs_certificate(g, srcs[i], d[i]) == (0, -1), f"source {srcs[i]}"
+
+
 def test_bfs_expand_once_all_configs(atos):
     """ATOS_FLAG_BFS_EXPAND_ONCE: bit-exact depths for every configuration (BSP ignores the flag)."""
     for g in (gg.rmat(12, 16, seed=1), gg.grid(97, 61, delete_frac=0.1, seed=3), gg.rmat(11, 16, seed=7, delete_frac=0.1)):

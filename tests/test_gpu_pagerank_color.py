@@ -179,7 +179,7 @@ def test_pagerank_crossing_all_configs(atos, graphs, gname):
             l1 = np.abs(q - ref).sum()
             assert st.status == 0 and l1 <= PR_L1_TOL, f"{gname}/{cname}: L1 {l1}"
             assert l1 <= st.error_bound * 1.0001 + 1e-12, f"{gname}/{cname}: L1 {l1} > bound {st.error_bound}"
-            if cname != "bsp":  # the level-synchronous form uses neither the ring nor the queued bits
+            if not cname.startswith("bsp"):  # the level-synchronous form uses neither the ring nor the queued bits
                 assert G.scratch_check() == (0, 0), f"{gname}/{cname}: {G.scratch_check()}"
 
 
@@ -236,7 +236,7 @@ def test_spread_ids_all_configs(atos, graphs, gname):
             colors, k, st = G.color(cfg=cfg)
             code, bad, kk = oracle.check_coloring(g, colors.cpu().numpy())
             assert st.status == 0 and code == 0 and k == kk, f"{gname}/{cname}: code {code} vertex {bad}"
-            if cname != "bsp":
+            if not cname.startswith("bsp"):
                 assert G.scratch_check() == (0, 0), f"{gname}/{cname}: {G.scratch_check()}"
 
 
@@ -360,7 +360,7 @@ def test_color_ordered_all_configs(atos, graphs, gname):
                 colors, k, st = G.color(cfg=cfg)
                 code, bad, kk = oracle.check_coloring(g, colors.cpu().numpy())
                 assert st.status == 0 and code == 0 and k == kk, f"{gname}/{cname}/{extra}: code {code} vertex {bad}"
-                if gname == "rmat12" and not extra and cname != "bsp":
+                if gname == "rmat12" and not extra and not cname.startswith("bsp"):
                     assert k <= greedy + 4, f"{cname}: {k} colours, serial greedy {greedy}"
 
 
