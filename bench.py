@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--flags", type=int, default=0, help="with --no-tune: atos_config.flags of PageRank and colouring")
     ap.add_argument("--policy", type=int, default=2, help="with --no-tune: PageRank's fetch policy (0 fixed, 1 greedy, 2 spread)")
     ap.add_argument("--no-compare", action="store_true", help="skip the BSP / unbatched comparisons")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads measured beside the main step (2048^2 grid, batched mix, "
+                         "serving window)")
     ap.add_argument("--study", default=None, choices=["color-ids"],
                     help="color-ids: colouring on the input ids, the spread ids and a random relabelling, for "
                          "several worker shapes and BSP (Section 6.4's permutation experiment); prints one JSON "
@@ -366,56 +369,14 @@ def run_atos(args, rank: int, world: int):
                 "fetch_policy": c.fetch_policy, "window": c.window, "check_size": c.check_size, "flags": c.flags}
 
     # comparators (untimed by the step, timed here with the same events): the level-synchronous
-    # BSP form and the unbatched single-query form of the same work
+    # BSP forms (host-driven levels, levels in a device-side graph loop; BFS one source at a time
+    # and all 64 at once) and the unbatched single-query form of the same work
     comparisons = {}
     if not args.no_compare:
-        def timed(fn):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            fn()
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            return a.elapsed_time(b)
-        bsp = atos.queue_config("bsp")
-        # the BSP PageRank and colouring at their better layout (input or spread ids), each timed
-        def best_layout(run):
-            cands = [atos.queue_config("bsp"), atos.queue_config("bsp", flags=atos.FLAG_SPREAD_IDS)]
-            return min(cands, key=lambda c: timed(lambda: run(c)))
-        bsp_pr = best_layout(lambda c: G.pagerank(ALPHA, EPS, rank_t, cfg=c, stream=stream, stats=False))
-        bsp_gc = best_layout(lambda c: G.color(colors, cfg=c, stream=stream, stats=False))
-        comparisons["bfs64_bsp_ms"] = round(timed(lambda: G.bfs(srcs, depths, cfg=bsp, stream=stream,
-                                                                  stats=False)), 3)
-        # work of the level-synchronous forms (neighbour entries read), for the workload ratio
-        # of Table 4: persistent work / BSP work
-        _, bsp_bfs = G.bfs(srcs, depths, cfg=bsp, stream=stream)
-        _, bsp_pr_st = G.pagerank(ALPHA, EPS, rank_t, cfg=bsp_pr, stream=stream)
-        _, _, bsp_gc_st = G.color(colors, cfg=bsp_gc, stream=stream)
-        comparisons["workload_ratio"] = {
-            "bfs": round(bfs_stats.edges / max(1, bsp_bfs.edges), 3),
-            "pagerank": round(pr_edges / max(1, bsp_pr_st.edges), 3),
-            "color": round(gc_edges / max(1, bsp_gc_st.edges), 3),
-            "note": "neighbour entries read by the persistent path / by the BSP path (Table 4's ratio)"}
-        one = torch.empty((1, g.n), dtype=torch.int32, device="cuda")
-
-        def unbatched():
-            for s0 in srcs:
-                G.bfs([int(s0)], one, cfg=cfg_bfs, stream=stream, stats=False)
-        comparisons["bfs64_unbatched_ms"] = round(timed(unbatched), 3)
-        comparisons["pagerank_bsp_ms"] = round(timed(lambda: G.pagerank(ALPHA, EPS, rank_t, cfg=bsp_pr, stream=stream,
-                                                                         stats=False)), 3)
-        comparisons["color_bsp_ms"] = round(timed(lambda: G.color(colors, cfg=bsp_gc, stream=stream, stats=False)), 3)
-        comparisons["bsp_layout"] = {"pagerank": "spread" if bsp_pr.flags else "input",
-                                     "color": "spread" if bsp_gc.flags else "input"}
-        # the quality option: assigns avoid only smaller neighbours' colours (ATOS_FLAG_GC_ORDERED)
-        ordered = atos.queue_config(worker_size=512, fetch_size=512, flags=atos.FLAG_GC_ORDERED)
-        _, k_ord, st_ord = G.color(colors, cfg=ordered, stream=stream)
-        comparisons["color_ordered"] = {"ms": round(st_ord.ms, 3), "colors": int(k_ord),
-                                        "tasks_per_vertex": round(st_ord.tasks / g.n, 3)}
-        comparisons["step_bsp_ms"] = round(comparisons["bfs64_bsp_ms"] + comparisons["pagerank_bsp_ms"]
-                                           + comparisons["color_bsp_ms"], 3)
-        comparisons["bfs64_batched_ms"] = round(mean(bfs_ms), 3)
+        comparisons = compare_rmat(atos, G, g, srcs, depths, rank_t, colors, stream,
+                                   dict(cfg_bfs=cfg_bfs, cfg_pr=cfg_pr, cfg_gc=cfg_gc, bfs_ms=bfs_ms, pr_ms=pr_ms,
+                                        gc_ms=gc_ms, ms_step=ms_step, bfs_edges=bfs_edges, pr_edges=pr_edges,
+                                        gc_edges=gc_edges, bfs_stats=bfs_stats, ncol=int(ncol)))
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -448,7 +409,271 @@ def run_atos(args, rank: int, world: int):
     if not args.no_e2e:
         result["e2e"] = run_e2e(args, g, srcs, (cfg_bfs, cfg_pr, cfg_gc), bfs_edges + pr_edges + gc_edges, world)
     G.close()
+    del depths
+    if not args.no_configs and world == 1:
+        # the other workloads, each measured on its own after the main step (not part of `value`)
+        result["configs"] = {"grid2048": grid_leg(atos, stream, dev, hbm_peak),
+                             "batched": batched_leg(atos, stream, dev, hbm_peak),
+                             "serving": serving_leg(atos, dev)}
     return result
+
+
+def timed_ms(fn, stream, reps=2):
+    """Device time of one call of fn on `stream` (CUDA events, after one untimed call), median of
+    `reps` calls."""
+    import torch
+    fn()
+    out = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return statistics.median(out)
+
+
+def bsp_configs(atos):
+    """The level-synchronous forms: levels driven by the host, or looped on the device in a CUDA
+    graph's conditional node."""
+    q = atos.queue_config
+    return {"host": q("bsp"), "device_loop": q("bsp", flags=atos.FLAG_BSP_DEVICE_LOOP)}
+
+
+def compare_rmat(atos, G, g, srcs, depths, rank_t, colors, stream, m):
+    """The persistent step against the project's level-synchronous (BSP) forms and the unbatched
+    single-query form, application by application, with Table 4's workload ratio and the paper's
+    normalised throughput (useful work, counted as the BSP form's work, per second)."""
+    import torch
+    q = atos.queue_config
+    mean = lambda xs: sum(xs) / len(xs)  # noqa: E731
+    out = {}
+    # BFS x 64
+    one = torch.empty((1, g.n), dtype=torch.int32, device="cuda")
+
+    def unbatched():
+        for s0 in srcs:
+            G.bfs([int(s0)], one, cfg=m["cfg_bfs"], stream=stream, stats=False)
+    bfs = {"persistent_batched_ms": round(mean(m["bfs_ms"]), 3),
+           "persistent_unbatched_ms": round(timed_ms(unbatched, stream, reps=1), 3)}
+    for name, cfg in bsp_configs(atos).items():
+        bfs[f"bsp_all_sources_{name}_ms"] = round(timed_ms(
+            lambda: G.bfs(srcs, depths, cfg=cfg, stream=stream, stats=False), stream), 3)
+    per_source = q("bsp", flags=atos.FLAG_BSP_PER_SOURCE)
+    bfs["bsp_per_source_host_ms"] = round(timed_ms(
+        lambda: G.bfs(srcs, depths, cfg=per_source, stream=stream, stats=False), stream, reps=1), 3)
+    bfs["best_bsp_ms"] = min(v for k, v in bfs.items() if k.startswith("bsp_"))
+    _, bsp_bfs = G.bfs(srcs, depths, cfg=q("bsp"), stream=stream)
+    bfs["bsp_levels"] = int(bsp_bfs.iterations)
+    out["bfs64"] = bfs
+    # PageRank and colouring: each BSP form at its better layout (input or spread ids)
+    def best_bsp(run):
+        best = None
+        for name, base in bsp_configs(atos).items():
+            for layout, flags in (("input", 0), ("spread", atos.FLAG_SPREAD_IDS)):
+                cfg = q("bsp", flags=base.flags | flags)
+                t = timed_ms(lambda: run(cfg), stream)
+                if best is None or t < best[0]:
+                    best = (t, name, layout, cfg)
+                out.setdefault("_bsp_times", {})[f"{run.__name__}_{name}_{layout}"] = round(t, 3)
+        return best
+
+    def pagerank(cfg):
+        G.pagerank(ALPHA, EPS, rank_t, cfg=cfg, stream=stream, stats=False)
+
+    def color(cfg):
+        G.color(colors, cfg=cfg, stream=stream, stats=False)
+    t_pr, form_pr, lay_pr, cfg_bsp_pr = best_bsp(pagerank)
+    t_gc, form_gc, lay_gc, cfg_bsp_gc = best_bsp(color)
+    bsp_times = out.pop("_bsp_times")
+    _, bsp_pr_st = G.pagerank(ALPHA, EPS, rank_t, cfg=cfg_bsp_pr, stream=stream)
+    _, k_bsp, bsp_gc_st = G.color(colors, cfg=cfg_bsp_gc, stream=stream)
+    out["pagerank"] = {"persistent_ms": round(mean(m["pr_ms"]), 3), "best_bsp_ms": round(t_pr, 3),
+                       "best_bsp_form": f"{form_pr}, {lay_pr} ids", "bsp_levels": int(bsp_pr_st.iterations),
+                       "bsp_error_bound": bsp_pr_st.error_bound,
+                       **{k.split("_", 1)[1] + "_ms": v for k, v in bsp_times.items() if k.startswith("pagerank_")}}
+    # colouring: the tuned run against the BSP form, the fastest speculative run of Algorithm 6
+    # and the ordered variant, each with its colour count
+    spec_cfg = q(worker_size=512, fetch_size=512, flags=atos.FLAG_SPREAD_IDS)
+    t_spec = timed_ms(lambda: color(spec_cfg), stream)
+    _, k_spec, st_spec = G.color(colors, cfg=spec_cfg, stream=stream)
+    ordered = q(worker_size=512, fetch_size=512, flags=atos.FLAG_GC_ORDERED)
+    _, k_ord, st_ord = G.color(colors, cfg=ordered, stream=stream)
+    out["color"] = {"persistent_ms": round(mean(m["gc_ms"]), 3), "persistent_colors": m["ncol"],
+                    "persistent_dependency_ordered": bool(m["cfg_gc"].flags & atos.FLAG_GC_DEPENDENCY),
+                    "best_bsp_ms": round(t_gc, 3), "best_bsp_form": f"{form_gc}, {lay_gc} ids",
+                    "bsp_colors": int(k_bsp), "bsp_levels": int(bsp_gc_st.iterations),
+                    **{k.split("_", 1)[1] + "_ms": v for k, v in bsp_times.items() if k.startswith("color_")},
+                    "speculative_cta512_spread": {"ms": round(t_spec, 3), "colors": int(k_spec),
+                                                  "tasks_per_vertex": round(st_spec.tasks / g.n, 3)},
+                    "ordered_cta512": {"ms": round(st_ord.ms, 3), "colors": int(k_ord),
+                                       "tasks_per_vertex": round(st_ord.tasks / g.n, 3)}}
+    best_step = bfs["best_bsp_ms"] + t_pr + t_gc
+    out["step"] = {"persistent_ms": round(m["ms_step"], 3), "best_bsp_ms": round(best_step, 3),
+                   "speedup_vs_best_bsp": round(best_step / m["ms_step"], 3),
+                   "note": "best BSP form per application (host- or device-driven levels, all sources at once or "
+                           "one at a time, input or spread ids) against the persistent step"}
+    out["workload_ratio"] = {
+        "bfs": round(m["bfs_stats"].edges / max(1, bsp_bfs.edges), 3),
+        "pagerank": round(m["pr_edges"] / max(1, bsp_pr_st.edges), 3),
+        "color": round(m["gc_edges"] / max(1, bsp_gc_st.edges), 3),
+        "note": "neighbour entries read by the persistent path / by the BSP path (Table 4's ratio)"}
+    useful = {"bfs": m["bfs_edges"], "pagerank": float(bsp_pr_st.edges), "color": float(bsp_gc_st.edges)}
+    times = {"bfs": mean(m["bfs_ms"]), "pagerank": mean(m["pr_ms"]), "color": mean(m["gc_ms"])}
+    out["normalized_gteps"] = {
+        **{k: round(useful[k] / (times[k] * 1e-3) / 1e9, 3) for k in useful},
+        "step": round(sum(useful.values()) / (m["ms_step"] * 1e-3) / 1e9, 3),
+        "note": "Section 6's normalised throughput: useful work per second, the useful work of PageRank and "
+                "colouring counted as the BSP form's edge work (BFS: Graph500 edges, as the headline)"}
+    return out
+
+
+def _pcts(xs):
+    return {"p50_ms": round(float(np.percentile(xs, 50)), 3), "p99_ms": round(float(np.percentile(xs, 99)), 3),
+            "mean_ms": round(float(np.mean(xs)), 3)}
+
+
+def _device_times(fn, stream, runs):
+    """Per-call device times (CUDA events on `stream`) of `runs` calls of fn after one warm-up."""
+    import torch
+    fn()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(runs + 1)]
+    evs[0].record(stream)
+    for k in range(runs):
+        fn()
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return [evs[k].elapsed_time(evs[k + 1]) for k in range(runs)]
+
+
+def grid_leg(atos, stream, dev, hbm_peak, runs=10):
+    """The high-diameter mesh: a 2048 x 2048 4-neighbour grid with 10% of its edges deleted
+    (seed 1), BFS from the corner vertex and FP32 PageRank, each autotuned, against the best BSP
+    form (levels driven by the host or looped on the device; PageRank at its better layout)."""
+    import torch
+    g = gg.grid(2048, delete_frac=0.1, seed=1)
+    G = atos.Graph.from_csr(g)
+    q = atos.queue_config
+    depth = torch.empty((1, g.n), dtype=torch.int32, device="cuda")
+    rank = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    cfg_b, _ = G.autotune("bfs", [0], repeats=1, stream=stream)
+    cfg_p, _ = G.autotune("pagerank", repeats=1, stream=stream)
+    _, st_b = G.bfs([0], depth, cfg=cfg_b, stream=stream)
+    _, st_p = G.pagerank(ALPHA, EPS, rank, cfg=cfg_p, stream=stream)
+    deg = torch.from_numpy(np.diff(g.row_ptr).astype(np.int64)).cuda()
+    comp = int(component_edges(depth, deg).sum().item())
+    with ClockSampler(dev) as clocks:
+        bfs_ms = _device_times(lambda: G.bfs([0], depth, cfg=cfg_b, stream=stream, stats=False), stream, runs)
+        pr_ms = _device_times(lambda: G.pagerank(ALPHA, EPS, rank, cfg=cfg_p, stream=stream, stats=False), stream,
+                              runs)
+    bfs = {"graph500_edges": comp, "gteps": round(comp / (np.mean(bfs_ms) * 1e-3) / 1e9, 3), **_pcts(bfs_ms),
+           "tasks": st_b.tasks, "cfg": cfg_brief(cfg_b)}
+    for name, cfg in bsp_configs(atos).items():
+        _, st = G.bfs([0], depth, cfg=cfg, stream=stream)
+        bfs[f"bsp_{name}_ms"] = round(min(st.ms, timed_ms(
+            lambda: G.bfs([0], depth, cfg=cfg, stream=stream, stats=False), stream, reps=1)), 3)
+        bfs["bsp_levels"] = int(st.iterations)
+    bfs["speedup_vs_best_bsp"] = round(min(bfs["bsp_host_ms"], bfs["bsp_device_loop_ms"]) / np.mean(bfs_ms), 3)
+    pr = {"edge_pushes": st_p.edges, "tasks": st_p.tasks,
+          "g_edge_pushes_per_s": round(st_p.edges / (np.mean(pr_ms) * 1e-3) / 1e9, 3), **_pcts(pr_ms),
+          "error_bound": st_p.error_bound, "cfg": cfg_brief(cfg_p)}
+    best = None
+    for name, base in bsp_configs(atos).items():
+        for layout, flags in (("input", 0), ("spread", atos.FLAG_SPREAD_IDS)):
+            cfg = q("bsp", flags=base.flags | flags)
+            t = timed_ms(lambda: G.pagerank(ALPHA, EPS, rank, cfg=cfg, stream=stream, stats=False), stream, reps=1)
+            pr[f"bsp_{name}_{layout}_ms"] = round(t, 3)
+            best = t if best is None else min(best, t)
+    pr["speedup_vs_best_bsp"] = round(best / np.mean(pr_ms), 3)
+    # PageRank's algorithmic bytes (20 B per task + 8 B per edge push) against the measured HBM peak
+    pr["roofline_frac"] = round((20.0 * st_p.tasks + 8.0 * st_p.edges) / (np.mean(pr_ms) * 1e-3) / 1e9 / hbm_peak, 4)
+    G.close()
+    return {"workload": "grid2048_del0.1_bfs0_pagerank", "graph": "2048 x 2048 4-neighbour grid, 10% of edges "
+            "deleted (seed 1), row-major ids", "n": g.n, "nnz": g.nnz, "bfs": bfs, "pagerank": pr,
+            "runs": runs, "clocks": clocks.summary()}
+
+
+def batched_leg(atos, stream, dev, hbm_peak, runs=5):
+    """The batched mix (256 graphs, 1024 BFS + 256 PageRank instances) in one persistent launch
+    replayed as a CUDA graph, with the configuration the batch autotuner chose on this mix
+    (512-thread CTAs, fetch 512, window 512, Check_Size 8, spread ids; `bench.py --workload
+    batched` reruns the sweep), against the same work as per-graph calls."""
+    import torch
+    graphs, specs = batched_workload()
+    Gs = [atos.Graph.from_csr(x) for x in graphs]
+    cfg = atos.queue_config(worker_size=512, fetch_size=512, window=512, check_size=8, flags=atos.FLAG_SPREAD_IDS)
+    B = atos.Batch(Gs, specs, cfg)
+    B.run(stream=stream, graph=True)
+    B.run(stream=stream, graph=True)
+    _, per = B.stats(stream=stream)
+    bfs_edges = pr_edges = pr_tasks = 0
+    bfs_bytes = 0.0
+    ok = True
+    for (kind, gi, *rest), out, st in zip(specs, B.outputs, per):
+        ok &= st.status == 0
+        x = graphs[gi]
+        if kind == "bfs":
+            deg = torch.from_numpy(np.diff(x.row_ptr).astype(np.int64)).cuda()
+            comp = int(((out != 2**31 - 1).to(torch.int64) * deg).sum().item())
+            bfs_edges += comp // 2
+            bfs_bytes += 12.0 * x.n + 8.0 * comp
+        else:
+            pr_edges += st.edges
+            pr_tasks += st.tasks
+    with ClockSampler(dev) as clocks:
+        ms = _device_times(lambda: B.run(stream=stream, graph=True), stream, runs)
+    outs = [(torch.empty((BATCH_BFS, x.n), dtype=torch.int32, device="cuda"),
+             torch.empty(x.n, dtype=torch.float32, device="cuda")) for x in graphs]
+    srcs = [[sp[2] for sp in specs if sp[0] == "bfs" and sp[1] == gi] for gi in range(len(graphs))]
+
+    def per_graph():
+        for gi, G in enumerate(Gs):
+            G.bfs(srcs[gi], outs[gi][0], cfg=cfg, stream=stream, stats=False)
+            G.pagerank(ALPHA, EPS, outs[gi][1], cfg=cfg, stream=stream, stats=False)
+    t_calls = timed_ms(per_graph, stream, reps=1)
+    work = bfs_edges + pr_edges
+    algo = bfs_bytes + 20.0 * pr_tasks + 8.0 * pr_edges
+    res = {"workload": "batched_mix_256g_bfs4_pr1", "graphs": "128 RMAT (scale U{10..18}) + 128 grids (side "
+           "U{64..1024}), 10% edge deletion, seed 1", "instances": len(specs), "all_ok": bool(ok),
+           "gteps": round(work / (np.mean(ms) * 1e-3) / 1e9, 3), **_pcts(ms),
+           "per_graph_calls_ms": round(t_calls, 3), "speedup_vs_per_graph_calls": round(t_calls / np.mean(ms), 3),
+           "roofline": {"bound": "hbm", "achieved": round(algo / (np.mean(ms) * 1e-3) / 1e9, 1), "peak": hbm_peak,
+                        "unit": "GB/s", "frac": round(algo / (np.mean(ms) * 1e-3) / 1e9 / hbm_peak, 4)},
+           "bfs_graph500_edges": bfs_edges, "pagerank_edge_pushes": pr_edges, "cfg": cfg_brief(cfg),
+           "window": B.window, "cuda_graph": True, "runs": runs, "clocks": clocks.summary()}
+    B.close()
+    for G in Gs:
+        G.close()
+    return res
+
+
+def serving_leg(atos, dev, duration=4.0):
+    """A bounded serving window: 64 resident graphs of the batched mix plus RMAT 23, Poisson
+    arrivals (BFS 60%, PageRank 30%, colouring 10%), admitted by footprint; offered at the 2000
+    req/s of the serving configuration and at 100 req/s.  Latency = completion - arrival."""
+    from paper_2112_00132_gb300 import serve as srv
+    csrs = srv.config_graphs()
+    graphs = [atos.Graph.from_csr(x) for x in csrs]
+    keys = ("offered_rps", "achieved_rps", "sustainable", "requests", "completed", "unfinished", "p50_ms", "p99_ms",
+            "p50_ms_by_kind", "p99_ms_by_kind", "gteps", "epochs", "wall_s")
+    out = {"workload": "serving: 64 graphs drawn from the batched mix + RMAT 23, Poisson arrivals, mix BFS 60% / "
+           "PageRank 30% / colouring 10%", "window_s": duration, "warmup_s": 1.0}
+    with ClockSampler(dev) as clocks:
+        for rate in (2000.0, 100.0):
+            r = srv.serve(csrs, rate=rate, duration=duration, warmup=1.0, drain_s=6.0, graphs=graphs)
+            out[f"offered_{int(rate)}"] = {k: r[k] for k in keys}
+    out["clocks"] = clocks.summary()
+    for G in graphs:
+        G.close()
+    return out
+
+
+def cfg_brief(c):
+    names = {0: "persistent", 1: "discrete", 2: "bsp"}
+    return {"worker": c.worker_size, "fetch": c.fetch_size, "strategy": names.get(c.strategy, c.strategy),
+            "fetch_policy": c.fetch_policy, "window": c.window, "check_size": c.check_size, "flags": c.flags}
 
 
 def run_color_ids_study(args):

@@ -116,6 +116,17 @@ extern "C" {
                                      frontiers of all sources advance together, one launch of each
                                      level kernel per level for all of them. */
 
+#define ATOS_FLAG_GC_DEPENDENCY 256u /* atos_color (persistent and discrete strategies): colour each
+                                     vertex once, after all of its smaller-id neighbours (in the ids
+                                     the run uses), with the smallest colour none of them holds: a
+                                     per-vertex count of uncoloured smaller neighbours makes a vertex
+                                     ready, and the task that colours a vertex counts down its larger
+                                     neighbours.  The result is exactly serial first fit in id order,
+                                     one task per vertex and no recolouring; the run takes as many
+                                     dependent steps as the longest path of increasing ids.  n int32
+                                     of scratch.  The BSP strategy ignores it; batches and servers
+                                     return ATOS_ERR_UNSUPPORTED. */
+
 typedef struct atos_config {
   int32_t worker_size;    /* 1 (thread worker, BFS only), 32 (warp worker) or a CTA worker of 64,
                              128, 256, 512 or 1024 threads */
@@ -388,14 +399,19 @@ int atos_server_destroy(atos_server_t s);
  * L1 distance of the normalised result to the fixed point) exceeds this are not chosen. */
 #define ATOS_TUNE_PR_MAX_ERROR 1e-4
 
+/* Colouring candidates of atos_autotune whose colour count exceeds this factor times the fewest
+ * colours any candidate reached are not chosen. */
+#define ATOS_TUNE_GC_MAX_COLOR_RATIO 1.05
+
 /* Times candidate configurations of `app` (ATOS_APP_*) on g and returns the fastest in *best
  * (its device time in *best_ms): CTA workers of 128..1024 threads, warp workers and (BFS) thread
- * workers, fixed /
- * greedy / spread fetch policies, persistent, discrete and BSP strategies, plus the instance
- * window for multi-source BFS, and Check_Size and the threshold-crossing enqueue for PageRank
- * (Figure 4's worker-size x FETCH_SIZE sweep with the kernel strategy of Section 3.4).  Each
- * candidate runs repeats + 1 times (the first warms up); failing candidates, and PageRank
- * candidates whose error bound exceeds ATOS_TUNE_PR_MAX_ERROR, are skipped.  sources/nsrc: BFS
+ * workers, fixed / greedy / spread fetch policies, persistent, discrete and BSP strategies (the
+ * BSP level loop on the host and on the device), plus the instance window for multi-source BFS,
+ * Check_Size and the threshold-crossing enqueue for PageRank, and the dependency-ordered mode
+ * for colouring (Figure 4's worker-size x FETCH_SIZE sweep with the kernel strategy of
+ * Section 3.4).  Each candidate runs repeats + 1 times (the first warms up); failing candidates,
+ * PageRank candidates whose error bound exceeds ATOS_TUNE_PR_MAX_ERROR and colouring candidates
+ * with more than ATOS_TUNE_GC_MAX_COLOR_RATIO times the fewest colours are skipped.  sources/nsrc: BFS
  * sources (HOST).
  * scratch_out: DEVICE output buffer the runs write into (nsrc * n int32 for BFS, n floats for
  * PageRank, n int32 for colouring).  The winner is cached per graph class (application, log2 n,

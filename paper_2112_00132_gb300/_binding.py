@@ -40,6 +40,7 @@ FLAG_GC_ORDERED = 16
 FLAG_BFS_EXPAND_ONCE = 32
 FLAG_BSP_DEVICE_LOOP = 64
 FLAG_BSP_PER_SOURCE = 128
+FLAG_GC_DEPENDENCY = 256
 DEVICE_PTRS, BORROW, CHECK_SYMMETRIC, SKIP_VALIDATION = 1, 2, 4, 8
 UNREACHED = 2**31 - 1
 

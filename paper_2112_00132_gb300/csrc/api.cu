@@ -24,6 +24,9 @@ cudaError_t pr_verify_sweep(Instance* d_insts, int ninst, int max_n, DevCtl* d_c
 cudaError_t pr_finish(Instance* d_insts, int ninst, int n, int64_t nnz, DevCtl* d_ctl, double* certificate_y,
                       double exact_sum, cudaStream_t s);
 cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s);
+cudaError_t gc_split_build(const int32_t* row_ptr, const int32_t* col, int n, int32_t* mid, int32_t* scol,
+                           cudaStream_t s);
+cudaError_t gc_wait_init(const int32_t* mid, int n, int32_t* wait, cudaStream_t s);
 size_t spread_build_scratch_bytes(int32_t n);
 cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, int32_t* perm, int32_t* new_rp,
                          int32_t* new_col, int32_t* bsums, void* scratch, int32_t* h_hubs, HubMap* h_map,
@@ -119,6 +122,11 @@ struct atos_graph_s {
   int32_t sp_hubs = 0;         // hubs of the copy (its highest-degree vertices)
   HubMap sp_hub = {0, 1, 1, 0};  // where they sit
   int32_t* d_expanded = nullptr;  // BFS: per source, the smallest depth each vertex was expanded at
+  int32_t* d_gc_wait = nullptr;   // dependency-ordered colouring: per vertex, counts still to go
+  // dependency-ordered colouring: per layout (input ids, spread-id copy), the rows with the
+  // smaller-id neighbours first (gc_col) and how many they are (gc_mid); built on first use
+  int32_t* gc_mid[2] = {nullptr, nullptr};
+  int32_t* gc_col[2] = {nullptr, nullptr};
   size_t expanded_rows = 0;
   unsigned long long* d_timeline = nullptr;  // throughput timeline (atos_timeline), 2 counters per bucket
   int64_t tl_bucket_ns = 0;
@@ -255,7 +263,7 @@ int check_config(const atos_config& c) {
     return ATOS_ERR_INVALID_ARG;
   if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS | ATOS_FLAG_USE_TUNED |
                   ATOS_FLAG_GC_ORDERED | ATOS_FLAG_BFS_EXPAND_ONCE | ATOS_FLAG_BSP_DEVICE_LOOP |
-                  ATOS_FLAG_BSP_PER_SOURCE))
+                  ATOS_FLAG_BSP_PER_SOURCE | ATOS_FLAG_GC_DEPENDENCY))
     return ATOS_ERR_INVALID_ARG;
   return ATOS_OK;
 }
@@ -602,6 +610,8 @@ int atos_graph_destroy(atos_graph_t g) {
   pool_free_host(g->h_bsp);
   pool_free(g->sp_row_ptr), pool_free(g->sp_col), pool_free(g->sp_out), pool_free(g->sp_perm);
   pool_free(g->d_expanded);
+  pool_free(g->d_gc_wait);
+  for (int k = 0; k < 2; ++k) pool_free(g->gc_mid[k]), pool_free(g->gc_col[k]);
   pool_free(g->d_timeline);
   g->s.release();
   delete g;
@@ -866,9 +876,30 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   I.gc_ordered = (cfg.flags & ATOS_FLAG_GC_ORDERED) ? 1 : 0;
   if (spread) I.row_ptr = g->sp_row_ptr, I.col = g->sp_col;
   I.qbits = g->d_qbits;
+  const bool dependency = (cfg.flags & ATOS_FLAG_GC_DEPENDENCY) != 0;
+  if (dependency) {
+    if (!g->d_gc_wait) ATOS_TRY(dev_alloc(&g->d_gc_wait, (size_t)n));
+    const int lay = spread ? 1 : 0;
+    if (!g->gc_mid[lay]) {  // the split rows of this layout, built once per graph
+      int32_t *mid = nullptr, *scol = nullptr;
+      int rc2 = from_cuda(dev_alloc(&mid, (size_t)n));
+      if (!rc2) rc2 = from_cuda(dev_alloc(&scol, (size_t)std::max<int64_t>(g->nnz, 1)));
+      if (!rc2) rc2 = from_cuda(gc_split_build(I.row_ptr, I.col, n, mid, scol, st));
+      if (rc2) {
+        cudaStreamSynchronize(st);
+        pool_free(mid), pool_free(scol);
+        return rc2;
+      }
+      g->gc_mid[lay] = mid, g->gc_col[lay] = scol;
+    }
+    I.gc_wait = g->d_gc_wait;
+    I.gc_mid = g->gc_mid[lay];
+    I.col = g->gc_col[lay];
+  }
   g->s.h_insts[0] = I;
   cfg.window = 1;
   ATOS_TRY(cudaEventRecord(g->s.ev0, st));
+  if (dependency) ATOS_TRY(gc_wait_init(I.gc_mid, n, I.gc_wait, st));
   int64_t iters = 0;
   rc = run_instances(g, 1, n, cfg, gc_persistent_kernel, gc_discrete_kernel, kAppGc, st, &iters);
   if (rc) return rc;

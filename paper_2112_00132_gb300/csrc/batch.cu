@@ -303,6 +303,7 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
   if (!worker_supported(cfg.worker_size)) return ATOS_ERR_UNSUPPORTED;
   if (cfg.strategy != ATOS_PERSISTENT && cfg.strategy != ATOS_DISCRETE) return ATOS_ERR_UNSUPPORTED;
   if (cfg.worker_size == 1) return ATOS_ERR_UNSUPPORTED;  // thread workers: BFS through atos_bfs only
+  if (cfg.flags & ATOS_FLAG_GC_DEPENDENCY) return ATOS_ERR_UNSUPPORTED;  // atos_color only
   if (cfg.fetch_size < 1 || cfg.fetch_size > 1024 || (cfg.worker_size != 32 && cfg.fetch_size > cfg.worker_size))
     return ATOS_ERR_INVALID_ARG;
   // validate every instance before allocating anything

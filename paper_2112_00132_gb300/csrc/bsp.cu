@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(kBlock) scan_chunks_kernel(Ctl* c) {
   __shared__ long long tmp[33];
   const long long F = c->F[c->cur];
   const long long nchunks = (F + kChunk - 1) / kChunk;
-  long long* offs = c->offs;
+  long long* __restrict__ offs = c->offs;
+  long long* __restrict__ bsums = c->bsums;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long base = ch * kChunk + (long long)threadIdx.x * kPerThread;
     long long d[kPerThread], local = 0;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kBlock) scan_chunks_kernel(Ctl* c) {
       if (base + k < F) offs[base + k] = pre;
       pre += d[k];
     }
-    if (threadIdx.x == 0) c->bsums[ch] = total;
+    if (threadIdx.x == 0) bsums[ch] = total;
   }
 }
 
@@ -143,15 +144,16 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(Ctl* c) {
   const long long nchunks = (F + kChunk - 1) / kChunk;
   const long long per = (nchunks + 1023) / 1024;
   const long long b0 = (long long)threadIdx.x * per;
+  long long* __restrict__ bsums = c->bsums;
   long long local = 0;
   for (long long k = 0; k < per; ++k)
-    if (b0 + k < nchunks) local += c->bsums[b0 + k];
+    if (b0 + k < nchunks) local += bsums[b0 + k];
   long long total;
   long long pre = block_excl_scan64<1024>(local, tmp, total);
   for (long long k = 0; k < per; ++k)
     if (b0 + k < nchunks) {
-      const long long x = c->bsums[b0 + k];
-      c->bsums[b0 + k] = pre;
+      const long long x = bsums[b0 + k];
+      bsums[b0 + k] = pre;
       pre += x;
     }
   if (threadIdx.x == 0) {
@@ -162,8 +164,10 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(Ctl* c) {
 
 __global__ void scan_add_kernel(Ctl* c) {
   const long long F = c->F[c->cur];
+  long long* __restrict__ offs = c->offs;
+  const long long* __restrict__ bsums = c->bsums;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < F; i += (long long)gridDim.x * blockDim.x)
-    c->offs[i] += c->bsums[i / kChunk];
+    offs[i] += bsums[i / kChunk];
 }
 
 // ---------------------------------------------------------------------------- level end
@@ -191,8 +195,9 @@ __global__ void level_end_kernel(Ctl* c, cudaGraphConditionalHandle handle, int 
 
 __global__ void bfs_fill_kernel(Ctl* c) {
   const long long total = (long long)c->nsrc * c->n;
+  int32_t* __restrict__ depth = c->depth;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
-    c->depth[i] = kUnreached;
+    depth[i] = kUnreached;
 }
 
 __global__ void bfs_seed_kernel(Ctl* c) {
@@ -206,10 +211,12 @@ __global__ void bfs_seed_kernel(Ctl* c) {
 
 __global__ void bfs_degrees_kernel(Ctl* c) {
   const long long F = c->F[c->cur];
-  const unsigned long long* fr = (const unsigned long long*)c->fr[c->cur];
+  const unsigned long long* __restrict__ fr = (const unsigned long long*)c->fr[c->cur];
+  const int32_t* __restrict__ row_ptr = c->row_ptr;
+  long long* __restrict__ offs = c->offs;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < F; i += (long long)gridDim.x * blockDim.x) {
     const int v = (int)(unsigned)fr[i];
-    c->offs[i] = __ldg(c->row_ptr + v + 1) - __ldg(c->row_ptr + v);
+    offs[i] = __ldg(row_ptr + v + 1) - __ldg(row_ptr + v);
   }
 }
 
@@ -249,29 +256,36 @@ __global__ void __launch_bounds__(kBlock) bfs_advance_kernel(Ctl* c) {
         s_start[k] = __ldg(row_ptr + (int)(unsigned)s_item[k]);
       }
     __syncthreads();
+    // each thread: kPerThread consecutive edges, one owner search
+    const long long ea = e0 + (long long)threadIdx.x * kPerThread;
+    long long i = 0;
+    if (ea < e1) i = staged ? owner64(s_off, cnt, ea) : owner64(offs + lo, cnt, ea);
+    int nbs[kPerThread], cur_d[kPerThread];
+    unsigned srcs[kPerThread];
 #pragma unroll
     for (int r = 0; r < kPerThread; ++r) {
-      const long long e = e0 + r * kBlock + threadIdx.x;
-      bool want = false;
-      unsigned long long out = 0;
+      const long long e = ea + r;
+      nbs[r] = -1;
       if (e < e1) {
-        unsigned long long it;
-        long long o;
-        int first;
         if (staged) {
-          const long long i = owner64(s_off, cnt, e);
-          it = s_item[i], o = s_off[i], first = s_start[i];
+          while (i + 1 < cnt && s_off[i + 1] <= e) ++i;
+          srcs[r] = (unsigned)(s_item[i] >> 32);
+          nbs[r] = __ldg(col + s_start[i] + (e - s_off[i]));
         } else {
-          const long long i = lo + owner64(offs + lo, cnt, e);
-          it = fr[i], o = offs[i], first = __ldg(row_ptr + (int)(unsigned)it);
+          while (i + 1 < cnt && offs[lo + i + 1] <= e) ++i;
+          const unsigned long long it = fr[lo + i];
+          srcs[r] = (unsigned)(it >> 32);
+          nbs[r] = __ldg(col + __ldg(row_ptr + (int)(unsigned)it) + (e - offs[lo + i]));
         }
-        const int nb = __ldg(col + first + (e - o));
-        const unsigned s = (unsigned)(it >> 32);
-        int32_t* d = depth + (long long)s * n + nb;
-        if (nd < __ldcg(d)) want = nd < atomicMin(d, nd);
-        out = ((unsigned long long)s << 32) | (unsigned)nb;
       }
-      append_next(c, nxt, want, out);
+    }
+#pragma unroll
+    for (int r = 0; r < kPerThread; ++r) cur_d[r] = nbs[r] >= 0 ? __ldcg(depth + (long long)srcs[r] * n + nbs[r]) : 0;
+#pragma unroll
+    for (int r = 0; r < kPerThread; ++r) {
+      bool want = false;
+      if (nbs[r] >= 0 && nd < cur_d[r]) want = nd < atomicMin(depth + (long long)srcs[r] * n + nbs[r], nd);
+      append_next(c, nxt, want, ((unsigned long long)srcs[r] << 32) | (unsigned)(nbs[r] < 0 ? 0 : nbs[r]));
     }
     __syncthreads();
   }
@@ -288,15 +302,21 @@ __global__ void iota_kernel(Ctl* c) {
 // degree (0 when there is nothing to scatter) for the scan.
 __global__ void pr_take_kernel(Ctl* c) {
   const long long F = c->F[c->cur];
-  const int32_t* fr = (const int32_t*)c->fr[c->cur];
+  const int32_t* __restrict__ fr = (const int32_t*)c->fr[c->cur];
+  const int32_t* __restrict__ row_ptr = c->row_ptr;
+  float* __restrict__ res = c->res;
+  float* __restrict__ rank = c->rank;
+  float* __restrict__ share = c->share;
+  long long* __restrict__ offs = c->offs;
+  const float alpha = c->alpha;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < F; i += (long long)gridDim.x * blockDim.x) {
     const int v = fr[i];
-    const float r = atomicExch(c->res + v, 0.0f);
-    const int d = __ldg(c->row_ptr + v + 1) - __ldg(c->row_ptr + v);
-    c->rank[v] += r;
+    const float r = atomicExch(res + v, 0.0f);
+    const int d = __ldg(row_ptr + v + 1) - __ldg(row_ptr + v);
+    rank[v] += r;
     const bool go = r != 0.0f && d > 0;
-    c->share[i] = go ? c->alpha * r / (float)d : 0.0f;
-    c->offs[i] = go ? d : 0;
+    share[i] = go ? alpha * r / (float)d : 0.0f;
+    offs[i] = go ? d : 0;
   }
 }
 
@@ -305,8 +325,12 @@ __global__ void pr_take_kernel(Ctl* c) {
 __global__ void __launch_bounds__(kBlock) pr_scatter_kernel(Ctl* c) {
   const long long F = c->F[c->cur];
   const long long total = c->total;
-  const int32_t* fr = (const int32_t*)c->fr[c->cur];
-  const long long* offs = c->offs;
+  const int32_t* __restrict__ fr = (const int32_t*)c->fr[c->cur];
+  const long long* __restrict__ offs = c->offs;
+  const int32_t* __restrict__ row_ptr = c->row_ptr;
+  const int32_t* __restrict__ col = c->col;
+  const float* __restrict__ share = c->share;
+  float* res = c->res;
   const long long nchunks = (total + kChunk - 1) / kChunk;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long e0 = ch * kChunk, e1 = min(total, e0 + kChunk);
@@ -319,8 +343,8 @@ __global__ void __launch_bounds__(kBlock) pr_scatter_kernel(Ctl* c) {
       if (e >= e1) break;
       while (i + 1 < F && offs[i + 1] <= e) ++i;
       const int v = fr[i];
-      const int nb = __ldg(c->col + __ldg(c->row_ptr + v) + (e - offs[i]));
-      red_add_f32(c->res + nb, c->share[i]);
+      const int nb = __ldg(col + __ldg(row_ptr + v) + (e - offs[i]));
+      red_add_f32(res + nb, share[i]);
     }
   }
 }
@@ -329,9 +353,21 @@ __global__ void __launch_bounds__(kBlock) pr_scatter_kernel(Ctl* c) {
 __global__ void pr_filter_kernel(Ctl* c) {
   const int nxt = c->cur ^ 1;
   const float eps = c->eps;
-  for (int r = blockIdx.x * blockDim.x; r < c->n; r += gridDim.x * blockDim.x) {
+  const int n = c->n;
+  const float* __restrict__ res = c->res;
+  unsigned long long* count = (unsigned long long*)&c->F[nxt];
+  int32_t* out = (int32_t*)c->fr[nxt];
+  const int lane = threadIdx.x & 31;
+  for (int r = blockIdx.x * blockDim.x; r < n; r += gridDim.x * blockDim.x) {
     const int v = r + threadIdx.x;
-    append_next(c, nxt, v < c->n && c->res[v] > eps, (int32_t)v);
+    const bool want = v < n && __ldcg(res + v) > eps;
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) continue;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) out[base + __popc(m & lanemask_lt())] = v;
   }
 }
 
@@ -349,19 +385,22 @@ __global__ void gc_init_kernel(Ctl* c) {
 // vertex, colour windows of 64 combined by an OR reduction over the lanes).
 __global__ void gc_assign_kernel(Ctl* c) {
   const long long F = c->F[c->cur];
-  const int32_t* fr = (const int32_t*)c->fr[c->cur];
+  const int32_t* __restrict__ fr = (const int32_t*)c->fr[c->cur];
+  const int32_t* __restrict__ row_ptr = c->row_ptr;
+  const int32_t* __restrict__ col = c->col;
+  int32_t* color = c->color;
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   long long ed = 0;
   for (long long i = gw; i < F; i += nw) {
     const int v = fr[i];
-    const int s = __ldg(c->row_ptr + v), e = __ldg(c->row_ptr + v + 1);
+    const int s = __ldg(row_ptr + v), e = __ldg(row_ptr + v + 1);
     int colour = -1;
     for (int base = 0; colour < 0; base += 64) {
       unsigned lo = 0, hi = 0;
       for (int k = s + lane; k < e; k += 32) {
-        const int rel = __ldcg(c->color + __ldg(c->col + k)) - base;
+        const int rel = __ldcg(color + __ldg(col + k)) - base;
         if (rel >= 0 && rel < 32) lo |= 1u << rel;
         else if (rel >= 32 && rel < 64) hi |= 1u << (rel - 32);
       }
@@ -371,7 +410,7 @@ __global__ void gc_assign_kernel(Ctl* c) {
       const unsigned long long used = ((unsigned long long)hi << 32) | lo;
       if (~used) colour = base + __ffsll((long long)~used) - 1;
     }
-    if (lane == 0) c->color[v] = colour;
+    if (lane == 0) color[v] = colour;
   }
   if (lane == 0 && ed) atomicAdd((unsigned long long*)&c->edges, (unsigned long long)ed);
 }
@@ -381,23 +420,25 @@ __global__ void gc_assign_kernel(Ctl* c) {
 __global__ void gc_conflicts_kernel(Ctl* c) {
   const int cur = c->cur, nxt = cur ^ 1;
   const long long F = c->F[cur];
-  const int32_t* fr = (const int32_t*)c->fr[cur];
+  const int32_t* __restrict__ fr = (const int32_t*)c->fr[cur];
+  const int32_t* __restrict__ row_ptr = c->row_ptr;
+  const int32_t* __restrict__ col = c->col;
+  const int32_t* __restrict__ color = c->color;
+  unsigned long long* count = (unsigned long long*)&c->F[nxt];
+  int32_t* out = (int32_t*)c->fr[nxt];
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long i = gw; i < F; i += nw) {
     const int v = fr[i];
-    const int s = __ldg(c->row_ptr + v), e = __ldg(c->row_ptr + v + 1);
-    const int cv = c->color[v];
+    const int s = __ldg(row_ptr + v), e = __ldg(row_ptr + v + 1);
+    const int cv = color[v];
     bool conflict = false;
     for (int k = s + lane; k < e; k += 32) {
-      const int u = __ldg(c->col + k);
-      conflict |= u < v && c->color[u] == cv;
+      const int u = __ldg(col + k);
+      conflict |= u < v && color[u] == cv;
     }
-    if (__any_sync(0xffffffffu, conflict) && lane == 0) {
-      const unsigned long long at = atomicAdd((unsigned long long*)&c->F[nxt], 1ull);
-      ((int32_t*)c->fr[nxt])[at] = v;
-    }
+    if (__any_sync(0xffffffffu, conflict) && lane == 0) out[atomicAdd(count, 1ull)] = v;
   }
 }
 

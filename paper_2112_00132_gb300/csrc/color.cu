@@ -17,6 +17,58 @@ __global__ void gc_max_kernel(const int32_t* color, int n, int* out) {
   if ((threadIdx.x & 31) == 0) atomicMax(out, m + 1);
 }
 
+// Dependency-ordered colouring uses a copy of the CSR columns whose rows list the smaller-id
+// neighbours first and then the larger ones, each part in the row's order (mid[v]: how many are
+// smaller).  One warp per row: a ballot per 32 entries gives each entry its place.
+__global__ void gc_split_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int n,
+                                int32_t* __restrict__ mid, int32_t* __restrict__ scol) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int s = __ldg(row_ptr + v), e = __ldg(row_ptr + v + 1);
+    int lower = 0;
+    for (int k = s + lane; k < e; k += 32) lower += __ldg(col + k) < v;
+    lower = __reduce_add_sync(0xffffffffu, lower);
+    int lo = s, hi = s + lower;  // next slot of the lower and of the upper part
+    for (int k0 = s; k0 < e; k0 += 32) {
+      const int k = k0 + lane;
+      const int u = k < e ? __ldg(col + k) : 0;
+      const bool below = k < e && u < v;
+      const unsigned mb = __ballot_sync(0xffffffffu, below);
+      const unsigned ma = __ballot_sync(0xffffffffu, k < e && !below);
+      const unsigned lt = (1u << lane) - 1u;
+      if (below) scol[lo + __popc(mb & lt)] = u;
+      else if (k < e) scol[hi + __popc(ma & lt)] = u;
+      lo += __popc(mb);
+      hi += __popc(ma);
+    }
+    if (lane == 0) mid[v] = lower;
+  }
+}
+
+__global__ void gc_wait_init_kernel(const int32_t* __restrict__ mid, int n, int32_t* wait) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) wait[v] = 1 + mid[v];
+}
+
+cudaError_t gc_split_build(const int32_t* row_ptr, const int32_t* col, int n, int32_t* mid, int32_t* scol,
+                           cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = ((int64_t)n * 32 + 255) / 256;
+  blocks = blocks < 1 ? 1 : (blocks > 8192 ? 8192 : blocks);
+  count_launches(1);
+  gc_split_kernel<<<(int)blocks, 256, 0, s>>>(row_ptr, col, n, mid, scol);
+  return cudaGetLastError();
+}
+
+cudaError_t gc_wait_init(const int32_t* mid, int n, int32_t* wait, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (n + 255) / 256;
+  blocks = blocks < 1 ? 1 : (blocks > 4096 ? 4096 : blocks);
+  count_launches(1);
+  gc_wait_init_kernel<<<blocks, 256, 0, s>>>(mid, n, wait);
+  return cudaGetLastError();
+}
+
 cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s) {
   cudaMemsetAsync(&d_ctl->num_colors, 0, sizeof(int), s);
   int gx = (h_inst->n + 255) / 256;

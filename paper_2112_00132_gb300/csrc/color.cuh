@@ -17,6 +17,18 @@
 // vertices x and y this is the store-buffering pattern W(x); fence; R(y) against W(y); fence;
 // R(x), so at least one of the two checks that follow their final writes sees the other's colour,
 // and the conflict is found.  Colours are read from L2 (ld.global.cg).
+//
+// Dependency-ordered mode (ATOS_FLAG_GC_DEPENDENCY, I.gc_wait set): a vertex is coloured once,
+// after all of its smaller-id neighbours, taking the smallest colour none of them holds, so the
+// result is exactly serial first fit in id order, with one colouring task per vertex and no
+// recolouring.  The rows (I.col) list each vertex's smaller-id neighbours first (I.gc_mid[v] of
+// them), so the colour pass reads only those.  gc_wait[v] starts at 1 + I.gc_mid[v].  The virtual initial task
+// v releases the 1; a coloured vertex decrements the counter of each larger neighbour; whichever
+// decrement reaches zero makes the vertex ready and (for a neighbour) pushes it as ~w.  Only one
+// decrement reaches zero, so each vertex is coloured exactly once.  A colour is written and
+// fenced before the decrements that follow it, and the task that reads it was pushed (fenced,
+// published) by the decrement that completed the count, so the colours a ready vertex reads are
+// final.
 #pragma once
 
 #include "engine.cuh"
@@ -42,8 +54,141 @@ struct GcBody {
   using Extra = GcExtra<B>;
   static constexpr int kResidentThreads = 1536;
 
+  // Dependency-ordered mode: item v >= 0 releases the initial count of v, item ~v is a vertex
+  // made ready by its last smaller neighbour.  Ready vertices take the smallest colour their
+  // smaller neighbours (the first gc_mid[v] entries of the row) do not hold, then count down
+  // their larger neighbours (the rest of the row).  A vertex made ready is published as soon as
+  // the round that made it ready ends, not at the end of the batch: a hub's row is long, and the
+  // next vertex on the longest dependency path is often among the first it releases.
+  template <int BLOCK, class S>
+  __device__ static void cta_batch_dependency(S& sm, int cnt, const Launch& L, unsigned long long* st) {
+    const Instance& I = sm.I;
+    const int t = threadIdx.x;
+    int v = 0, lower = 0, upper = 0, s = 0;
+    bool ready = false;
+    if (t < cnt) {
+      const int item = sm.items[t];
+      v = item >= 0 ? item : ~item;
+      ready = item < 0 || atomicSub(I.gc_wait + v, 1) == 1;
+      s = ldg(I.row_ptr + v);
+      if (ready) {
+        lower = ldg(I.gc_mid + v);
+        upper = ldg(I.row_ptr + v + 1) - s - lower;
+      }
+      sm.start[t] = s;
+    }
+    int64_t edges = 0;
+    int colour = -1;
+    constexpr int R = LbsRun<BLOCK>::R;
+    // First fit is at most the number of smaller neighbours, so a vertex needs lower + 1 colour
+    // bits.  When the batch's bitmaps fit in shared memory (2 words per thread) one pass over the
+    // smaller neighbours decides every colour; otherwise windows of 64 colours are examined in turn.
+    int words_total;
+    const int woff = block_exclusive_scan<BLOCK>(ready ? (lower + 32) >> 5 : 0, sm.tmp, words_total);
+    if (words_total <= 2 * BLOCK) {
+      if (t < cnt) {
+        sm.aux[t] = woff;
+        sm.items[t] = ready ? (lower + 32) >> 5 : 0;  // the task items are in registers by now
+      }
+      for (int k = t; k < words_total; k += BLOCK) sm.x.bits[k] = 0u;
+      int total;
+      const int off = block_exclusive_scan<BLOCK>(ready ? lower : 0, sm.tmp, total);  // ends with a barrier
+      if (t < cnt) sm.off[t] = off;
+      __syncthreads();
+      for (int r = 0; r < total; r += BLOCK * R) {
+        int owner[R], nb[R], c[R];
+        lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
+#pragma unroll
+        for (int j = 0; j < R; ++j) c[j] = owner[j] >= 0 ? __ldcg(I.color + nb[j]) : -1;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          if (owner[j] >= 0 && c[j] >= 0 && (c[j] >> 5) < sm.items[owner[j]])
+            atomicOr(&sm.x.bits[sm.aux[owner[j]] + (c[j] >> 5)], 1u << (c[j] & 31));
+      }
+      edges += total;
+      __syncthreads();
+      if (ready)
+        for (int w = 0; colour < 0; ++w) {  // a zero bit exists among the first lower + 1
+          const unsigned free_bits = ~sm.x.bits[woff + w];
+          if (free_bits) colour = 32 * w + __ffs(free_bits) - 1;
+        }
+      __syncthreads();
+    } else {
+      bool active = ready;
+      for (int base = 0;; base += kGcWindow) {
+        int total;
+        const int off = block_exclusive_scan<BLOCK>(active ? lower : 0, sm.tmp, total);
+        if (t < cnt) {
+          sm.off[t] = off;
+          sm.x.bits[2 * t] = 0u;
+          sm.x.bits[2 * t + 1] = 0u;
+        }
+        if (total == 0 && base > 0) break;
+        __syncthreads();
+        for (int r = 0; r < total; r += BLOCK * R) {
+          int owner[R], nb[R], c[R];
+          lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
+#pragma unroll
+          for (int j = 0; j < R; ++j) c[j] = owner[j] >= 0 ? __ldcg(I.color + nb[j]) : -1;
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            const int rel = c[j] - base;
+            if (owner[j] >= 0 && rel >= 0 && rel < kGcWindow)
+              atomicOr(&sm.x.bits[2 * owner[j] + (rel >> 5)], 1u << (rel & 31));
+          }
+        }
+        edges += total;
+        __syncthreads();
+        bool again = false;
+        if (active) {
+          const unsigned long long used = ((unsigned long long)sm.x.bits[2 * t + 1] << 32) | sm.x.bits[2 * t];
+          if (~used) colour = base + __ffsll((long long)~used) - 1;
+          else again = true;
+        }
+        active = again;
+        if (!__syncthreads_or(again)) break;
+      }
+    }
+    if (ready) {
+      st_relaxed(I.color + v, colour);
+      __threadfence();  // the colour is visible before any decrement below can make a neighbour ready
+    }
+    // count down the larger neighbours of every ready vertex; the decrement that reaches zero
+    // pushes the neighbour
+    if (t < cnt) {
+      sm.start[t] = s + lower;
+      sm.aux[t] = v;
+    }
+    int total;
+    const int off = block_exclusive_scan<BLOCK>(upper, sm.tmp, total);
+    if (t < cnt) sm.off[t] = off;
+    __syncthreads();
+    __threadfence();  // (the other threads' colour writes of this batch, ordered by the barrier)
+    for (int r = 0; r < total; r += BLOCK * R) {
+      int owner[R], nb[R];
+      lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const bool go = owner[j] >= 0 && atomicSub(I.gc_wait + nb[j], 1) == 1;
+        cta_push(sm, go, ~nb[j]);
+      }
+      __syncthreads();
+      if (sm.npush > 0) cta_flush<BLOCK>(sm, I, 0, L, st);
+    }
+    __syncthreads();
+    if (t == 0) {
+      st[kStatTasks] += cnt;
+      st[kStatEdges] += edges + total;
+    }
+    cta_flush<BLOCK>(sm, I, cnt, L, st);
+  }
+
   template <int BLOCK, class S>
   __device__ static void cta_batch(S& sm, int cnt, const Launch& L, unsigned long long* st) {
+    if (sm.I.gc_wait) {
+      cta_batch_dependency<BLOCK>(sm, cnt, L, st);
+      return;
+    }
     const Instance& I = sm.I;
     const int t = threadIdx.x;
     int v = 0, deg = 0, s = 0;
@@ -153,8 +298,56 @@ struct GcBody {
     return threadIdx.x == 0 ? (instance_quiescent(sm.I) ? 1 : 0) : 0;
   }
 
+  // Dependency-ordered mode for a warp worker (see cta_batch_dependency).
+  __device__ static void warp_item_dependency(WarpSmem& ws, const Instance& I, int item, const Launch& L,
+                                              unsigned long long* st) {
+    const int lane = threadIdx.x & 31;
+    const int v = item >= 0 ? item : ~item;
+    int ready = 0;
+    if (lane == 0) ready = item < 0 || atomicSub(I.gc_wait + v, 1) == 1;
+    if (!__shfl_sync(0xffffffffu, ready, 0)) return;
+    const int s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
+    const int m = s + ldg(I.gc_mid + v);  // [s, m): smaller neighbours, [m, e): larger ones
+    int64_t edges = 0;
+    int colour = -1;
+    for (int base = 0; colour < 0; base += kGcWindow) {
+      unsigned lo = 0, hi = 0;
+      for (int k = s + lane; k < m; k += 32) {
+        const int rel = __ldcg(I.color + ldg(I.col + k)) - base;
+        if (rel >= 0 && rel < 32) lo |= 1u << rel;
+        else if (rel >= 32 && rel < 64) hi |= 1u << (rel - 32);
+      }
+      edges += m - s;
+      lo = __reduce_or_sync(0xffffffffu, lo);
+      hi = __reduce_or_sync(0xffffffffu, hi);
+      const unsigned long long used = ((unsigned long long)hi << 32) | lo;
+      if (~used) colour = base + __ffsll((long long)~used) - 1;
+    }
+    if (lane == 0) {
+      st_relaxed(I.color + v, colour);
+      __threadfence();  // the colour is visible before any decrement below
+    }
+    __syncwarp();
+    for (int k0 = m; k0 < e; k0 += 32) {
+      const int k = k0 + lane;
+      int w = 0;
+      bool go = false;
+      if (k < e) {
+        w = ldg(I.col + k);
+        go = atomicSub(I.gc_wait + w, 1) == 1;
+      }
+      warp_push(ws, go, ~w);
+      if (ws.npush > 0) warp_flush(ws, I, 0, L, st);  // publish a ready vertex right away
+    }
+    if (lane == 0) st[kStatEdges] += edges + (e - m);
+  }
+
   __device__ static void warp_item(WarpSmem& ws, const Instance& I, int item, const Launch& L,
                                    unsigned long long* st) {
+    if (I.gc_wait) {
+      warp_item_dependency(ws, I, item, L, st);
+      return;
+    }
     const int lane = threadIdx.x & 31;
     const bool assign = item >= 0;
     const int v = assign ? item : ~item;

@@ -101,6 +101,9 @@ struct Instance {
   unsigned* orphans[2];  // serving: pending tickets recorded at a pause, by epoch parity
   uint32_t orphan_cap;
   int32_t gc_ordered;    // colouring: 1 = an assign avoids only the colours of smaller-id neighbours
+  int32_t* gc_wait;      // colouring in dependency order: 1 + smaller-id neighbours not coloured yet
+  const int32_t* gc_mid; // colouring in dependency order: smaller-id neighbours of each vertex, which
+                         // `col` lists first in its row (the larger ones follow)
   double* cert_y;        // PageRank in batches and serving: FP64 scratch (n) of the output certificate
   int32_t* expanded;     // BFS (optional): the smallest depth at which each vertex has been expanded
   double exact_sum;      // PageRank: n - alpha * (isolated vertices), the fixed point's sum

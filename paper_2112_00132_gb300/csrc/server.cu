@@ -239,6 +239,7 @@ int atos_server_create(const atos_graph_t* graphs, int32_t ngraphs, int32_t max_
   else atos_queue_config(&cfg, nullptr);
   if (cfg.strategy != ATOS_PERSISTENT || warp_hosted(cfg.worker_size) || !worker_supported(cfg.worker_size))
     return ATOS_ERR_UNSUPPORTED;  // serving pauses CTA workers only
+  if (cfg.flags & ATOS_FLAG_GC_DEPENDENCY) return ATOS_ERR_UNSUPPORTED;  // atos_color only
   if (cfg.fetch_size < 1 || cfg.fetch_size > cfg.worker_size) return ATOS_ERR_INVALID_ARG;
   atos_server_s* s = new (std::nothrow) atos_server_s();
   if (!s) return ATOS_ERR_OOM;

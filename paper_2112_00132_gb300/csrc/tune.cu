@@ -7,7 +7,9 @@
 // Candidates are run on the caller's graph through the public entry points (each run is checked:
 // a candidate that fails, or a PageRank candidate whose FP64 error bound exceeds
 // ATOS_TUNE_PR_MAX_ERROR, is skipped), timed with the library's own CUDA events, best of
-// `repeats` runs.  The winner is cached per graph class -- application, log2 of the vertex count,
+// `repeats` runs.  A colouring qualifies only when its colour count is within
+// ATOS_TUNE_GC_MAX_COLOR_RATIO of the fewest any candidate reached, so a fast colouring with many
+// more colours does not win.  The winner is cached per graph class -- application, log2 of the vertex count,
 // log2 of the average degree and log2 of the max/average degree ratio -- so graphs of the same
 // shape reuse it through atos_tuned_config without a new sweep.
 #include <cuda_runtime.h>
@@ -58,6 +60,23 @@ std::vector<atos_config> candidates(int app, int nsrc) {
   out.push_back(make("persist-warp", 0, 0, -1));
   out.push_back(make("discrete-cta", 0, 0, -1));
   out.push_back(make("bsp", 0, 0, -1));
+  {
+    atos_config c = make("bsp", 0, 0, -1);  // the level loop on the device (conditional graph node)
+    c.flags |= ATOS_FLAG_BSP_DEVICE_LOOP;
+    out.push_back(c);
+  }
+  if (app == ATOS_APP_COLOR) {
+    // dependency-ordered colouring: exactly serial first fit in id order, one task per vertex
+    for (int w : {256, 512, 1024})
+      for (int f : {w, 64}) {  // small pops spread the long dependency chains' ready vertices
+        atos_config c = make(nullptr, w, f, ATOS_FETCH_GREEDY);
+        c.flags |= ATOS_FLAG_GC_DEPENDENCY;
+        out.push_back(c);
+      }
+    atos_config c = make(nullptr, 32, 32, ATOS_FETCH_GREEDY);
+    c.flags |= ATOS_FLAG_GC_DEPENDENCY;
+    out.push_back(c);
+  }
   if (app == ATOS_APP_PAGERANK) {
     for (int w : {512, 1024})
       for (int cs : {8, 16, 64}) {
@@ -122,29 +141,43 @@ int atos_autotune(atos_graph_t g, int32_t app, const int32_t* sources, int32_t n
   double best_t = INFINITY;
   atos_config best_c;
   atos_queue_config(&best_c, nullptr);
-  int tried = 0;
+  struct Tried {
+    atos_config c;
+    double ms;
+    int32_t colors;
+  };
+  std::vector<Tried> done;
   for (const atos_config& c : candidates(app, app == ATOS_APP_BFS ? nsrc : 1)) {
     double t = INFINITY;
+    int32_t colors = 0;
     bool ok = true;
     for (int r = 0; r <= repeats && ok; ++r) {  // run 0 warms up
-      atos_stats st;
+      atos_stats st = {};
       int rc;
       if (app == ATOS_APP_BFS) rc = atos_bfs(g, sources, nsrc, (int32_t*)scratch_out, &c, stream, &st);
       else if (app == ATOS_APP_PAGERANK) rc = atos_pagerank(g, 0.85f, 1e-9f, (float*)scratch_out, &c, stream, &st);
       else rc = atos_color(g, (int32_t*)scratch_out, nullptr, &c, stream, &st);
+      colors = st.num_colors;
       if (rc != ATOS_OK) ok = false;
       else if (app == ATOS_APP_PAGERANK && !(st.error_bound <= ATOS_TUNE_PR_MAX_ERROR)) ok = false;
       else if (r > 0) t = std::min(t, st.ms);
-      else if (st.ms > 4.0 * best_t) ok = false;  // the warm-up alone is far slower: not a contender
+      // the warm-up alone is far slower: not a contender (colourings are judged on their colour
+      // count first, so every one of them is timed)
+      else if (app != ATOS_APP_COLOR && st.ms > 4.0 * best_t) ok = false;
     }
     if (!ok) continue;
-    tried++;
-    if (t < best_t) {
-      best_t = t;
-      best_c = c;
-    }
+    done.push_back(Tried{c, t, colors});
+    if (t < best_t) best_t = t;
   }
-  if (!tried) return ATOS_ERR_CUDA;
+  if (done.empty()) return ATOS_ERR_CUDA;
+  // colourings: only those within ATOS_TUNE_GC_MAX_COLOR_RATIO of the fewest colours qualify
+  int32_t fewest = INT32_MAX;
+  for (const Tried& d : done) fewest = std::min(fewest, d.colors);
+  best_t = INFINITY;
+  for (const Tried& d : done) {
+    if (app == ATOS_APP_COLOR && (double)d.colors > ATOS_TUNE_GC_MAX_COLOR_RATIO * (double)fewest) continue;
+    if (d.ms < best_t) best_t = d.ms, best_c = d.c;
+  }
   *best = best_c;
   if (best_ms) *best_ms = best_t;
   std::lock_guard<std::mutex> lock(g_cache_mu);

@@ -382,3 +382,57 @@ def test_throughput_timeline(atos):
         assert tasks.sum() == 0 and edges.sum() == 0
         G.timeline()
         G.pagerank(ALPHA, EPS)
+
+
+@pytest.mark.parametrize("gname", ["rmat12", "rmat11_del", "grid97x61_del", "star1000", "clique40", "two_parts",
+                                   "path300", "single", "isolated3"])
+def test_color_dependency_equals_serial_greedy(atos, graphs, gname):
+    """ATOS_FLAG_GC_DEPENDENCY: every vertex is coloured once, after its smaller-id neighbours, so
+    the colouring equals serial first fit in id order exactly -- on the input ids, and on the
+    spread-id copy in that copy's id order -- for every worker shape and strategy (BSP ignores the
+    flag and is checked for properness only)."""
+    g = graphs[gname]
+    ref, kref = oracle.greedy_color(g)
+    with atos.Graph.from_csr(g) as G:
+        perm, _ = G.spread_layout()
+        ref_sp, kref_sp = oracle.greedy_color(g, order=np.argsort(perm))
+        for cname, cfg in configs(atos).items():
+            for spread in (False, True):
+                cfg.flags = (cfg.flags & ~atos.FLAG_SPREAD_IDS) | atos.FLAG_GC_DEPENDENCY | (
+                    atos.FLAG_SPREAD_IDS if spread else 0)
+                colors, k, st = G.color(cfg=cfg)
+                c = colors.cpu().numpy()
+                assert st.status == 0, f"{gname}/{cname}/{spread}"
+                if cname.startswith("bsp"):
+                    assert oracle.check_coloring(g, c)[0] == 0
+                    continue
+                want, kw = (ref_sp, kref_sp) if spread else (ref, kref)
+                bad = np.flatnonzero(c != want)
+                assert bad.size == 0, f"{gname}/{cname}/spread={spread}: {bad.size} colours differ"
+                assert k == kw
+                assert st.tasks <= 2 * g.n  # one release per vertex, at most one ready push
+                assert G.scratch_check()[1] == 0
+
+
+def test_color_dependency_full_size(atos):
+    """Dependency-ordered colouring on RMAT 22 (hubs have the smallest ids) and on the 2048 x 2048
+    grid (its longest increasing-id path has 4094 steps): exactly serial first fit in id order."""
+    for g in (gg.rmat(22, 16, seed=1), gg.grid(2048, delete_frac=0.1, seed=1)):
+        ref, kref = oracle.greedy_color(g)
+        with atos.Graph.from_csr(g) as G:
+            colors, k, st = G.color(cfg=atos.queue_config(worker_size=512, fetch_size=512,
+                                                          flags=atos.FLAG_GC_DEPENDENCY))
+        assert st.status == 0 and k == kref
+        assert np.array_equal(colors.cpu().numpy(), ref)
+
+
+def test_color_dependency_rejected_by_batches_and_servers(atos):
+    g = gg.rmat(10, 16, seed=3)
+    cfg = atos.queue_config(flags=atos.FLAG_GC_DEPENDENCY)
+    with atos.Graph.from_csr(g) as G:
+        with pytest.raises(atos.AtosError) as e:
+            atos.Batch([G], [("color", 0)], cfg)
+        assert e.value.status == atos.abi.ERR_UNSUPPORTED
+        with pytest.raises(atos.AtosError) as e:
+            atos.Server([G], max_slots=4, budget_bytes=1 << 26, cfg=cfg)
+        assert e.value.status == atos.abi.ERR_UNSUPPORTED
