@@ -459,8 +459,12 @@ def compare_rmat(atos, G, g, srcs, depths, rank_t, colors, stream, m):
     bfs = {"persistent_batched_ms": round(mean(m["bfs_ms"]), 3),
            "persistent_unbatched_ms": round(timed_ms(unbatched, stream, reps=1), 3)}
     for name, cfg in bsp_configs(atos).items():
-        bfs[f"bsp_all_sources_{name}_ms"] = round(timed_ms(
+        # sources in groups that keep their depth arrays L2-resident (the default), and all at once
+        bfs[f"bsp_grouped_{name}_ms"] = round(timed_ms(
             lambda: G.bfs(srcs, depths, cfg=cfg, stream=stream, stats=False), stream), 3)
+        every = q("bsp", flags=cfg.flags, window=len(srcs))
+        bfs[f"bsp_all_sources_{name}_ms"] = round(timed_ms(
+            lambda: G.bfs(srcs, depths, cfg=every, stream=stream, stats=False), stream, reps=1), 3)
     per_source = q("bsp", flags=atos.FLAG_BSP_PER_SOURCE)
     bfs["bsp_per_source_host_ms"] = round(timed_ms(
         lambda: G.bfs(srcs, depths, cfg=per_source, stream=stream, stats=False), stream, reps=1), 3)

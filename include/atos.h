@@ -113,8 +113,10 @@ extern "C" {
                                      reads the next frontier's size after every level. */
 
 #define ATOS_FLAG_BSP_PER_SOURCE 128u /* ATOS_BSP BFS: one source after another.  Without it the
-                                     frontiers of all sources advance together, one launch of each
-                                     level kernel per level for all of them. */
+                                     frontiers of a group of sources advance together, one launch of
+                                     each level kernel per level for the whole group: cfg->window
+                                     sources (0 = as many as keep their depth arrays within about
+                                     64 MB, half of L2, as the persistent strategy's window). */
 
 #define ATOS_FLAG_GC_DEPENDENCY 256u /* atos_color (persistent and discrete strategies): colour each
                                      vertex once, after all of its smaller-id neighbours (in the ids
@@ -137,7 +139,8 @@ typedef struct atos_config {
   int32_t num_blocks;     /* persistent grid size; 0 = all CTAs that fit at once (occupancy x SMs) */
   int32_t check_size;     /* PageRank: vertex ids checked per task (Check_Size of Algorithm 4);
                              0 = 32 */
-  int32_t window;         /* batched runs: instances active at once; 0 = automatic */
+  int32_t window;         /* batched runs: instances active at once; 0 = automatic (also the
+                             group size of a multi-source BSP BFS) */
   uint32_t flags;         /* ATOS_FLAG_* */
   int64_t queue_capacity; /* ring slots per instance, rounded up to a power of two; 0 = automatic */
   int64_t spin_limit_ns;  /* budget of any single device-side wait; 0 = 4 seconds */

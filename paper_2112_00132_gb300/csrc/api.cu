@@ -227,7 +227,7 @@ int ensure_bsp(atos_graph_s* g, size_t bytes) {
 
 // One BSP run on g's comparator scratch; accumulates into *acc.
 int run_bsp(atos_graph_s* g, const BspRun& r, cudaStream_t st, BspResult* acc) {
-  int rc = ensure_bsp(g, bsp_scratch_bytes(r.app, r.n, r.nsrc));
+  int rc = ensure_bsp(g, bsp_scratch_bytes(r.app, r.n, r.nnz, r.nsrc));
   if (rc) return rc;
   BspResult one = {};
   rc = bsp_run(r, g->d_bsp, g->bsp_bytes, g->h_bsp, &g->bsp_graphs, st, acc ? &one : nullptr);
@@ -640,22 +640,27 @@ int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* dept
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = g->n;
   if (cfg.strategy == ATOS_BSP) {
-    // Algorithm 1: every source's frontier advances in the same launches, one level at a time
-    // (or one source after another with ATOS_FLAG_BSP_PER_SOURCE)
+    // Algorithm 1: the frontiers of a group of sources advance in the same launches, one level at
+    // a time (one source after another with ATOS_FLAG_BSP_PER_SOURCE)
     rc = clear_timeline(g, st);
     if (rc) return rc;
-    const bool per_source = (cfg.flags & ATOS_FLAG_BSP_PER_SOURCE) != 0;
+    // sources advance together in groups of cfg.window (0: as many as keep their depth arrays
+    // within about half of L2, as for the persistent strategy)
+    int32_t group = nsrc;
+    if (cfg.flags & ATOS_FLAG_BSP_PER_SOURCE) group = 1;
+    else if (cfg.window > 0) group = std::min(cfg.window, nsrc);
+    else group = (int32_t)std::max<int64_t>(1, std::min<int64_t>(nsrc, (64LL << 20) / (4 * n + 1)));
     BspRun r = {};
     r.app = kAppBfs;
-    r.row_ptr = g->row_ptr, r.col = g->col, r.n = g->n;
+    r.row_ptr = g->row_ptr, r.col = g->col, r.n = g->n, r.nnz = g->nnz;
     r.device_loop = (cfg.flags & ATOS_FLAG_BSP_DEVICE_LOOP) != 0;
-    rc = ensure_bsp(g, bsp_scratch_bytes(kAppBfs, g->n, per_source ? 1 : nsrc));
+    rc = ensure_bsp(g, bsp_scratch_bytes(kAppBfs, g->n, g->nnz, group));
     if (rc) return rc;
     ATOS_TRY(cudaEventRecord(g->s.ev0, st));
     BspResult acc = {};
-    for (int32_t i = 0; i < nsrc; i += per_source ? 1 : nsrc) {
+    for (int32_t i = 0; i < nsrc; i += group) {
       r.sources = sources + i;
-      r.nsrc = per_source ? 1 : nsrc;
+      r.nsrc = std::min(group, nsrc - i);
       r.depth = depths + (size_t)i * n;
       rc = run_bsp(g, r, st, stats ? &acc : nullptr);
       if (rc) return rc;
@@ -731,7 +736,7 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
   const bool bsp = cfg.strategy == ATOS_BSP;
   if (bsp) {
     cfg.strategy = ATOS_PERSISTENT;  // the prepare step below is shared; the loop is not run
-    rc = ensure_bsp(g, bsp_scratch_bytes(kAppPr, n, 1));
+    rc = ensure_bsp(g, bsp_scratch_bytes(kAppPr, n, g->nnz, 1));
     if (rc) return rc;
   }
   const uint32_t cap = ring_capacity(cfg, n, (uint32_t)n);
@@ -770,7 +775,7 @@ int atos_pagerank(atos_graph_t g, float alpha, float eps, float* rank, const ato
     ATOS_TRY(launch_pr_init(g->s.d_insts, 1, g->nnz, st));
     BspRun r = {};
     r.app = kAppPr;
-    r.row_ptr = I.row_ptr, r.col = I.col, r.n = n;
+    r.row_ptr = I.row_ptr, r.col = I.col, r.n = n, r.nnz = g->nnz;
     r.rank = I.rank, r.res = g->d_res, r.alpha = alpha, r.eps = eps;
     r.device_loop = (cfg.flags & ATOS_FLAG_BSP_DEVICE_LOOP) != 0;
     rc = run_bsp(g, r, st, stats ? &bsp_acc : nullptr);
@@ -817,7 +822,7 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
   cudaStream_t st = (cudaStream_t)stream;
   const int32_t n = g->n;
   if (cfg.strategy == ATOS_BSP) {
-    rc = ensure_bsp(g, bsp_scratch_bytes(kAppGc, n, 1));
+    rc = ensure_bsp(g, bsp_scratch_bytes(kAppGc, n, g->nnz, 1));
     if (rc) return rc;
     const bool spread_bsp = (cfg.flags & ATOS_FLAG_SPREAD_IDS) != 0;
     if (spread_bsp) {
@@ -831,6 +836,7 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
     BspRun r = {};
     r.app = kAppGc;
     r.row_ptr = spread_bsp ? g->sp_row_ptr : g->row_ptr, r.col = spread_bsp ? g->sp_col : g->col, r.n = n;
+    r.nnz = g->nnz;
     r.color = out;
     r.device_loop = (cfg.flags & ATOS_FLAG_BSP_DEVICE_LOOP) != 0;
     BspResult acc = {};

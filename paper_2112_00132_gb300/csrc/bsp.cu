@@ -24,7 +24,7 @@ namespace bsp {
 constexpr int kBlock = 256;
 constexpr int kPerThread = 4;
 constexpr int kChunk = kBlock * kPerThread;  // items per scan chunk, edges per CTA per advance step
-constexpr int kPerLevel[3] = {6, 7, 3};      // kernels in a level of BFS, PageRank, colouring
+constexpr int kPerLevel[3] = {7, 8, 3};      // kernels in a level of BFS, PageRank, colouring
 
 // The control block: level state first (what the host reads back), then the run's parameters.
 struct Ctl {
@@ -45,6 +45,7 @@ struct Ctl {
   void* fr[2];       // BFS: uint64 (source << 32 | vertex); PageRank, colouring: int32 vertex
   long long* offs;   // scan of the current frontier's degrees (F + 1 entries)
   long long* bsums;  // per-chunk sums of the scan
+  int32_t* chunk_lo; // per edge chunk of kChunk edges: the frontier item owning its first edge
   float* share;      // PageRank: alpha * residue / degree per frontier item
   int32_t* sources;  // BFS: the nsrc sources
 };
@@ -170,6 +171,42 @@ __global__ void scan_add_kernel(Ctl* c) {
     offs[i] += bsums[i / kChunk];
 }
 
+// Owner of each edge chunk's first edge: item i writes itself for every chunk that starts in its
+// edge range [offs[i], offs[i + 1]) (a parallel scatter instead of a binary search per chunk).
+__global__ void mark_chunks_kernel(Ctl* c) {
+  const long long F = c->F[c->cur];
+  const long long* __restrict__ offs = c->offs;
+  int32_t* __restrict__ lo = c->chunk_lo;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < F; i += (long long)gridDim.x * blockDim.x) {
+    const long long a = offs[i], b = offs[i + 1];
+    for (long long ch = (a + kChunk - 1) / kChunk; ch * kChunk < b; ++ch) lo[ch] = (int32_t)i;
+  }
+}
+
+// Stages the frontier items that own the edges of chunk `ch` (shared: their scan offsets, item
+// words and row starts); returns the first item and the count through *lo / *cnt, or cnt > kChunk
+// + 1 when the range (degree-0 items included) does not fit, then nothing is staged.
+template <class Item, class RowOf>
+__device__ __forceinline__ void stage_chunk(const Ctl* c, long long ch, long long nchunks, long long F,
+                                            const Item* __restrict__ fr, long long* s_off, Item* s_item,
+                                            int* s_start, long long* s_lo, long long* s_cnt, RowOf row_of) {
+  if (threadIdx.x == 0) {
+    const long long lo = c->chunk_lo[ch];
+    const long long hi = ch + 1 < nchunks ? c->chunk_lo[ch + 1] : F - 1;
+    *s_lo = lo;
+    *s_cnt = hi - lo + 1;
+  }
+  __syncthreads();
+  const long long lo = *s_lo, cnt = *s_cnt;
+  if (cnt <= kChunk + 1)
+    for (int k = threadIdx.x; k < cnt; k += kBlock) {
+      s_off[k] = c->offs[lo + k];
+      s_item[k] = fr[lo + k];
+      s_start[k] = __ldg(c->row_ptr + row_of(s_item[k]));
+    }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------- level end
 
 // One thread: account the level, make the next frontier current, decide whether to go on.
@@ -239,23 +276,12 @@ __global__ void __launch_bounds__(kBlock) bfs_advance_kernel(Ctl* c) {
   const long long nchunks = (total + kChunk - 1) / kChunk;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long e0 = ch * kChunk, e1 = min(total, e0 + kChunk);
-    if (threadIdx.x == 0) {
-      const long long lo = owner64(offs, F, e0);
-      s_lo = lo;
-      s_cnt = owner64(offs, F, e1 - 1) - lo + 1;
-    }
-    __syncthreads();
+    stage_chunk(c, ch, nchunks, F, fr, s_off, s_item, s_start, &s_lo, &s_cnt,
+                [](unsigned long long it) { return (int)(unsigned)it; });
     const long long lo = s_lo, cnt = s_cnt;
     // items of degree 0 can make the owning range longer than the chunk; such a chunk searches
-    // the global offsets instead of a staged copy
+    // the global offsets of its range instead of a staged copy
     const bool staged = cnt <= kChunk + 1;
-    if (staged)
-      for (int k = threadIdx.x; k < cnt; k += kBlock) {
-        s_off[k] = offs[lo + k];
-        s_item[k] = fr[lo + k];
-        s_start[k] = __ldg(row_ptr + (int)(unsigned)s_item[k]);
-      }
-    __syncthreads();
     // each thread: kPerThread consecutive edges, one owner search
     const long long ea = e0 + (long long)threadIdx.x * kPerThread;
     long long i = 0;
@@ -266,6 +292,7 @@ __global__ void __launch_bounds__(kBlock) bfs_advance_kernel(Ctl* c) {
     for (int r = 0; r < kPerThread; ++r) {
       const long long e = ea + r;
       nbs[r] = -1;
+      srcs[r] = 0;
       if (e < e1) {
         if (staged) {
           while (i + 1 < cnt && s_off[i + 1] <= e) ++i;
@@ -323,6 +350,10 @@ __global__ void pr_take_kernel(Ctl* c) {
 // Load-balanced scatter over the frontier's edges: each thread kPerThread consecutive edges, one
 // owner search.
 __global__ void __launch_bounds__(kBlock) pr_scatter_kernel(Ctl* c) {
+  __shared__ long long s_off[kChunk + 1];
+  __shared__ int32_t s_item[kChunk + 1];
+  __shared__ int s_start[kChunk + 1];
+  __shared__ long long s_lo, s_cnt;
   const long long F = c->F[c->cur];
   const long long total = c->total;
   const int32_t* __restrict__ fr = (const int32_t*)c->fr[c->cur];
@@ -334,18 +365,29 @@ __global__ void __launch_bounds__(kBlock) pr_scatter_kernel(Ctl* c) {
   const long long nchunks = (total + kChunk - 1) / kChunk;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long e0 = ch * kChunk, e1 = min(total, e0 + kChunk);
+    stage_chunk(c, ch, nchunks, F, fr, s_off, s_item, s_start, &s_lo, &s_cnt, [](int32_t v) { return v; });
+    const long long lo = s_lo, cnt = s_cnt;
+    const bool staged = cnt <= kChunk + 1;
+    // each thread: kPerThread consecutive edges, one owner search
     const long long ea = e0 + (long long)threadIdx.x * kPerThread;
-    if (ea >= e1) continue;
-    long long i = owner64(offs, F, ea);
+    if (ea < e1) {
+      long long i = staged ? owner64(s_off, cnt, ea) : owner64(offs + lo, cnt, ea);
 #pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-      const long long e = ea + k;
-      if (e >= e1) break;
-      while (i + 1 < F && offs[i + 1] <= e) ++i;
-      const int v = fr[i];
-      const int nb = __ldg(col + __ldg(row_ptr + v) + (e - offs[i]));
-      red_add_f32(res + nb, share[i]);
+      for (int k = 0; k < kPerThread; ++k) {
+        const long long e = ea + k;
+        if (e >= e1) break;
+        int nb;
+        if (staged) {
+          while (i + 1 < cnt && s_off[i + 1] <= e) ++i;
+          nb = __ldg(col + s_start[i] + (e - s_off[i]));
+        } else {
+          while (i + 1 < cnt && offs[lo + i + 1] <= e) ++i;
+          nb = __ldg(col + __ldg(row_ptr + fr[lo + i]) + (e - offs[lo + i]));
+        }
+        red_add_f32(res + nb, share[lo + i]);
+      }
     }
+    __syncthreads();
   }
 }
 
@@ -508,11 +550,13 @@ cudaError_t scan_inplace(int32_t* a, int32_t F, int32_t* bsums, cudaStream_t s) 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t ctl, fr0, fr1, offs, bsums, share, sources, total;
+  size_t ctl, fr0, fr1, offs, bsums, chunk_lo, share, sources, total;
 };
 
-Layout layout_for(int app, int32_t n, int32_t nsrc) {
+Layout layout_for(int app, int32_t n, int64_t nnz, int32_t nsrc) {
   const size_t items = app == kAppBfs ? (size_t)n * (size_t)std::max(nsrc, 1) : (size_t)n;
+  // a level scans at most every source's whole CSR: nsrc * nnz edges
+  const size_t edges = app == kAppBfs ? (size_t)nnz * (size_t)std::max(nsrc, 1) : (size_t)nnz;
   const size_t isz = app == kAppBfs ? 8 : 4;
   Layout L;
   size_t p = 0;
@@ -521,6 +565,7 @@ Layout layout_for(int app, int32_t n, int32_t nsrc) {
   L.fr1 = p, p += align256(isz * std::max<size_t>(items, 1));
   L.offs = p, p += app == kAppGc ? 0 : align256(8 * (items + 1));
   L.bsums = p, p += app == kAppGc ? 0 : align256(8 * (items / kChunk + 2));
+  L.chunk_lo = p, p += app == kAppGc ? 0 : align256(4 * (edges / kChunk + 2));
   L.share = p, p += app == kAppPr ? align256(4 * std::max<size_t>(items, 1)) : 0;
   L.sources = p, p += app == kAppBfs ? align256(4 * (size_t)std::max(nsrc, 1)) : 0;
   L.total = p;
@@ -546,12 +591,14 @@ cudaError_t launch_level(int app, Ctl* c, const Grids& g, cudaGraphConditionalHa
     scan_chunks_kernel<<<g.items, kBlock, 0, s>>>(c);
     scan_top_kernel<<<1, 1024, 0, s>>>(c);
     scan_add_kernel<<<g.items, kBlock, 0, s>>>(c);
+    mark_chunks_kernel<<<g.items, kBlock, 0, s>>>(c);
     bfs_advance_kernel<<<g.edges, kBlock, 0, s>>>(c);
   } else if (app == kAppPr) {
     pr_take_kernel<<<g.items, kBlock, 0, s>>>(c);
     scan_chunks_kernel<<<g.items, kBlock, 0, s>>>(c);
     scan_top_kernel<<<1, 1024, 0, s>>>(c);
     scan_add_kernel<<<g.items, kBlock, 0, s>>>(c);
+    mark_chunks_kernel<<<g.items, kBlock, 0, s>>>(c);
     pr_scatter_kernel<<<g.edges, kBlock, 0, s>>>(c);
     pr_filter_kernel<<<g.items, kBlock, 0, s>>>(c);
   } else {
@@ -607,7 +654,9 @@ void BspGraphs::release() {
   scratch = nullptr;
 }
 
-size_t bsp_scratch_bytes(int app, int32_t n, int32_t nsrc) { return bsp::layout_for(app, n, nsrc).total; }
+size_t bsp_scratch_bytes(int app, int32_t n, int64_t nnz, int32_t nsrc) {
+  return bsp::layout_for(app, n, nnz, nsrc).total;
+}
 
 size_t bsp_host_bytes() { return 2 * bsp::align256(sizeof(bsp::Ctl)); }
 
@@ -615,7 +664,7 @@ int bsp_run(const BspRun& r, void* scratch, size_t scratch_bytes, void* host_buf
             BspResult* result) {
   using namespace bsp;
   const int nsrc = r.app == kAppBfs ? r.nsrc : 1;
-  const Layout Lo = layout_for(r.app, r.n, nsrc);
+  const Layout Lo = layout_for(r.app, r.n, r.nnz, nsrc);
   if (!scratch || scratch_bytes < Lo.total || !host_buf || r.n < 1 || nsrc < 1) return ATOS_ERR_INVALID_ARG;
   char* base = (char*)scratch;
   Ctl* d_ctl = (Ctl*)(base + Lo.ctl);
@@ -631,6 +680,7 @@ int bsp_run(const BspRun& r, void* scratch, size_t scratch_bytes, void* host_buf
   c.fr[0] = base + Lo.fr0, c.fr[1] = base + Lo.fr1;
   c.offs = (long long*)(base + Lo.offs);
   c.bsums = (long long*)(base + Lo.bsums);
+  c.chunk_lo = (int32_t*)(base + Lo.chunk_lo);
   c.share = (float*)(base + Lo.share);
   c.sources = (int32_t*)(base + Lo.sources);
   // the pinned image may still be in flight from the previous run on this scratch

@@ -27,6 +27,7 @@ struct BspRun {
   const int32_t* row_ptr;   // device CSR of the graph the run works on
   const int32_t* col;
   int32_t n;
+  int64_t nnz;
   const int32_t* sources;   // BFS: HOST array of nsrc source vertices
   int32_t nsrc;
   int32_t* depth;           // BFS: DEVICE nsrc x n depths
@@ -54,7 +55,7 @@ struct BspGraphs {
 };
 
 // Bytes of device scratch a run of `app` needs (frontiers, scan offsets, control block).
-size_t bsp_scratch_bytes(int app, int32_t n, int32_t nsrc);
+size_t bsp_scratch_bytes(int app, int32_t n, int64_t nnz, int32_t nsrc);
 
 // Runs r on `s`.  scratch: bsp_scratch_bytes(...) bytes of device memory; host_buf: pinned host
 // memory of at least bsp_host_bytes() bytes.  With `result` non-NULL (or in the host-driven form)

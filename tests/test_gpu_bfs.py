@@ -156,14 +156,17 @@ def test_bfs_full_size_rmat22_64_sources(atos):
         assert oracle.bfs_certificate(g, srcs[i], d[i]) == (0, -1), f"source {srcs[i]}"
 
 
-@pytest.mark.parametrize("flags", ["host", "device_loop", "per_source", "per_source_device_loop"])
+@pytest.mark.parametrize("flags", ["host", "device_loop", "per_source", "per_source_device_loop", "groups_of_7",
+                                   "groups_of_7_device_loop"])
 def test_bfs_bsp_forms_many_sources(atos, flags):
-    """The level-synchronous comparator (Algorithm 1) over 40 sources: every source's frontier in
-    one launch per level (or one source after another), levels driven by the host or by a CUDA
-    graph's conditional loop; bit-exact, with no overwork (each reached vertex expanded once per
-    source) and one level per depth."""
+    """The level-synchronous comparator (Algorithm 1) over 41 sources: the frontiers of all sources
+    (or of groups of 7) in one launch per level, or one source after another, levels driven by the
+    host or by a CUDA graph's conditional loop; bit-exact, with no overwork (each reached vertex
+    expanded once per source) and one level per depth of each group."""
     f = {"host": 0, "device_loop": atos.FLAG_BSP_DEVICE_LOOP, "per_source": atos.FLAG_BSP_PER_SOURCE,
-         "per_source_device_loop": atos.FLAG_BSP_PER_SOURCE | atos.FLAG_BSP_DEVICE_LOOP}[flags]
+         "per_source_device_loop": atos.FLAG_BSP_PER_SOURCE | atos.FLAG_BSP_DEVICE_LOOP,
+         "groups_of_7": 0, "groups_of_7_device_loop": atos.FLAG_BSP_DEVICE_LOOP}[flags]
+    group = 1 if f & atos.FLAG_BSP_PER_SOURCE else (7 if "groups_of_7" in flags else 0)
     g = gg.rmat(12, 16, seed=1, delete_frac=0.1)
     srcs = [int(x) for x in gg.sources(g, 40, seed=2)] + [0]
     refs = np.stack([oracle.bfs(g, s) for s in srcs])
@@ -171,11 +174,12 @@ def test_bfs_bsp_forms_many_sources(atos, flags):
     ecc = np.where(reached, refs, 0).max(axis=1)
     with atos.Graph.from_csr(g) as G:
         for _ in range(2):  # a second run reuses the scratch (and the graph of the device loop)
-            depths, st = G.bfs(srcs, cfg=atos.queue_config("bsp", flags=f))
+            depths, st = G.bfs(srcs, cfg=atos.queue_config("bsp", flags=f, window=7 if group == 7 else 0))
             assert st.status == 0
             assert np.array_equal(depths.cpu().numpy(), refs)
             assert st.tasks == int(reached.sum())
-            levels = int((ecc + 1).sum()) if f & atos.FLAG_BSP_PER_SOURCE else int(ecc.max() + 1)
+            size = group or len(srcs)  # 4096 vertices: every source fits the default group
+            levels = sum(int(ecc[i:i + size].max() + 1) for i in range(0, len(srcs), size))
             assert st.iterations == levels
 
 
