@@ -49,8 +49,9 @@ extern "C" {
 /* ------------------------------------------------------------------ configuration */
 #define ATOS_WORKER_WARP 32 /* worker_size == 32: one warp per worker (persist-32) */
 #define ATOS_WORKER_THREAD 1 /* worker_size == 1: one thread per worker, scheduled per warp (the
-                                warp pops up to fetch_size <= 32 tasks, each lane expands one);
-                                BFS through atos_bfs only (ATOS_ERR_UNSUPPORTED elsewhere) */
+                                warp pops up to fetch_size <= 32 tasks, each lane runs one; a task
+                                whose row exceeds 32 entries is run by the whole warp); every
+                                application and batches (servers pause CTA workers only) */
 
 #define ATOS_PERSISTENT 0 /* one launch; workers loop on the queue until it drains (Section 3.4) */
 #define ATOS_DISCRETE 1   /* one launch per queue generation; the host reads the next size */
@@ -130,7 +131,7 @@ extern "C" {
                                      return ATOS_ERR_UNSUPPORTED. */
 
 typedef struct atos_config {
-  int32_t worker_size;    /* 1 (thread worker, BFS only), 32 (warp worker) or a CTA worker of 64,
+  int32_t worker_size;    /* 1 (thread worker), 32 (warp worker) or a CTA worker of 64,
                              128, 256, 512 or 1024 threads */
   int32_t fetch_size;     /* tasks per pop, 1..1024; at most worker_size for CTA workers (FETCH_SIZE
                              of Section 4); at most 32 for thread and warp workers */
@@ -407,7 +408,7 @@ int atos_server_destroy(atos_server_t s);
 #define ATOS_TUNE_GC_MAX_COLOR_RATIO 1.05
 
 /* Times candidate configurations of `app` (ATOS_APP_*) on g and returns the fastest in *best
- * (its device time in *best_ms): CTA workers of 128..1024 threads, warp workers and (BFS) thread
+ * (its device time in *best_ms): CTA workers of 128..1024 threads, warp workers and thread
  * workers, fixed / greedy / spread fetch policies, persistent, discrete and BSP strategies (the
  * BSP level loop on the host and on the device), plus the instance window for multi-source BFS,
  * Check_Size and the threshold-crossing enqueue for PageRank, and the dependency-ordered mode

@@ -66,6 +66,14 @@ struct MixedBody {
       default: GcBody::warp_item(ws, I, item, L, st); break;
     }
   }
+  __device__ static void lane_items(WarpSmem& ws, const Instance& I, int item, const Launch& L,
+                                    unsigned long long* st) {
+    switch (I.app) {
+      case kAppBfs: BfsBody::lane_items(ws, I, item, L, st); break;
+      case kAppPr: PrBody::lane_items(ws, I, item, L, st); break;
+      default: GcBody::lane_items(ws, I, item, L, st); break;
+    }
+  }
   __device__ static int warp_idle(WarpSmem& ws, const Instance& I, const Launch& L, unsigned long long* st) {
     switch (I.app) {
       case kAppBfs: return BfsBody::warp_idle(ws, I, L, st);
@@ -124,8 +132,12 @@ __global__ void batch_normalise_kernel(const Instance* insts, const InstResult* 
     I.rank[v] = (float)((double)I.rank[v] * inv);
 }
 
-const void* mixed_persistent_kernel(int worker) { return persistent_kernel_ptr<MixedBody>(worker); }
-const void* mixed_discrete_kernel(int worker) { return discrete_kernel_ptr<MixedBody>(worker); }
+const void* mixed_persistent_kernel(int worker) {
+  return worker == 1 ? (const void*)warp_persistent_kernel<MixedBody, true> : persistent_kernel_ptr<MixedBody>(worker);
+}
+const void* mixed_discrete_kernel(int worker) {
+  return worker == 1 ? (const void*)warp_discrete_kernel<MixedBody, true> : discrete_kernel_ptr<MixedBody>(worker);
+}
 
 // Finishes the terminated instances among d_insts[0, ninst) (PageRank normalisation, colour
 // count) into d_results[k] (InstResult each); instances still running are left alone.
@@ -250,7 +262,7 @@ int enqueue_run(atos_batch_s* b, cudaStream_t st) {
   L.fail_site = &b->d_ctl->fail_site;
   L.spin_limit_ns = b->cfg.spin_limit_ns > 0 ? b->cfg.spin_limit_ns : 4000000000LL;
   L.lifetime_ns = L.spin_limit_ns * 16;
-  const int workers_per_block = b->cfg.worker_size == 32 ? kWarpBlock / 32 : 1;
+  const int workers_per_block = warp_hosted(b->cfg.worker_size) ? kWarpBlock / 32 : 1;
   L.nworkers = std::max(1, b->nb * workers_per_block / b->window);
   const bool discrete = b->cfg.strategy == ATOS_DISCRETE;
   BATCH_TRY(launch_prepare(b->d_insts, b->ninst, b->max_n, b->d_ctl, b->cfg.flags,
@@ -259,7 +271,7 @@ int enqueue_run(atos_batch_s* b, cudaStream_t st) {
   if (discrete) {
     // one launch per generation over every instance, the generation size read back each time
     L.window = b->ninst;
-    const int per_block = b->cfg.worker_size == 32 ? std::min(b->cfg.fetch_size, 32) * (kWarpBlock / 32)
+    const int per_block = warp_hosted(b->cfg.worker_size) ? std::min(b->cfg.fetch_size, 32) * (kWarpBlock / 32)
                                                    : b->cfg.fetch_size;
     BATCH_TRY(discrete_loop(b->fn_discrete, b->threads, per_block, L, b->d_insts, b->ninst, b->max_n, b->first_gen,
                             b->has_pr, b->d_ctl, b->h_ctl, st, nullptr));
@@ -302,9 +314,8 @@ int atos_batch_create(const atos_graph_t* graphs, int32_t ngraphs, const atos_in
   else atos_queue_config(&cfg, nullptr);
   if (!worker_supported(cfg.worker_size)) return ATOS_ERR_UNSUPPORTED;
   if (cfg.strategy != ATOS_PERSISTENT && cfg.strategy != ATOS_DISCRETE) return ATOS_ERR_UNSUPPORTED;
-  if (cfg.worker_size == 1) return ATOS_ERR_UNSUPPORTED;  // thread workers: BFS through atos_bfs only
   if (cfg.flags & ATOS_FLAG_GC_DEPENDENCY) return ATOS_ERR_UNSUPPORTED;  // atos_color only
-  if (cfg.fetch_size < 1 || cfg.fetch_size > 1024 || (cfg.worker_size != 32 && cfg.fetch_size > cfg.worker_size))
+  if (cfg.fetch_size < 1 || cfg.fetch_size > (warp_hosted(cfg.worker_size) ? 32 : cfg.worker_size))
     return ATOS_ERR_INVALID_ARG;
   // validate every instance before allocating anything
   std::vector<int32_t> gn(ngraphs);

@@ -7,8 +7,13 @@
 
 namespace atos {
 
-const void* gc_persistent_kernel(int worker) { return persistent_kernel_ptr<GcBody>(worker); }
-const void* gc_discrete_kernel(int worker) { return discrete_kernel_ptr<GcBody>(worker); }
+// worker 1: thread workers (each lane of a warp runs its own task, GcBody::lane_items)
+const void* gc_persistent_kernel(int worker) {
+  return worker == 1 ? (const void*)warp_persistent_kernel<GcBody, true> : persistent_kernel_ptr<GcBody>(worker);
+}
+const void* gc_discrete_kernel(int worker) {
+  return worker == 1 ? (const void*)warp_discrete_kernel<GcBody, true> : discrete_kernel_ptr<GcBody>(worker);
+}
 
 __global__ void gc_max_kernel(const int32_t* color, int n, int* out) {
   int m = -1;

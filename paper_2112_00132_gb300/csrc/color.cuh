@@ -406,6 +406,134 @@ struct GcBody {
     if (lane == 0) st[kStatEdges] += edges;
   }
 
+  // Thread worker (worker_size 1, Section 3.2's smallest worker): each lane runs its own task
+  // (kEmpty: none), walking its row one entry per step with the warp stepping together; tasks
+  // whose rows are longer than kLaneRowMax are run afterwards by the warp worker's path.
+  static constexpr int kLaneRowMax = 32;
+  __device__ static void lane_items(WarpSmem& ws, const Instance& I, int item, const Launch& L,
+                                    unsigned long long* st) {
+    bool have = item != kEmpty;
+    const int v = !have ? 0 : (item >= 0 ? item : ~item);
+    int s = 0, e = 0;
+    bool longrow = false;
+    if (have) {
+      s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
+      longrow = e - s > kLaneRowMax;
+      have = !longrow;
+    }
+    if (I.gc_wait) lane_dependency(ws, I, item, have, v, s, e, L, st);
+    else lane_speculative(ws, I, item, have, v, s, e, L, st);
+    for (unsigned big = __ballot_sync(0xffffffffu, longrow); big; big &= big - 1)
+      warp_item(ws, I, __shfl_sync(0xffffffffu, item, __ffs(big) - 1), L, st);
+  }
+
+  // Algorithm 6 per lane: an assign task takes the first colour free among its neighbours'
+  // (windows of 64 colours, the row walked again for each), writes it and pushes its check task;
+  // a check task pushes the larger endpoint of each conflict (itself once if a smaller neighbour
+  // shares its colour).
+  __device__ static void lane_speculative(WarpSmem& ws, const Instance& I, int item, bool have, int v, int s, int e,
+                                          const Launch& L, unsigned long long* st) {
+    const bool assign = have && item >= 0;
+    const bool check = have && item < 0;
+    if (assign) atomicAnd(I.qbits + (v >> 5), ~(1u << (v & 31)));  // later requests queue a new assign
+    if (__any_sync(0xffffffffu, check)) __threadfence();  // store-buffering pattern (see the file comment)
+    unsigned long long edges = 0;
+    int colour = -1;
+    for (int base = 0; __any_sync(0xffffffffu, assign && colour < 0); base += kGcWindow) {
+      const bool active = assign && colour < 0;
+      unsigned long long used = 0;
+      int k = active ? s : e;
+      while (__any_sync(0xffffffffu, k < e)) {
+        if (k < e) {
+          const int u = ldg(I.col + k);
+          if (!I.gc_ordered || u < v) {
+            const int rel = __ldcg(I.color + u) - base;
+            if (rel >= 0 && rel < kGcWindow) used |= 1ull << rel;
+          }
+          ++k;
+        }
+      }
+      if (active) {
+        edges += (unsigned long long)(e - s);
+        if (~used) colour = base + __ffsll((long long)~used) - 1;
+      }
+    }
+    if (assign) {
+      st_relaxed(I.color + v, colour);
+      __threadfence();  // the colour is visible before the check task can be taken
+    }
+    warp_push(ws, assign, ~v);
+    // check tasks
+    const int cv = check ? __ldcg(I.color + v) : 0;
+    bool conflict = false;
+    int k = check ? s : e;
+    if (check) edges += (unsigned long long)(e - s);
+    while (__any_sync(0xffffffffu, k < e)) {
+      bool larger = false;
+      int u = 0;
+      if (k < e) {
+        u = ldg(I.col + k);
+        if (u != v && __ldcg(I.color + u) == cv) {
+          if (u < v) conflict = true;
+          else larger = gc_claim_assign(I, u);
+        }
+        ++k;
+      }
+      warp_push(ws, larger, u);  // the larger neighbour recolours
+      warp_maybe_flush(ws, I, L, st);
+    }
+    warp_push(ws, check && conflict && gc_claim_assign(I, v), v);
+    warp_maybe_flush(ws, I, L, st);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) edges += __shfl_xor_sync(0xffffffffu, edges, o);
+    if ((threadIdx.x & 31) == 0) st[kStatEdges] += edges;
+  }
+
+  // Dependency-ordered mode per lane (see cta_batch_dependency).
+  __device__ static void lane_dependency(WarpSmem& ws, const Instance& I, int item, bool have, int v, int s, int e,
+                                         const Launch& L, unsigned long long* st) {
+    const bool ready = have && (item < 0 || atomicSub(I.gc_wait + v, 1) == 1);
+    const int m = ready ? s + ldg(I.gc_mid + v) : s;  // [s, m): smaller neighbours, [m, e): larger
+    unsigned long long edges = 0;
+    int colour = -1;
+    for (int base = 0; __any_sync(0xffffffffu, ready && colour < 0); base += kGcWindow) {
+      const bool active = ready && colour < 0;
+      unsigned long long used = 0;
+      int k = active ? s : m;
+      while (__any_sync(0xffffffffu, k < m)) {
+        if (k < m) {
+          const int rel = __ldcg(I.color + ldg(I.col + k)) - base;
+          if (rel >= 0 && rel < kGcWindow) used |= 1ull << rel;
+          ++k;
+        }
+      }
+      if (active) {
+        edges += (unsigned long long)(m - s);
+        if (~used) colour = base + __ffsll((long long)~used) - 1;
+      }
+    }
+    if (ready) {
+      st_relaxed(I.color + v, colour);
+      __threadfence();  // the colour is visible before any decrement below
+      edges += (unsigned long long)(e - m);
+    }
+    int k = ready ? m : e;
+    while (__any_sync(0xffffffffu, k < e)) {
+      bool go = false;
+      int w = 0;
+      if (k < e) {
+        w = ldg(I.col + k);
+        go = atomicSub(I.gc_wait + w, 1) == 1;
+        ++k;
+      }
+      warp_push(ws, go, ~w);
+      if (ws.npush > 0) warp_flush(ws, I, 0, L, st);  // publish a ready vertex right away
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) edges += __shfl_xor_sync(0xffffffffu, edges, o);
+    if ((threadIdx.x & 31) == 0) st[kStatEdges] += edges;
+  }
+
   __device__ static int warp_idle(WarpSmem&, const Instance& I, const Launch&, unsigned long long*) {
     return (threadIdx.x & 31) == 0 ? (instance_quiescent(I) ? 1 : 0) : 0;
   }

@@ -7,7 +7,7 @@
 
 namespace atos {
 
-// Worker shapes that are compiled: thread workers (1, BFS only), the warp worker (32) and CTA
+// Worker shapes that are compiled: thread workers (1), the warp worker (32) and CTA
 // workers of 64 .. 1024 threads.
 inline bool worker_supported(int w) {
   return w == 1 || w == 32 || w == 64 || w == 128 || w == 256 || w == 512 || w == 1024;

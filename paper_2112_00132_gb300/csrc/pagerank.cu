@@ -26,8 +26,13 @@
 
 namespace atos {
 
-const void* pr_persistent_kernel(int worker) { return persistent_kernel_ptr<PrBody>(worker); }
-const void* pr_discrete_kernel(int worker) { return discrete_kernel_ptr<PrBody>(worker); }
+// worker 1: thread workers (each lane of a warp runs its own task, PrBody::lane_items)
+const void* pr_persistent_kernel(int worker) {
+  return worker == 1 ? (const void*)warp_persistent_kernel<PrBody, true> : persistent_kernel_ptr<PrBody>(worker);
+}
+const void* pr_discrete_kernel(int worker) {
+  return worker == 1 ? (const void*)warp_discrete_kernel<PrBody, true> : discrete_kernel_ptr<PrBody>(worker);
+}
 
 // Discrete strategy: after a generation comes back empty, one full sweep enqueues every vertex
 // whose residue still exceeds epsilon (they form the next generation).

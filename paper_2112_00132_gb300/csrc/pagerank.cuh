@@ -367,6 +367,53 @@ struct PrBody {
     warp_check_scan(ws, I, I.check_size, L, st);
   }
 
+  // Thread worker (worker_size 1, Section 3.2's smallest worker): each lane runs its own task v
+  // (kEmpty: none) -- takes the residue, and walks its row one entry per step, the warp stepping
+  // together until every lane's row is done -- then the warp runs one Check_Size scan for all of
+  // them.  A row longer than kLaneRowMax would hold the whole warp for its length, so such a task
+  // is run afterwards by the warp worker's path, 32 entries per step.
+  static constexpr int kLaneRowMax = 32;
+  __device__ static void lane_items(WarpSmem& ws, const Instance& I, int v, const Launch& L, unsigned long long* st) {
+    int k = 0, e = 0;
+    float share = 0.0f;
+    bool longrow = false;
+    if (v != kEmpty) {
+      const int s = ldg(I.row_ptr + v), end = ldg(I.row_ptr + v + 1);
+      if (end - s > kLaneRowMax) {
+        longrow = true;  // the whole task goes to the warp path below
+      } else {
+        atomicAnd(I.qbits + (v >> 5), ~(1u << (v & 31)));
+        const float r = atomicExch(I.res + v, 0.0f);
+        if (r != 0.0f) {
+          red_add_f32(I.rank + v, r);
+          if (end > s) share = I.alpha * r / (float)(end - s), k = s, e = end;
+        }
+      }
+    }
+    unsigned long long edges = (unsigned long long)(e - k);
+    while (__any_sync(0xffffffffu, k < e)) {
+      bool want = false;
+      int u = 0;
+      if (k < e) {
+        u = ldg(I.col + k);
+        if (I.pr_crossing) want = pr_add_crossing(I, u, share);
+        else red_add_f32(I.res + u, share);
+        ++k;
+      }
+      if (I.pr_crossing) {
+        warp_push(ws, want, u);
+        warp_maybe_flush(ws, I, L, st);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) edges += __shfl_xor_sync(0xffffffffu, edges, o);
+    if ((threadIdx.x & 31) == 0) st[kStatEdges] += edges;
+    const unsigned shortm = __ballot_sync(0xffffffffu, v != kEmpty && !longrow);
+    if (!I.pr_crossing && shortm) warp_check_scan(ws, I, (unsigned)__popc(shortm) * I.check_size, L, st);
+    for (unsigned big = __ballot_sync(0xffffffffu, longrow); big; big &= big - 1)
+      warp_item(ws, I, __shfl_sync(0xffffffffu, v, __ffs(big) - 1), L, st);
+  }
+
   // The Check_Size scan for a warp: lane k takes group k of the range (see check_scan).
   __device__ static void warp_check_scan(WarpSmem& ws, const Instance& I, unsigned nchk, const Launch& L,
                                          unsigned long long* st) {

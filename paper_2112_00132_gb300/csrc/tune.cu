@@ -1,6 +1,6 @@
 // tune.cu -- autotuner: picks worker size, fetch size, fetch policy, strategy and (BFS with many
 // sources) the instance window for one application on one graph by timing the candidates, the
-// sweep of Figure 4 (worker size x FETCH_SIZE, thread workers included for BFS) extended with
+// sweep of Figure 4 (worker size x FETCH_SIZE, thread workers included) extended with
 // the kernel strategy (Section 3.4) and, for PageRank and colouring, the spread-id layout of the
 // graph.
 //
@@ -105,7 +105,7 @@ std::vector<atos_config> candidates(int app, int nsrc) {
         out.push_back(c);
       }
   }
-  if (app == ATOS_APP_BFS) out.push_back(make(nullptr, 1, 32, ATOS_FETCH_SPREAD));  // thread workers
+  out.push_back(make(nullptr, 1, 32, ATOS_FETCH_SPREAD));  // thread workers
   if (app == ATOS_APP_BFS) {
     // the same shapes with expansion markers
     const size_t k = out.size();

@@ -62,3 +62,15 @@ def configs(atos):
         "bsp-device-loop": q("bsp", flags=atos.FLAG_BSP_DEVICE_LOOP),
         "bsp-per-source": q("bsp", flags=atos.FLAG_BSP_PER_SOURCE),
     }
+
+
+def thread_worker_configs(atos):
+    """Thread workers (worker_size 1): a warp pops up to 32 tasks and each lane runs one."""
+    q = atos.queue_config
+    return {
+        "persist-thread-f32": q(worker_size=1, fetch_size=32, fetch_policy=atos.FETCH_SPREAD),
+        "persist-thread-f7-fixed": q(worker_size=1, fetch_size=7, fetch_policy=atos.FETCH_FIXED),
+        "persist-thread-greedy-4blocks": q(worker_size=1, fetch_size=32, fetch_policy=atos.FETCH_GREEDY, num_blocks=4),
+        "discrete-thread-f32": q("discrete-warp", worker_size=1, fetch_size=32),
+        "discrete-thread-f5": q("discrete-warp", worker_size=1, fetch_size=5),
+    }

@@ -119,9 +119,9 @@ def test_batch_invalid(atos, graphs):
     with pytest.raises(atos.AtosError) as e:
         atos.Batch([G], [("bfs", 0, 0)], atos.queue_config("bsp"))
     assert e.value.status == atos.abi.ERR_UNSUPPORTED
-    with pytest.raises(atos.AtosError) as e:  # thread workers run through the single-graph BFS only
-        atos.Batch([G], [("bfs", 0, 0)], atos.queue_config(worker_size=1, fetch_size=32))
-    assert e.value.status == atos.abi.ERR_UNSUPPORTED
+    with pytest.raises(atos.AtosError) as e:  # a thread worker fetches at most 32 tasks
+        atos.Batch([G], [("bfs", 0, 0)], atos.queue_config(worker_size=1, fetch_size=64))
+    assert e.value.status == atos.abi.ERR_INVALID_ARG
     with atos.Batch([G], [("bfs", 0, 0)], atos.queue_config("discrete-cta")) as B:
         with pytest.raises(atos.AtosError) as e:  # host-driven generations cannot be captured
             B.run(graph=True)

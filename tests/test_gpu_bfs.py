@@ -5,7 +5,7 @@ import pytest
 
 import graphgen as gg
 import oracle
-from gpu_common import atos_lib, bfs_sources, configs, small_graphs
+from gpu_common import thread_worker_configs, atos_lib, bfs_sources, configs, small_graphs
 
 pytestmark = pytest.mark.gpu
 
@@ -220,18 +220,6 @@ def test_bfs_expand_once_all_configs(atos):
                 assert st.status == 0 and np.array_equal(d.cpu().numpy(), ref), cname
 
 
-def thread_worker_configs(atos):
-    """Thread workers (worker_size 1): a warp pops up to 32 tasks and each lane expands one."""
-    q = atos.queue_config
-    return {
-        "persist-thread-f32": q(worker_size=1, fetch_size=32, fetch_policy=atos.FETCH_SPREAD),
-        "persist-thread-f7-fixed": q(worker_size=1, fetch_size=7, fetch_policy=atos.FETCH_FIXED),
-        "persist-thread-greedy-4blocks": q(worker_size=1, fetch_size=32, fetch_policy=atos.FETCH_GREEDY, num_blocks=4),
-        "discrete-thread-f32": q("discrete-warp", worker_size=1, fetch_size=32),
-        "discrete-thread-f5": q("discrete-warp", worker_size=1, fetch_size=5),
-    }
-
-
 @pytest.mark.parametrize("gname", list(small_graphs().keys()))
 def test_bfs_thread_workers_bit_exact(atos, graphs, gname):
     """Thread workers reach the same exact depths, with and without expansion markers."""
@@ -266,18 +254,17 @@ def test_bfs_thread_workers_windows_and_grid(atos):
         assert st.status == 0 and np.array_equal(d.cpu().numpy()[0], ref)
 
 
-def test_thread_workers_rejected_outside_bfs(atos):
-    """Thread workers are built for BFS only: the other entry points answer UNSUPPORTED, and a
-    fetch size above 32 is an invalid argument."""
+def test_thread_workers_arguments(atos):
+    """A thread worker fetches at most 32 tasks (one per lane): a larger fetch size is an invalid
+    argument, and the graph still works afterwards; servers pause CTA workers only."""
     g = gg.rmat(10, 8, seed=3)
     cfg = atos.queue_config(worker_size=1, fetch_size=32)
     with atos.Graph.from_csr(g) as G:
-        for call in (lambda: G.pagerank(0.85, 1e-6, cfg=cfg), lambda: G.color(cfg=cfg)):
-            with pytest.raises(atos.AtosError) as e:
-                call()
-            assert e.value.status == atos.abi.ERR_UNSUPPORTED
         with pytest.raises(atos.AtosError) as e:
             G.bfs([0], cfg=atos.queue_config(worker_size=1, fetch_size=64))
         assert e.value.status == atos.abi.ERR_INVALID_ARG
-        d, st = G.bfs([0], cfg=cfg)  # the graph still works afterwards
+        d, st = G.bfs([0], cfg=cfg)
         assert np.array_equal(d.cpu().numpy()[0], oracle.bfs(g, 0))
+        with pytest.raises(atos.AtosError) as e:
+            atos.Server([G], max_slots=4, budget_bytes=1 << 26, cfg=cfg)
+        assert e.value.status == atos.abi.ERR_UNSUPPORTED

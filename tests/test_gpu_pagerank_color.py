@@ -9,7 +9,7 @@ import pytest
 
 import graphgen as gg
 import oracle
-from gpu_common import ALPHA, EPS, PR_L1_TOL, atos_lib, configs, small_graphs
+from gpu_common import ALPHA, EPS, PR_L1_TOL, atos_lib, configs, small_graphs, thread_worker_configs
 
 pytestmark = pytest.mark.gpu
 
@@ -436,3 +436,57 @@ def test_color_dependency_rejected_by_batches_and_servers(atos):
         with pytest.raises(atos.AtosError) as e:
             atos.Server([G], max_slots=4, budget_bytes=1 << 26, cfg=cfg)
         assert e.value.status == atos.abi.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("gname", ["rmat12", "rmat11_del", "grid97x61_del", "star1000", "clique40", "two_parts",
+                                   "path300", "single", "isolated3"])
+def test_thread_workers_pagerank_and_color(atos, graphs, gname):
+    """Thread workers (worker_size 1) for PageRank (Check_Size scan and threshold crossing, input
+    and spread layouts) and colouring (Algorithm 6 and the dependency-ordered mode): the same
+    gates as the other workers, rows longer than 32 entries handed to the warp path."""
+    g = graphs[gname]
+    ref = pr_reference(g)
+    greedy, kg = oracle.greedy_color(g)
+    with atos.Graph.from_csr(g) as G:
+        for cname, cfg in thread_worker_configs(atos).items():
+            for flags in (0, atos.FLAG_SPREAD_IDS, atos.FLAG_PR_CROSSING):
+                cfg.flags = flags
+                rank, st = G.pagerank(ALPHA, EPS, cfg=cfg)
+                q = rank.cpu().numpy().astype(np.float64)
+                l1 = np.abs(q - ref).sum()
+                assert st.status == 0 and l1 <= PR_L1_TOL, f"{gname}/{cname}/{flags}: L1 {l1}"
+                assert l1 <= st.error_bound * 1.0001 + 1e-12
+                assert G.scratch_check() == (0, 0)
+            for flags in (0, atos.FLAG_SPREAD_IDS, atos.FLAG_GC_ORDERED):
+                cfg.flags = flags
+                colors, k, st = G.color(cfg=cfg)
+                code, bad, kk = oracle.check_coloring(g, colors.cpu().numpy())
+                assert st.status == 0 and code == 0 and k == kk, f"{gname}/{cname}/{flags}: vertex {bad}"
+            cfg.flags = atos.FLAG_GC_DEPENDENCY
+            colors, k, st = G.color(cfg=cfg)
+            assert st.status == 0 and k == kg and np.array_equal(colors.cpu().numpy(), greedy), f"{gname}/{cname}"
+
+
+def test_thread_workers_in_batches(atos):
+    """A mixed batch (BFS, PageRank, colouring over three graphs) run by thread workers: each
+    result as the oracle has it."""
+    gs = [gg.rmat(11, 16, seed=2), gg.grid(60, 45, delete_frac=0.1, seed=4), gg.star(300)]
+    Gs = [atos.Graph.from_csr(x) for x in gs]
+    specs = [("bfs", 0, 0), ("pagerank", 1), ("color", 2), ("bfs", 1, 7), ("pagerank", 0), ("color", 0)]
+    for cfg in (atos.queue_config(worker_size=1, fetch_size=32), atos.queue_config("discrete-warp", worker_size=1,
+                                                                                    fetch_size=16)):
+        with atos.Batch(Gs, specs, cfg) as B:
+            B.run()
+            _, per = B.stats()
+            for (kind, gi, *rest), out, st in zip(specs, B.outputs, per):
+                assert st.status == 0
+                x = gs[gi]
+                o = out.cpu().numpy()
+                if kind == "bfs":
+                    assert np.array_equal(o, oracle.bfs(x, rest[0]))
+                elif kind == "pagerank":
+                    assert np.abs(o.astype(np.float64) - pr_reference(x)).sum() <= PR_L1_TOL
+                else:
+                    assert oracle.check_coloring(x, o)[0] == 0
+    for G in Gs:
+        G.close()
