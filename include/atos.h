@@ -45,6 +45,8 @@ extern "C" {
 #define ATOS_ERR_CUDA (-6)           /* a CUDA runtime call failed (no device, launch error...) */
 #define ATOS_ERR_UNSUPPORTED (-7)    /* configuration not built (e.g. this worker size) */
 #define ATOS_ERR_BUSY (-8)           /* serving: no free slot or not enough arena memory now */
+#define ATOS_ERR_BOUNDS (-9)         /* bounds-checked builds only: an index outside its array was
+                                        caught (and the access redirected) during the run */
 
 /* ------------------------------------------------------------------ configuration */
 #define ATOS_WORKER_WARP 32 /* worker_size == 32: one warp per worker (persist-32) */

@@ -27,6 +27,7 @@ ERR_TIMEOUT = -5
 ERR_CUDA = -6
 ERR_UNSUPPORTED = -7
 ERR_BUSY = -8
+ERR_BOUNDS = -9
 
 WORKER_WARP = 32
 WORKER_THREAD = 1

@@ -480,6 +480,7 @@ const char* atos_status_string(int status) {
     case ATOS_ERR_CUDA: return "CUDA runtime error";
     case ATOS_ERR_UNSUPPORTED: return "unsupported configuration";
     case ATOS_ERR_BUSY: return "no free slot or arena memory for the request now";
+    case ATOS_ERR_BOUNDS: return "an index outside its array was caught (bounds-checked build)";
   }
   return "unknown status";
 }

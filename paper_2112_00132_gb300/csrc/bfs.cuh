@@ -111,7 +111,7 @@ struct BfsBody {
       bool want = false;
       int nb = 0;
       if (j < e) {
-        nb = ldg(I.col + j);
+        nb = nbr_at(I, j, L);
         if (nd < __ldcg(I.depth + nb)) want = nd < atomicMin(I.depth + nb, nd);
       }
       warp_push(ws, want, nb);
@@ -149,7 +149,7 @@ struct BfsBody {
       bool want = false;
       int nb = 0;
       if (k < e) {
-        nb = ldg(I.col + k);
+        nb = nbr_at(I, k, L);
         if (nd < __ldcg(I.depth + nb)) want = nd < atomicMin(I.depth + nb, nd);
         ++k;
       }

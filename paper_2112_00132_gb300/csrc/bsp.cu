@@ -33,6 +33,11 @@ struct Ctl {
   long long edges, tasks, iters;
   long long max_iters;
   int cur, level, status, app;
+  int fail_site;     // checked builds: the first bounds violation's site
+  int pad;
+  long long cap_items;   // frontier buffer capacity (items)
+  long long cap_chunks;  // chunk_lo capacity
+  long long nnz;
   // parameters
   const int32_t* row_ptr;
   const int32_t* col;
@@ -56,6 +61,23 @@ struct Header {  // the leading fields of Ctl, as read back by the host
   int cur, level, status, app;
 };
 static_assert(sizeof(Header) <= sizeof(Ctl), "header");
+
+// Where checked builds record a violation (the control block's status and site words).
+struct CtlErr {
+  int* status;
+  int* fail_site;
+  __device__ explicit CtlErr(Ctl* c) : status(&c->status), fail_site(&c->fail_site) {}
+};
+
+// col[k] with the entry index and the neighbour id checked in checked builds.
+__device__ __forceinline__ int col_at(const int32_t* __restrict__ col, long long k, const Ctl* c, const CtlErr& ce) {
+#ifdef ATOS_CHECKED
+  return ATOS_IX(__ldg(col + ATOS_IX(k, c->nnz, ce, kSiteEntry)), c->n, ce, kSiteNeighbour);
+#else
+  (void)c, (void)ce;
+  return __ldg(col + k);
+#endif
+}
 
 __device__ __forceinline__ long long warp_incl_scan64(long long x) {
   const int lane = threadIdx.x & 31;
@@ -107,7 +129,8 @@ __device__ __forceinline__ void append_next(Ctl* c, int nxt, bool want, T item) 
   unsigned long long base = 0;
   if (lane == leader) base = atomicAdd((unsigned long long*)&c->F[nxt], (unsigned long long)__popc(m));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (want) ((T*)c->fr[nxt])[base + __popc(m & lanemask_lt())] = item;
+  const CtlErr ce(c);
+  if (want) ((T*)c->fr[nxt])[ATOS_IX((long long)(base + __popc(m & lanemask_lt())), c->cap_items, ce, kSiteFrontier)] = item;
 }
 
 // ------------------------------------------------------------------------------------ scan
@@ -177,9 +200,10 @@ __global__ void mark_chunks_kernel(Ctl* c) {
   const long long F = c->F[c->cur];
   const long long* __restrict__ offs = c->offs;
   int32_t* __restrict__ lo = c->chunk_lo;
+  const CtlErr ce(c);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < F; i += (long long)gridDim.x * blockDim.x) {
     const long long a = offs[i], b = offs[i + 1];
-    for (long long ch = (a + kChunk - 1) / kChunk; ch * kChunk < b; ++ch) lo[ch] = (int32_t)i;
+    for (long long ch = (a + kChunk - 1) / kChunk; ch * kChunk < b; ++ch) lo[ATOS_IX(ch, c->cap_chunks, ce, kSiteChunk)] = (int32_t)i;
   }
 }
 
@@ -273,6 +297,7 @@ __global__ void __launch_bounds__(kBlock) bfs_advance_kernel(Ctl* c) {
   const int32_t* __restrict__ row_ptr = c->row_ptr;
   const int32_t* __restrict__ col = c->col;
   int32_t* depth = c->depth;
+  const CtlErr ce(c);
   const long long nchunks = (total + kChunk - 1) / kChunk;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long e0 = ch * kChunk, e1 = min(total, e0 + kChunk);
@@ -297,12 +322,12 @@ __global__ void __launch_bounds__(kBlock) bfs_advance_kernel(Ctl* c) {
         if (staged) {
           while (i + 1 < cnt && s_off[i + 1] <= e) ++i;
           srcs[r] = (unsigned)(s_item[i] >> 32);
-          nbs[r] = __ldg(col + s_start[i] + (e - s_off[i]));
+          nbs[r] = col_at(col, s_start[i] + (e - s_off[i]), c, ce);
         } else {
           while (i + 1 < cnt && offs[lo + i + 1] <= e) ++i;
           const unsigned long long it = fr[lo + i];
           srcs[r] = (unsigned)(it >> 32);
-          nbs[r] = __ldg(col + __ldg(row_ptr + (int)(unsigned)it) + (e - offs[lo + i]));
+          nbs[r] = col_at(col, __ldg(row_ptr + (int)(unsigned)it) + (e - offs[lo + i]), c, ce);
         }
       }
     }
@@ -362,6 +387,7 @@ __global__ void __launch_bounds__(kBlock) pr_scatter_kernel(Ctl* c) {
   const int32_t* __restrict__ col = c->col;
   const float* __restrict__ share = c->share;
   float* res = c->res;
+  const CtlErr ce(c);
   const long long nchunks = (total + kChunk - 1) / kChunk;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long e0 = ch * kChunk, e1 = min(total, e0 + kChunk);
@@ -379,10 +405,10 @@ __global__ void __launch_bounds__(kBlock) pr_scatter_kernel(Ctl* c) {
         int nb;
         if (staged) {
           while (i + 1 < cnt && s_off[i + 1] <= e) ++i;
-          nb = __ldg(col + s_start[i] + (e - s_off[i]));
+          nb = col_at(col, s_start[i] + (e - s_off[i]), c, ce);
         } else {
           while (i + 1 < cnt && offs[lo + i + 1] <= e) ++i;
-          nb = __ldg(col + __ldg(row_ptr + fr[lo + i]) + (e - offs[lo + i]));
+          nb = col_at(col, __ldg(row_ptr + fr[lo + i]) + (e - offs[lo + i]), c, ce);
         }
         red_add_f32(res + nb, share[lo + i]);
       }
@@ -399,6 +425,9 @@ __global__ void pr_filter_kernel(Ctl* c) {
   const float* __restrict__ res = c->res;
   unsigned long long* count = (unsigned long long*)&c->F[nxt];
   int32_t* out = (int32_t*)c->fr[nxt];
+  const long long cap = c->cap_items;
+  const CtlErr ce(c);
+  (void)cap, (void)ce;
   const int lane = threadIdx.x & 31;
   for (int r = blockIdx.x * blockDim.x; r < n; r += gridDim.x * blockDim.x) {
     const int v = r + threadIdx.x;
@@ -409,7 +438,7 @@ __global__ void pr_filter_kernel(Ctl* c) {
     unsigned long long base = 0;
     if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (want) out[base + __popc(m & lanemask_lt())] = v;
+    if (want) out[ATOS_IX((long long)(base + __popc(m & lanemask_lt())), cap, ce, kSiteFrontier)] = v;
   }
 }
 
@@ -431,6 +460,7 @@ __global__ void gc_assign_kernel(Ctl* c) {
   const int32_t* __restrict__ row_ptr = c->row_ptr;
   const int32_t* __restrict__ col = c->col;
   int32_t* color = c->color;
+  const CtlErr ce(c);
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -442,7 +472,7 @@ __global__ void gc_assign_kernel(Ctl* c) {
     for (int base = 0; colour < 0; base += 64) {
       unsigned lo = 0, hi = 0;
       for (int k = s + lane; k < e; k += 32) {
-        const int rel = __ldcg(color + __ldg(col + k)) - base;
+        const int rel = __ldcg(color + col_at(col, k, c, ce)) - base;
         if (rel >= 0 && rel < 32) lo |= 1u << rel;
         else if (rel >= 32 && rel < 64) hi |= 1u << (rel - 32);
       }
@@ -468,6 +498,7 @@ __global__ void gc_conflicts_kernel(Ctl* c) {
   const int32_t* __restrict__ color = c->color;
   unsigned long long* count = (unsigned long long*)&c->F[nxt];
   int32_t* out = (int32_t*)c->fr[nxt];
+  const CtlErr ce(c);
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -477,10 +508,11 @@ __global__ void gc_conflicts_kernel(Ctl* c) {
     const int cv = color[v];
     bool conflict = false;
     for (int k = s + lane; k < e; k += 32) {
-      const int u = __ldg(col + k);
+      const int u = col_at(col, k, c, ce);
       conflict |= u < v && color[u] == cv;
     }
-    if (__any_sync(0xffffffffu, conflict) && lane == 0) out[atomicAdd(count, 1ull)] = v;
+    if (__any_sync(0xffffffffu, conflict) && lane == 0)
+      out[ATOS_IX((long long)atomicAdd(count, 1ull), c->cap_items, ce, kSiteFrontier)] = v;
   }
 }
 
@@ -551,6 +583,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t ctl, fr0, fr1, offs, bsums, chunk_lo, share, sources, total;
+  size_t items, chunks;  // frontier capacity (items) and chunk_lo capacity (entries)
 };
 
 Layout layout_for(int app, int32_t n, int64_t nnz, int32_t nsrc) {
@@ -569,6 +602,8 @@ Layout layout_for(int app, int32_t n, int64_t nnz, int32_t nsrc) {
   L.share = p, p += app == kAppPr ? align256(4 * std::max<size_t>(items, 1)) : 0;
   L.sources = p, p += app == kAppBfs ? align256(4 * (size_t)std::max(nsrc, 1)) : 0;
   L.total = p;
+  L.items = std::max<size_t>(items, 1);
+  L.chunks = app == kAppGc ? 0 : edges / kChunk + 2;
   return L;
 }
 
@@ -681,6 +716,9 @@ int bsp_run(const BspRun& r, void* scratch, size_t scratch_bytes, void* host_buf
   c.offs = (long long*)(base + Lo.offs);
   c.bsums = (long long*)(base + Lo.bsums);
   c.chunk_lo = (int32_t*)(base + Lo.chunk_lo);
+  c.cap_items = (long long)Lo.items;
+  c.cap_chunks = (long long)Lo.chunks;
+  c.nnz = r.nnz;
   c.share = (float*)(base + Lo.share);
   c.sources = (int32_t*)(base + Lo.sources);
   // the pinned image may still be in flight from the previous run on this scratch

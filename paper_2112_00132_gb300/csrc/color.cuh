@@ -103,7 +103,8 @@ struct GcBody {
 #pragma unroll
         for (int j = 0; j < R; ++j)
           if (owner[j] >= 0 && c[j] >= 0 && (c[j] >> 5) < sm.items[owner[j]])
-            atomicOr(&sm.x.bits[sm.aux[owner[j]] + (c[j] >> 5)], 1u << (c[j] & 31));
+            atomicOr(&sm.x.bits[ATOS_IX(sm.aux[owner[j]] + (c[j] >> 5), 2 * BLOCK, sm, kSiteShared)],
+                     1u << (c[j] & 31));
       }
       edges += total;
       __syncthreads();
@@ -313,7 +314,7 @@ struct GcBody {
     for (int base = 0; colour < 0; base += kGcWindow) {
       unsigned lo = 0, hi = 0;
       for (int k = s + lane; k < m; k += 32) {
-        const int rel = __ldcg(I.color + ldg(I.col + k)) - base;
+        const int rel = __ldcg(I.color + nbr_at(I, k, L)) - base;
         if (rel >= 0 && rel < 32) lo |= 1u << rel;
         else if (rel >= 32 && rel < 64) hi |= 1u << (rel - 32);
       }
@@ -333,7 +334,7 @@ struct GcBody {
       int w = 0;
       bool go = false;
       if (k < e) {
-        w = ldg(I.col + k);
+        w = nbr_at(I, k, L);
         go = atomicSub(I.gc_wait + w, 1) == 1;
       }
       warp_push(ws, go, ~w);
@@ -360,7 +361,7 @@ struct GcBody {
       for (int base = 0; colour < 0; base += kGcWindow) {
         unsigned lo = 0, hi = 0;
         for (int k = s + lane; k < e; k += 32) {
-          const int u = ldg(I.col + k);
+          const int u = nbr_at(I, k, L);
           if (I.gc_ordered && u > v) continue;
           const int rel = __ldcg(I.color + u) - base;
           if (rel >= 0 && rel < 32) lo |= 1u << rel;
@@ -389,7 +390,7 @@ struct GcBody {
         bool larger = false;
         int nb = 0;
         if (j < e) {
-          nb = ldg(I.col + j);
+          nb = nbr_at(I, j, L);
           if (nb != v && __ldcg(I.color + nb) == cv) {
             if (nb < v) conflict = true;
             else larger = gc_claim_assign(I, nb);
@@ -445,7 +446,7 @@ struct GcBody {
       int k = active ? s : e;
       while (__any_sync(0xffffffffu, k < e)) {
         if (k < e) {
-          const int u = ldg(I.col + k);
+          const int u = nbr_at(I, k, L);
           if (!I.gc_ordered || u < v) {
             const int rel = __ldcg(I.color + u) - base;
             if (rel >= 0 && rel < kGcWindow) used |= 1ull << rel;
@@ -472,7 +473,7 @@ struct GcBody {
       bool larger = false;
       int u = 0;
       if (k < e) {
-        u = ldg(I.col + k);
+        u = nbr_at(I, k, L);
         if (u != v && __ldcg(I.color + u) == cv) {
           if (u < v) conflict = true;
           else larger = gc_claim_assign(I, u);
@@ -502,7 +503,7 @@ struct GcBody {
       int k = active ? s : m;
       while (__any_sync(0xffffffffu, k < m)) {
         if (k < m) {
-          const int rel = __ldcg(I.color + ldg(I.col + k)) - base;
+          const int rel = __ldcg(I.color + nbr_at(I, k, L)) - base;
           if (rel >= 0 && rel < kGcWindow) used |= 1ull << rel;
           ++k;
         }
@@ -522,7 +523,7 @@ struct GcBody {
       bool go = false;
       int w = 0;
       if (k < e) {
-        w = ldg(I.col + k);
+        w = nbr_at(I, k, L);
         go = atomicSub(I.gc_wait + w, 1) == 1;
         ++k;
       }

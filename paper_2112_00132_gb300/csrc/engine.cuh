@@ -214,6 +214,69 @@ __device__ __forceinline__ void raise_timeout(const Launch& L, int site) {
   if (atomicCAS(L.status, 0, ATOS_ERR_TIMEOUT) == 0 && L.fail_site) atomicExch(L.fail_site, site);
 }
 
+// ----------------------------------------------------------------- bounds-checked build
+//
+// Compiled with ATOS_CHECKED, the worker engines and task bodies check every popped item, every
+// CSR entry index and neighbour id read from the CSR, and every push-buffer and shared-bitmap
+// slot before use.  A violation records ATOS_ERR_BOUNDS in the launch status (the first one's
+// site in fail_site) and the access goes to index 0 instead, so nothing outside the arrays is
+// touched; the status stops the launch at its next check.  Ring slots need no check: their index
+// is masked by the power-of-two capacity.  Without the macro every check compiles to nothing.
+enum : int {
+  kSiteItem = 101,        // a popped item outside the instance's vertices
+  kSiteEntry = 102,       // a CSR entry index outside [0, nnz)
+  kSiteNeighbour = 103,   // a neighbour id outside [0, n)
+  kSitePushBuffer = 104,  // a CTA push-buffer slot
+  kSiteWarpPush = 105,    // a warp push-buffer slot
+  kSiteShared = 106,      // a shared-memory bitmap or accumulator slot
+  kSiteFrontier = 107,    // a BSP frontier slot
+  kSiteChunk = 108        // a BSP edge-chunk slot
+};
+
+#ifdef ATOS_CHECKED
+static __device__ __noinline__ void record_bounds(int* status, int* fail_site, int site) {
+  if (atomicCAS(status, 0, ATOS_ERR_BOUNDS) == 0 && fail_site) atomicExch(fail_site, site);
+}
+template <class T>
+__device__ __forceinline__ T checked_ix(T i, long long limit, int* status, int* fail_site, int site) {
+  if ((long long)i < 0 || (long long)i >= limit) {
+    record_bounds(status, fail_site, site);
+    return T(0);
+  }
+  return i;
+}
+// i if 0 <= i < limit; else the violation is recorded through `ctx` (anything with status and
+// fail_site pointers: the Launch, a worker's shared state) and the result is 0
+#define ATOS_IX(i, limit, ctx, site) ::atos::checked_ix((i), (long long)(limit), (ctx).status, (ctx).fail_site, (site))
+#else
+#define ATOS_IX(i, limit, ctx, site) (i)
+#endif
+
+// col[k] of an instance's CSR (the entry index and the neighbour id checked in checked builds).
+__device__ __forceinline__ int nbr_at(const Instance& I, int k, const Launch& L) {
+#ifdef ATOS_CHECKED
+  const int nnz = ldg(I.row_ptr + I.n);
+  return ATOS_IX(ldg(I.col + ATOS_IX(k, nnz, L, kSiteEntry)), I.n, L, kSiteNeighbour);
+#else
+  (void)L;
+  return ldg(I.col + k);
+#endif
+}
+
+// A popped item: a vertex of the instance, or (colouring) the check task ~v of one.
+__device__ __forceinline__ int checked_item(const Instance& I, int item, const Launch& L) {
+#ifdef ATOS_CHECKED
+  const bool ok = (item >= 0 && item < I.n) || (I.app == kAppGc && item < 0 && ~item < I.n);
+  if (!ok) {
+    record_bounds(L.status, L.fail_site, kSiteItem);
+    return 0;
+  }
+#else
+  (void)I, (void)L;
+#endif
+  return item;
+}
+
 // Waits until a ring slot of the previous lap has been consumed.  Returns false on timeout or
 // when the launch has failed.
 __device__ __forceinline__ bool wait_slot_empty(unsigned long long* slot, const Launch& L) {
@@ -352,6 +415,8 @@ struct CtaSmem {
   int h, n, flag, cnt;
   unsigned base;
   int inst_id;
+  int* status;     // the launch's status and failed-site words (checked builds record here)
+  int* fail_site;
   Instance I;
   Extra x;
 };
@@ -368,7 +433,7 @@ __device__ __forceinline__ void cta_push(S& sm, bool want, int item) {
   int base = 0;
   if (lane == leader) base = atomicAdd(&sm.npush, __popc(m));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (want) sm.push[base + __popc(m & lanemask_lt())] = item;
+  if (want) sm.push[ATOS_IX(base + __popc(m & lanemask_lt()), S::kPushCap, sm, kSitePushBuffer)] = item;
 }
 
 // Publishes the CTA push buffer and reports `done` finished tasks (call with the whole block,
@@ -424,7 +489,12 @@ __device__ __forceinline__ void lbs_round(const S& sm, const int32_t* __restrict
     if (e < total) {
       while (i + 1 < cnt && sm.off[i + 1] <= e) ++i;
       item[j] = i;
+#ifdef ATOS_CHECKED
+      const int k = ATOS_IX(sm.start[i] + (e - sm.off[i]), ldg(sm.I.row_ptr + sm.I.n), sm, kSiteEntry);
+      nb[j] = ATOS_IX(ldg(col + k), sm.I.n, sm, kSiteNeighbour);
+#else
       nb[j] = ldg(col + sm.start[i] + (e - sm.off[i]));
+#endif
     }
   }
 }
@@ -559,7 +629,7 @@ __device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::template Extra<BLO
       int item = kEmpty;
       if (pending) {
         item = take_ticket(I, sm.tk[threadIdx.x]);
-        if (item != kEmpty) pending = false;
+        if (item != kEmpty) pending = false, item = checked_item(I, item, L);
       }
       // compact the items taken this round into sm.items
       const bool got = item != kEmpty;
@@ -622,7 +692,7 @@ __global__ void __launch_bounds__(BLOCK, (MinBlocks<Body, BLOCK>::value)) cta_pe
   unsigned long long st[kNumStats] = {};
   const unsigned long long t0 = globaltimer();
   int inst = (int)(blockIdx.x % (unsigned)min(L.window, L.ninst));
-  if (threadIdx.x == 0) sm.npush = 0;
+  if (threadIdx.x == 0) sm.npush = 0, sm.status = L.status, sm.fail_site = L.fail_site;
   while (inst >= 0) {
     if (threadIdx.x == 0) {
       sm.I = L.insts[inst];
@@ -657,6 +727,8 @@ __global__ void __launch_bounds__(BLOCK) cta_discrete_kernel(Launch L) {
   if (threadIdx.x == 0) {
     sm.I = L.insts[inst];
     sm.npush = 0;
+    sm.status = L.status;
+    sm.fail_site = L.fail_site;
   }
   __syncthreads();
   const Instance& I = sm.I;
@@ -666,7 +738,8 @@ __global__ void __launch_bounds__(BLOCK) cta_discrete_kernel(Launch L) {
   const int span = (int)min((unsigned)L.fetch, e - lo);
   // every ticket of a generation was written by the previous launch; an EMPTY one can only
   // follow a failed push (the status is already set), and is skipped
-  const int item = (int)threadIdx.x < span ? take_ticket(I, lo + threadIdx.x) : kEmpty;
+  int item = (int)threadIdx.x < span ? take_ticket(I, lo + threadIdx.x) : kEmpty;
+  if (item != kEmpty) item = checked_item(I, item, L);
   int cnt;
   const int pos = block_exclusive_scan<BLOCK>(item != kEmpty ? 1 : 0, sm.tmp, cnt);
   if (item != kEmpty) sm.items[pos] = item;
@@ -689,6 +762,8 @@ struct WarpSmem {
   int push[kWarpPushCap];
   int npush;
   unsigned bits[4];
+  int* status;  // the launch's status and failed-site words (checked builds record here)
+  int* fail_site;
 };
 
 // Appends (warp-wide call) and flushes when the buffer could overflow in the next round.
@@ -697,7 +772,7 @@ __device__ __forceinline__ void warp_push(WarpSmem& ws, bool want, int item) {
   if (!m) return;
   const int lane = threadIdx.x & 31;
   int base = ws.npush;
-  if (want) ws.push[base + __popc(m & lanemask_lt())] = item;
+  if (want) ws.push[ATOS_IX(base + __popc(m & lanemask_lt()), kWarpPushCap, ws, kSiteWarpPush)] = item;
   __syncwarp();
   if (lane == 0) ws.npush = base + __popc(m);
   __syncwarp();
@@ -749,7 +824,7 @@ __device__ void warp_run_instance(WarpSmem& ws, const Instance& I, const Launch&
       int item = kEmpty;
       if (pending) {
         item = take_ticket(I, h + lane);
-        if (item != kEmpty) pending = false;
+        if (item != kEmpty) pending = false, item = checked_item(I, item, L);
       }
       unsigned got = __ballot_sync(0xffffffffu, item != kEmpty);
       const unsigned still = __ballot_sync(0xffffffffu, pending);
@@ -803,7 +878,7 @@ __global__ void __launch_bounds__(kWarpBlock) warp_persistent_kernel(Launch L) {
   const int gw = blockIdx.x * (kWarpBlock / 32) + wid;
   const unsigned long long t0 = globaltimer();
   int inst = gw % min(L.window, L.ninst);
-  if (lane == 0) ws.npush = 0;
+  if (lane == 0) ws.npush = 0, ws.status = L.status, ws.fail_site = L.fail_site;
   __syncwarp();
   while (inst >= 0) {
     const Instance I = L.insts[inst];
@@ -834,10 +909,11 @@ __global__ void __launch_bounds__(kWarpBlock) warp_discrete_kernel(Launch L) {
   const unsigned b = I.ctl->gen_begin, e = I.ctl->gen_end;
   const unsigned lo = b + (blockIdx.x * (kWarpBlock / 32) + wid) * (unsigned)fetch;
   if (lo >= e) return;
-  if (lane == 0) ws.npush = 0;
+  if (lane == 0) ws.npush = 0, ws.status = L.status, ws.fail_site = L.fail_site;
   __syncwarp();
   const int span = (int)min((unsigned)fetch, e - lo);
-  const int item = lane < span ? take_ticket(I, lo + lane) : kEmpty;
+  int item = lane < span ? take_ticket(I, lo + lane) : kEmpty;
+  if (item != kEmpty) item = checked_item(I, item, L);
   unsigned got = __ballot_sync(0xffffffffu, item != kEmpty);  // EMPTY only after a failed push
   const int cnt = __popc(got);
   if constexpr (kLanes) {

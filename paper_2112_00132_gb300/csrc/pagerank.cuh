@@ -266,7 +266,7 @@ struct PrBody {
           if (item[j] >= 0) {
             const float share = __int_as_float(sm.aux[item[j]]);
             const uint32_t slot = I.hub.rank_of(nb[j]);
-            if (slot < (uint32_t)nhub) atomicAdd(&sm.x.hub[slot], share);
+            if (slot < (uint32_t)nhub) atomicAdd(&sm.x.hub[ATOS_IX(slot, HubSlots<BLOCK>::value, sm, kSiteShared)], share);
             else red_add_f32(res + nb[j], share);
           }
       }
@@ -355,7 +355,7 @@ struct PrBody {
         int u = 0;
         bool want = false;
         if (k < e) {
-          u = ldg(I.col + k);
+          u = nbr_at(I, k, L);
           want = pr_add_crossing(I, u, share);
         }
         warp_push(ws, want, u);
@@ -363,7 +363,7 @@ struct PrBody {
       }
       return;
     }
-    for (int k = s + lane; k < e; k += 32) red_add_f32(I.res + ldg(I.col + k), share);
+    for (int k = s + lane; k < e; k += 32) red_add_f32(I.res + nbr_at(I, k, L), share);
     warp_check_scan(ws, I, I.check_size, L, st);
   }
 
@@ -395,7 +395,7 @@ struct PrBody {
       bool want = false;
       int u = 0;
       if (k < e) {
-        u = ldg(I.col + k);
+        u = nbr_at(I, k, L);
         if (I.pr_crossing) want = pr_add_crossing(I, u, share);
         else red_add_f32(I.res + u, share);
         ++k;

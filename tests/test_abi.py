@@ -33,7 +33,7 @@ def test_exports_every_declared_symbol(atos):
 
 def test_status_strings(atos):
     assert atos.status_string(0) == "ok"
-    for code in range(-7, 0):
+    for code in range(-9, 0):
         assert atos.status_string(code) not in ("", "unknown status")
     assert atos.status_string(-99) == "unknown status"
     assert "sm_103a" in atos.version()
@@ -103,3 +103,14 @@ def test_product_path_does_not_import_the_oracle():
     src = "\n".join(open(f).read() for f in glob.glob(os.path.join(ROOT, "paper_2112_00132_gb300", "**", "*.*"),
                                                        recursive=True) if f.endswith((".py", ".cu", ".cuh")))
     assert "import oracle" not in src and "oracle." not in src
+
+
+def test_checked_library_exports_the_same_symbols(atos):
+    """The bounds-checked variant (built with ATOS_CHECKED) exports every function the header
+    declares, like the normal library (no GPU needed to load it)."""
+    from paper_2112_00132_gb300.compile_lib import build
+    lib = ctypes.CDLL(build(checked=True))
+    for name in atos.header_functions():
+        assert hasattr(lib, name), name
+    lib.atos_status_string.restype = ctypes.c_char_p
+    assert b"bounds" in lib.atos_status_string(-9)
