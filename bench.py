@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--flags", type=int, default=0, help="with --no-tune: atos_config.flags of PageRank and colouring")
     ap.add_argument("--policy", type=int, default=2, help="with --no-tune: PageRank's fetch policy (0 fixed, 1 greedy, 2 spread)")
     ap.add_argument("--no-compare", action="store_true", help="skip the BSP / unbatched comparisons")
+    ap.add_argument("--cfg", action="append", default=[], metavar="APP=W,F,P,C,WIN,FLAGS[,STRATEGY]",
+                    help="fix one application's configuration instead of autotuning it (app: bfs, pagerank, "
+                         "color; worker, fetch, fetch policy, Check_Size, window, flags, strategy 0/1/2)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads measured beside the main step (2048^2 grid, batched mix, "
                          "serving window)")
@@ -67,6 +70,20 @@ def parse():
                     help="rmat22: the single-graph step (default); batched: 256 graphs x (4 BFS + 1 PageRank) "
                          "in one batched launch")
     return ap.parse_args()
+
+
+def parse_cfgs(atos, specs):
+    """{app: Config} from --cfg APP=worker,fetch,policy,check_size,window,flags[,strategy]."""
+    out = {}
+    for spec in specs:
+        app, vals = spec.split("=", 1)
+        v = [int(x) for x in vals.split(",")]
+        cfg = atos.queue_config(worker_size=v[0], fetch_size=v[1], fetch_policy=v[2], check_size=v[3], window=v[4],
+                                flags=v[5])
+        if len(v) > 6:
+            cfg.strategy = v[6]
+        out[app] = cfg
+    return out
 
 
 def workload(scale: int):
@@ -240,10 +257,23 @@ def run_atos(args, rank: int, world: int):
                                    flags=args.flags, fetch_policy=args.policy)
         tune_ms = {}
     else:
-        cfg_bfs, t_b = G.autotune("bfs", srcs, repeats=1, stream=stream)
-        cfg_pr, t_p = G.autotune("pagerank", repeats=1, stream=stream)
-        cfg_gc, t_c = G.autotune("color", repeats=1, stream=stream)
-        tune_ms = {"bfs": round(t_b, 3), "pagerank": round(t_p, 3), "color": round(t_c, 3)}
+        fixed = parse_cfgs(atos, args.cfg)
+        tune_ms = {}
+        if "bfs" in fixed:
+            cfg_bfs = fixed["bfs"]
+        else:
+            cfg_bfs, t_b = G.autotune("bfs", srcs, repeats=1, stream=stream)
+            tune_ms["bfs"] = round(t_b, 3)
+        if "pagerank" in fixed:
+            cfg_pr = fixed["pagerank"]
+        else:
+            cfg_pr, t_p = G.autotune("pagerank", repeats=1, stream=stream)
+            tune_ms["pagerank"] = round(t_p, 3)
+        if "color" in fixed:
+            cfg_gc = fixed["color"]
+        else:
+            cfg_gc, t_c = G.autotune("color", repeats=1, stream=stream)
+            tune_ms["color"] = round(t_c, 3)
 
     # warm-up steps with statistics (synchronising), to count the work of a step
     bfs_edges = pr_edges = gc_edges = 0
