@@ -480,14 +480,17 @@ def compare_rmat(atos, G, g, srcs, depths, rank_t, colors, stream, m):
     q = atos.queue_config
     mean = lambda xs: sum(xs) / len(xs)  # noqa: E731
     out = {}
-    # BFS x 64
+    # BFS x 64; the unbatched single-query form with the configuration the autotuner picks for one
+    # source (the tuned multi-source one is shaped for 64 searches at once)
     one = torch.empty((1, g.n), dtype=torch.int32, device="cuda")
+    cfg_one, _ = G.autotune("bfs", [int(srcs[0])], repeats=1, stream=stream)
 
     def unbatched():
         for s0 in srcs:
-            G.bfs([int(s0)], one, cfg=m["cfg_bfs"], stream=stream, stats=False)
+            G.bfs([int(s0)], one, cfg=cfg_one, stream=stream, stats=False)
     bfs = {"persistent_batched_ms": round(mean(m["bfs_ms"]), 3),
-           "persistent_unbatched_ms": round(timed_ms(unbatched, stream, reps=1), 3)}
+           "persistent_unbatched_ms": round(timed_ms(unbatched, stream, reps=1), 3),
+           "unbatched_cfg": cfg_brief(cfg_one)}
     for name, cfg in bsp_configs(atos).items():
         # sources in groups that keep their depth arrays L2-resident (the default), and all at once
         bfs[f"bsp_grouped_{name}_ms"] = round(timed_ms(
@@ -499,6 +502,7 @@ def compare_rmat(atos, G, g, srcs, depths, rank_t, colors, stream, m):
     bfs["bsp_per_source_host_ms"] = round(timed_ms(
         lambda: G.bfs(srcs, depths, cfg=per_source, stream=stream, stats=False), stream, reps=1), 3)
     bfs["best_bsp_ms"] = min(v for k, v in bfs.items() if k.startswith("bsp_"))
+    bfs["unbatched_vs_bsp_per_source"] = round(bfs["bsp_per_source_host_ms"] / bfs["persistent_unbatched_ms"], 3)
     _, bsp_bfs = G.bfs(srcs, depths, cfg=q("bsp"), stream=stream)
     bfs["bsp_levels"] = int(bsp_bfs.iterations)
     out["bfs64"] = bfs

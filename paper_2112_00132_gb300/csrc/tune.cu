@@ -96,6 +96,11 @@ std::vector<atos_config> candidates(int app, int nsrc) {
       out.push_back(c);
     }
   }
+  if (app == ATOS_APP_BFS) {
+    // small greedy pops: a search's late re-expansions of long rows spread over more workers
+    for (int w : {512, 1024})
+      for (int f : {64, 128}) out.push_back(make(nullptr, w, f, ATOS_FETCH_GREEDY));
+  }
   if (app == ATOS_APP_BFS && nsrc > 1) {
     for (int w : {256, 512})
       for (int win : {1, 2, 4, 8, 16, 32}) {
@@ -103,6 +108,11 @@ std::vector<atos_config> candidates(int app, int nsrc) {
         atos_config c = make(nullptr, w, w, ATOS_FETCH_SPREAD);
         c.window = win;
         out.push_back(c);
+        if (w == 512 && win >= 4 && win <= 16) {
+          c = make(nullptr, w, 64, ATOS_FETCH_GREEDY);
+          c.window = win;
+          out.push_back(c);
+        }
       }
   }
   out.push_back(make(nullptr, 1, 32, ATOS_FETCH_SPREAD));  // thread workers
