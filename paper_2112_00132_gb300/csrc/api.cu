@@ -25,7 +25,7 @@ cudaError_t pr_finish(Instance* d_insts, int ninst, int n, int64_t nnz, DevCtl* 
                       double exact_sum, cudaStream_t s);
 cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s);
 cudaError_t gc_split_build(const int32_t* row_ptr, const int32_t* col, int n, int32_t* mid, int32_t* scol,
-                           cudaStream_t s);
+                           int32_t* long_rows, int* long_count, cudaStream_t s);
 cudaError_t gc_wait_init(const int32_t* mid, int n, int32_t* wait, cudaStream_t s);
 size_t spread_build_scratch_bytes(int32_t n);
 cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, int32_t* perm, int32_t* new_rp,
@@ -888,12 +888,14 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
     if (!g->d_gc_wait) ATOS_TRY(dev_alloc(&g->d_gc_wait, (size_t)n));
     const int lay = spread ? 1 : 0;
     if (!g->gc_mid[lay]) {  // the split rows of this layout, built once per graph
-      int32_t *mid = nullptr, *scol = nullptr;
+      int32_t *mid = nullptr, *scol = nullptr, *tmp = nullptr;
       int rc2 = from_cuda(dev_alloc(&mid, (size_t)n));
       if (!rc2) rc2 = from_cuda(dev_alloc(&scol, (size_t)std::max<int64_t>(g->nnz, 1)));
-      if (!rc2) rc2 = from_cuda(gc_split_build(I.row_ptr, I.col, n, mid, scol, st));
+      if (!rc2) rc2 = from_cuda(dev_alloc(&tmp, (size_t)n + 1));  // long rows and their count
+      if (!rc2) rc2 = from_cuda(gc_split_build(I.row_ptr, I.col, n, mid, scol, tmp + 1, (int*)tmp, st));
+      cudaStreamSynchronize(st);  // the list's scratch goes back now
+      pool_free(tmp);
       if (rc2) {
-        cudaStreamSynchronize(st);
         pool_free(mid), pool_free(scol);
         return rc2;
       }

@@ -24,13 +24,22 @@ __global__ void gc_max_kernel(const int32_t* color, int n, int* out) {
 
 // Dependency-ordered colouring uses a copy of the CSR columns whose rows list the smaller-id
 // neighbours first and then the larger ones, each part in the row's order (mid[v]: how many are
-// smaller).  One warp per row: a ballot per 32 entries gives each entry its place.
+// smaller).  One warp per row of at most kLongRow entries (a ballot per 32 entries gives each
+// entry its place); longer rows are listed and split by a whole CTA each, so a hub row does not
+// hold one warp for its whole length.
+constexpr int kLongRow = 2048;
+
 __global__ void gc_split_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int n,
-                                int32_t* __restrict__ mid, int32_t* __restrict__ scol) {
+                                int32_t* __restrict__ mid, int32_t* __restrict__ scol, int32_t* long_rows,
+                                int* long_count) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     const int s = __ldg(row_ptr + v), e = __ldg(row_ptr + v + 1);
+    if (e - s > kLongRow) {
+      if (lane == 0) long_rows[atomicAdd(long_count, 1)] = v;
+      continue;
+    }
     int lower = 0;
     for (int k = s + lane; k < e; k += 32) lower += __ldg(col + k) < v;
     lower = __reduce_add_sync(0xffffffffu, lower);
@@ -51,17 +60,56 @@ __global__ void gc_split_kernel(const int32_t* __restrict__ row_ptr, const int32
   }
 }
 
+// The listed long rows, one CTA of kSplitBlock threads per row at a time: count the smaller
+// neighbours, then place each chunk of kSplitBlock entries with one block scan.
+constexpr int kSplitBlock = 1024;
+
+__global__ void __launch_bounds__(kSplitBlock) gc_split_long_kernel(const int32_t* __restrict__ row_ptr,
+                                                                   const int32_t* __restrict__ col,
+                                                                   int32_t* __restrict__ mid,
+                                                                   int32_t* __restrict__ scol,
+                                                                   const int32_t* long_rows, const int* long_count) {
+  __shared__ int tmp[33];
+  const int t = threadIdx.x;
+  for (int i = blockIdx.x; i < *long_count; i += gridDim.x) {
+    const int v = long_rows[i];
+    const int s = __ldg(row_ptr + v), e = __ldg(row_ptr + v + 1);
+    int c = 0;
+    for (int k = s + t; k < e; k += kSplitBlock) c += __ldg(col + k) < v;
+    int lower;
+    block_exclusive_scan<kSplitBlock>(c, tmp, lower);
+    int lo = 0, hi = 0;  // entries of each part placed so far
+    for (int k0 = s; k0 < e; k0 += kSplitBlock) {
+      const int k = k0 + t;
+      const int u = k < e ? __ldg(col + k) : 0;
+      const bool below = k < e && u < v;
+      int below_total;
+      const int pre = block_exclusive_scan<kSplitBlock>(below ? 1 : 0, tmp, below_total);
+      if (below) scol[s + lo + pre] = u;
+      else if (k < e) scol[s + lower + hi + (t - pre)] = u;
+      lo += below_total;
+      hi += min(kSplitBlock, e - k0) - below_total;
+    }
+    if (t == 0) mid[v] = lower;
+    __syncthreads();
+  }
+}
+
 __global__ void gc_wait_init_kernel(const int32_t* __restrict__ mid, int n, int32_t* wait) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) wait[v] = 1 + mid[v];
 }
 
+// scratch: long_rows of up to n entries and one counter, device memory the caller provides
 cudaError_t gc_split_build(const int32_t* row_ptr, const int32_t* col, int n, int32_t* mid, int32_t* scol,
-                           cudaStream_t s) {
+                           int32_t* long_rows, int* long_count, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(long_count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   int64_t blocks = ((int64_t)n * 32 + 255) / 256;
   blocks = blocks < 1 ? 1 : (blocks > 8192 ? 8192 : blocks);
-  count_launches(1);
-  gc_split_kernel<<<(int)blocks, 256, 0, s>>>(row_ptr, col, n, mid, scol);
+  count_launches(2);
+  gc_split_kernel<<<(int)blocks, 256, 0, s>>>(row_ptr, col, n, mid, scol, long_rows, long_count);
+  gc_split_long_kernel<<<256, kSplitBlock, 0, s>>>(row_ptr, col, mid, scol, long_rows, long_count);
   return cudaGetLastError();
 }
 

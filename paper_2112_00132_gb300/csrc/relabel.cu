@@ -50,7 +50,7 @@ struct HubPlan {
   int32_t hubs;        // H
   int32_t bmin;        // lowest degree class of the hubs (kDegBuckets: none)
   int32_t m;           // n - H
-  int32_t pad;
+  int32_t long_count;  // rows longer than kLongRow, listed for the renaming of their entries
   uint64_t a, c;       // spreading map of the non-hubs
   HubMap map;          // where the hubs sit
   int32_t hist[kDegBuckets];
@@ -210,16 +210,36 @@ __global__ void spread_perm_kernel(const int32_t* __restrict__ rp, int32_t n, co
   }
 }
 
-// One warp per row of the original graph; lanes stride the row and rename through perm.
+// One warp per row of the original graph of at most kLongRow entries; lanes stride the row and
+// rename through perm.  Longer rows are listed for spread_cols_long_kernel, so that a hub row
+// does not hold one warp for its whole length.
+constexpr int kLongRow = 2048;
+
 __global__ void spread_cols_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, int32_t n,
                                    const int32_t* __restrict__ perm, const int32_t* __restrict__ new_rp,
-                                   int32_t* __restrict__ new_col) {
+                                   int32_t* __restrict__ new_col, int32_t* long_rows, int* long_count) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     const int s = __ldg(rp + v), e = __ldg(rp + v + 1);
+    if (e - s > kLongRow) {
+      if (lane == 0) long_rows[atomicAdd(long_count, 1)] = v;
+      continue;
+    }
     const int d = __ldg(new_rp + __ldg(perm + v));
     for (int k = s + lane; k < e; k += 32) new_col[d + (k - s)] = __ldg(perm + __ldg(col + k));
+  }
+}
+
+// The listed long rows, one CTA per row at a time.
+__global__ void spread_cols_long_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                        const int32_t* __restrict__ perm, const int32_t* __restrict__ new_rp,
+                                        int32_t* __restrict__ new_col, const int32_t* long_rows, const int* long_count) {
+  for (int i = blockIdx.x; i < *long_count; i += gridDim.x) {
+    const int v = long_rows[i];
+    const int s = __ldg(rp + v), e = __ldg(rp + v + 1);
+    const int d = __ldg(new_rp + __ldg(perm + v));
+    for (int k = s + threadIdx.x; k < e; k += blockDim.x) new_col[d + (k - s)] = __ldg(perm + __ldg(col + k));
   }
 }
 
@@ -283,8 +303,11 @@ cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, int32
   if (e != cudaSuccess) return e;
   e = bsp::scan_inplace(new_rp, n, bsums, s);  // exclusive scan; new_rp[n] = nnz
   if (e != cudaSuccess) return e;
-  count_launches(1);
-  spread_cols_kernel<<<grid_for((int64_t)n * 32, 256, 8192), 256, 0, s>>>(rp, col, n, perm, new_rp, new_col);
+  count_launches(2);
+  // `before` is free again: it lists the long rows
+  spread_cols_kernel<<<grid_for((int64_t)n * 32, 256, 8192), 256, 0, s>>>(rp, col, n, perm, new_rp, new_col, before,
+                                                                          &plan->long_count);
+  spread_cols_long_kernel<<<512, 1024, 0, s>>>(rp, col, perm, new_rp, new_col, before, &plan->long_count);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   HubPlan h;
