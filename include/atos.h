@@ -132,6 +132,16 @@ extern "C" {
                                      of scratch.  The BSP strategy ignores it; batches and servers
                                      return ATOS_ERR_UNSUPPORTED. */
 
+#define ATOS_FLAG_BFS_SPLIT_ROWS 512u /* atos_bfs with a CTA worker (worker_size >= 64, persistent
+                                     and discrete): a popped vertex whose row holds more than 8192
+                                     entries is pushed back as segment tasks of 4096 entries, which
+                                     any worker expands, instead of one CTA walking the whole row.
+                                     A segment re-reads the vertex's depth when it runs and is
+                                     dropped if the vertex has improved since (the copy queued by the
+                                     improvement expands the row).  About 2 nnz / 4096 16-byte table
+                                     entries per source of scratch; when the table is full a row is
+                                     expanded whole.  Ignored by other workers, batches and servers. */
+
 typedef struct atos_config {
   int32_t worker_size;    /* 1 (thread worker), 32 (warp worker) or a CTA worker of 64,
                              128, 256, 512 or 1024 threads */
@@ -412,8 +422,8 @@ int atos_server_destroy(atos_server_t s);
 /* Times candidate configurations of `app` (ATOS_APP_*) on g and returns the fastest in *best
  * (its device time in *best_ms): CTA workers of 128..1024 threads, warp workers and thread
  * workers, fixed / greedy / spread fetch policies, persistent, discrete and BSP strategies (the
- * BSP level loop on the host and on the device), plus the instance window for multi-source BFS,
- * Check_Size and the threshold-crossing enqueue for PageRank, and the dependency-ordered mode
+ * BSP level loop on the host and on the device), plus the instance window, expansion markers
+ * and row splitting for BFS, Check_Size and the threshold-crossing enqueue for PageRank, and the dependency-ordered mode
  * for colouring (Figure 4's worker-size x FETCH_SIZE sweep with the kernel strategy of
  * Section 3.4).  Each candidate runs repeats + 1 times (the first warms up); failing candidates,
  * PageRank candidates whose error bound exceeds ATOS_TUNE_PR_MAX_ERROR and colouring candidates

@@ -7,7 +7,7 @@ in ``libatos.so`` (hand-written CUDA behind the C ABI of ``include/atos.h``); th
 Python binding.
 """
 from ._binding import (  # noqa: F401
-    BSP, DISCRETE, FETCH_FIXED, FETCH_GREEDY, FETCH_SPREAD, FLAG_PHANTOM_TASK, FLAG_PR_CROSSING, FLAG_SPREAD_IDS, FLAG_GC_ORDERED, FLAG_BFS_EXPAND_ONCE, FLAG_BSP_DEVICE_LOOP, FLAG_BSP_PER_SOURCE, FLAG_GC_DEPENDENCY, PERSISTENT, UNREACHED, WORKER_WARP, WORKER_THREAD,
+    BSP, DISCRETE, FETCH_FIXED, FETCH_GREEDY, FETCH_SPREAD, FLAG_PHANTOM_TASK, FLAG_PR_CROSSING, FLAG_SPREAD_IDS, FLAG_GC_ORDERED, FLAG_BFS_EXPAND_ONCE, FLAG_BSP_DEVICE_LOOP, FLAG_BSP_PER_SOURCE, FLAG_GC_DEPENDENCY, FLAG_BFS_SPLIT_ROWS, PERSISTENT, UNREACHED, WORKER_WARP, WORKER_THREAD,
     AtosError, Batch, Completion, batch_autotune, Config, Graph, Instance, Server, Stats, csr_validate, header_functions, kernel_launches, lib, queue_config, status_string,
     version,
 )

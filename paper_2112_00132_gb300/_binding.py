@@ -42,6 +42,7 @@ FLAG_BFS_EXPAND_ONCE = 32
 FLAG_BSP_DEVICE_LOOP = 64
 FLAG_BSP_PER_SOURCE = 128
 FLAG_GC_DEPENDENCY = 256
+FLAG_BFS_SPLIT_ROWS = 512
 DEVICE_PTRS, BORROW, CHECK_SYMMETRIC, SKIP_VALIDATION = 1, 2, 4, 8
 UNREACHED = 2**31 - 1
 

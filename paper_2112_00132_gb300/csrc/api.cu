@@ -122,6 +122,9 @@ struct atos_graph_s {
   int32_t sp_hubs = 0;         // hubs of the copy (its highest-degree vertices)
   HubMap sp_hub = {0, 1, 1, 0};  // where they sit
   int32_t* d_expanded = nullptr;  // BFS: per source, the smallest depth each vertex was expanded at
+  int4* d_segs = nullptr;         // BFS row splitting: per source, a segment table of seg_cap entries
+  size_t seg_rows = 0;
+  uint32_t seg_cap = 0;
   int32_t* d_gc_wait = nullptr;   // dependency-ordered colouring: per vertex, counts still to go
   // dependency-ordered colouring: per layout (input ids, spread-id copy), the rows with the
   // smaller-id neighbours first (gc_col) and how many they are (gc_mid); built on first use
@@ -263,7 +266,7 @@ int check_config(const atos_config& c) {
     return ATOS_ERR_INVALID_ARG;
   if (c.flags & ~(ATOS_FLAG_PHANTOM_TASK | ATOS_FLAG_PR_CROSSING | ATOS_FLAG_SPREAD_IDS | ATOS_FLAG_USE_TUNED |
                   ATOS_FLAG_GC_ORDERED | ATOS_FLAG_BFS_EXPAND_ONCE | ATOS_FLAG_BSP_DEVICE_LOOP |
-                  ATOS_FLAG_BSP_PER_SOURCE | ATOS_FLAG_GC_DEPENDENCY))
+                  ATOS_FLAG_BSP_PER_SOURCE | ATOS_FLAG_GC_DEPENDENCY | ATOS_FLAG_BFS_SPLIT_ROWS))
     return ATOS_ERR_INVALID_ARG;
   return ATOS_OK;
 }
@@ -611,6 +614,7 @@ int atos_graph_destroy(atos_graph_t g) {
   pool_free_host(g->h_bsp);
   pool_free(g->sp_row_ptr), pool_free(g->sp_col), pool_free(g->sp_out), pool_free(g->sp_perm);
   pool_free(g->d_expanded);
+  pool_free(g->d_segs);
   pool_free(g->d_gc_wait);
   for (int k = 0; k < 2; ++k) pool_free(g->gc_mid[k]), pool_free(g->gc_col[k]);
   pool_free(g->d_timeline);
@@ -695,10 +699,25 @@ int atos_bfs(atos_graph_t g, const int32_t* sources, int32_t nsrc, int32_t* dept
     ATOS_TRY(dev_alloc(&g->d_expanded, (size_t)nsrc * (size_t)n));
     g->expanded_rows = (size_t)nsrc;
   }
+  // row splitting needs a CTA worker (the warp and thread workers expand a row themselves)
+  const bool split = (cfg.flags & ATOS_FLAG_BFS_SPLIT_ROWS) != 0 && cfg.worker_size > 32;
+  if (split && (size_t)nsrc > g->seg_rows) {
+    // per source, room for every row longer than the split threshold split twice over (a row
+    // split again after an improvement of its vertex); a full table expands rows whole
+    cudaDeviceSynchronize();
+    pool_free(g->d_segs);
+    g->d_segs = nullptr;
+    g->seg_rows = 0;
+    const uint64_t cap_segs = std::max<uint64_t>(1024, 2 * (uint64_t)g->nnz / 4096 + 64);
+    g->seg_cap = (uint32_t)std::min<uint64_t>(cap_segs, 1u << 30);
+    ATOS_TRY(dev_alloc(&g->d_segs, (size_t)nsrc * g->seg_cap));
+    g->seg_rows = (size_t)nsrc;
+  }
   for (int32_t i = 0; i < nsrc; ++i) {
     Instance I = base_instance(g, i, kAppBfs, cap, 1, sources[i]);
     I.depth = depths + (size_t)i * n;
     I.expanded = marks ? g->d_expanded + (size_t)i * n : nullptr;
+    if (split) I.segs = g->d_segs + (size_t)i * g->seg_cap, I.seg_cap = g->seg_cap;
     g->s.h_insts[i] = I;
   }
   if (cfg.window == 0) {

@@ -6,6 +6,8 @@
 namespace atos {
 
 constexpr int kMarkMinDegree = 16;  // ATOS_FLAG_BFS_EXPAND_ONCE: rows this long or longer are marked
+constexpr int kSplitDegree = 8192;  // ATOS_FLAG_BFS_SPLIT_ROWS: longer rows become segment tasks
+constexpr int kSegment = 4096;      // entries per segment task
 
 struct BfsBody {
   template <int B>
@@ -32,24 +34,69 @@ struct BfsBody {
     }
   }
 
+  // Row splitting: the rows of `parts` > 0 become segment tasks of kSegment entries, table entry
+  // (vertex, first entry, depth the row was popped at) and item -(entry + 1); returns false
+  // (nothing split) when the table is full.  Whole block.
+  template <int BLOCK, class S>
+  __device__ static bool split_rows(S& sm, int parts, int v, int s, int d, const Launch& L, unsigned long long* st) {
+    const Instance& I = sm.I;
+    int total;
+    const int off = block_exclusive_scan<BLOCK>(parts, sm.tmp, total);  // ends with a barrier
+    if (threadIdx.x == 0) sm.base = atomicAdd(&I.ctl->seg_next, (unsigned)total);
+    __syncthreads();
+    const unsigned j0 = sm.base;
+    if (j0 + (unsigned)total > I.seg_cap || j0 + (unsigned)total < j0) return false;  // uniform
+    for (int k = 0; k < parts; ++k) I.segs[j0 + off + k] = make_int4(v, s + k * kSegment, d, 0);
+    for (int w = 0; w < total; w += S::kPushCap) {  // push the segment items, a buffer at a time
+      const int need = min(S::kPushCap, total - w);
+      if (sm.npush + need > S::kPushCap) cta_flush<BLOCK>(sm, I, 0, L, st);
+      const int at = sm.npush - w;
+      for (int k = 0; k < parts; ++k) {
+        const int idx = off + k;
+        if (idx >= w && idx < w + need) sm.push[ATOS_IX(at + idx, S::kPushCap, sm, kSitePushBuffer)] = -(int)(j0 + idx + 1);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) sm.npush += need;
+      __syncthreads();
+    }
+    return true;
+  }
+
   // CTA worker: stage (row start, depth + 1) of the popped vertices, scan their degrees and map
   // the flattened neighbour range onto the threads (load-balancing search inside the worker).
+  // With a segment table (ATOS_FLAG_BFS_SPLIT_ROWS) a popped vertex whose row exceeds
+  // kSplitDegree entries is pushed back as segment tasks, which any worker expands (re-reading the
+  // vertex's depth then), so one long row is spread over the grid instead of holding one CTA.
   template <int BLOCK, class S>
   __device__ static void cta_batch(S& sm, int cnt, const Launch& L, unsigned long long* st) {
     const Instance& I = sm.I;
-    int deg = 0;
+    int deg = 0, parts = 0, v = 0, s = 0, d = 0;
     if ((int)threadIdx.x < cnt) {
-      const int v = sm.items[threadIdx.x];
-      const int s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
-      const int d = ld_relaxed(I.depth + v);
+      const int item = sm.items[threadIdx.x];
+      int e;
+      if (item >= 0) {
+        v = item;
+        s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
+        d = ld_relaxed(I.depth + v);
+      } else {  // a segment of a split row (entries are written once per run: read past L1)
+        const int4 sg = __ldcg(I.segs + ATOS_IX(-(item + 1), I.seg_cap, sm, kSiteItem));
+        v = sg.x, s = sg.y;
+        e = min(ldg(I.row_ptr + v + 1), s + kSegment);
+        d = ld_relaxed(I.depth + v);
+        // the vertex improved since the row was split: the copy pushed by that improvement
+        // expands the whole row at the better depth
+        if (d < sg.z) e = s;
+      }
       sm.start[threadIdx.x] = s;
       sm.aux[threadIdx.x] = d + 1;
       deg = d == kUnreached ? 0 : e - s;  // a queued vertex always has a depth; never relax from INT32_MAX
       // a vertex queued twice is expanded once per depth: a task finding it already expanded at
       // this depth or a better one (by a copy popped after the improvement) skips the expansion;
       // rows shorter than kMarkMinDegree are cheaper to re-expand than to mark
-      if (deg >= kMarkMinDegree && I.expanded && atomicMin(I.expanded + v, d) <= d) deg = 0;
+      if (item >= 0 && deg >= kMarkMinDegree && I.expanded && atomicMin(I.expanded + v, d) <= d) deg = 0;
+      if (item >= 0 && deg > kSplitDegree && I.segs) parts = (deg + kSegment - 1) / kSegment;
     }
+    if (I.segs && __syncthreads_or(parts > 0) && split_rows<BLOCK>(sm, parts, v, s, d, L, st) && parts > 0) deg = 0;
     int total;
     const int off = block_exclusive_scan<BLOCK>(deg, sm.tmp, total);
     if ((int)threadIdx.x < cnt) sm.off[threadIdx.x] = off;

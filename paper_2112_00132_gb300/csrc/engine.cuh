@@ -72,7 +72,8 @@ struct alignas(128) QueueCtl {
   unsigned int gen_end;
   unsigned int orphan_count[2];  // serving: pop tickets left pending by paused workers, per epoch parity
   unsigned int orphan_head;      // serving: orphans of the previous epoch handed out so far
-  char pad3[84];
+  unsigned int seg_next;         // BFS row splitting: segment-table entries handed out
+  char pad3[80];
 };
 static_assert(sizeof(QueueCtl) == 512, "QueueCtl layout");
 
@@ -106,6 +107,8 @@ struct Instance {
                          // `col` lists first in its row (the larger ones follow)
   double* cert_y;        // PageRank in batches and serving: FP64 scratch (n) of the output certificate
   int32_t* expanded;     // BFS (optional): the smallest depth at which each vertex has been expanded
+  int4* segs;            // BFS row splitting (optional): segment tasks (vertex, first entry, depth, -)
+  uint32_t seg_cap;      // entries of segs
   double exact_sum;      // PageRank: n - alpha * (isolated vertices), the fixed point's sum
   HubMap hub;            // PageRank on the spread-id copy: the hubs' ids
 };
@@ -266,7 +269,8 @@ __device__ __forceinline__ int nbr_at(const Instance& I, int k, const Launch& L)
 // A popped item: a vertex of the instance, or (colouring) the check task ~v of one.
 __device__ __forceinline__ int checked_item(const Instance& I, int item, const Launch& L) {
 #ifdef ATOS_CHECKED
-  const bool ok = (item >= 0 && item < I.n) || (I.app == kAppGc && item < 0 && ~item < I.n);
+  const bool ok = (item >= 0 && item < I.n) || (I.app == kAppGc && item < 0 && ~item < I.n) ||
+                  (I.app == kAppBfs && I.segs && item < 0 && (uint32_t)(-(item + 1)) < I.seg_cap);
   if (!ok) {
     record_bounds(L.status, L.fail_site, kSiteItem);
     return 0;

@@ -43,6 +43,7 @@ __global__ void prepare_kernel(Instance* insts, DevCtl* ctl, uint32_t flags, uns
     c->gen_end = I.prefix_len;
     c->orphan_count[0] = c->orphan_count[1] = 0;
     c->orphan_head = 0;
+    c->seg_next = 0;
     for (int k = 0; k < kNumStats; ++k) I.stats[k] = 0;
     if (blockIdx.y == 0) {
       ctl->status = 0;

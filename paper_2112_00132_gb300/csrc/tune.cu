@@ -124,6 +124,10 @@ std::vector<atos_config> candidates(int app, int nsrc) {
         atos_config c = out[i];
         c.flags |= ATOS_FLAG_BFS_EXPAND_ONCE;
         out.push_back(c);
+        if (c.worker_size > 32) {  // and with long rows split into segment tasks
+          c.flags |= ATOS_FLAG_BFS_SPLIT_ROWS;
+          out.push_back(c);
+        }
       }
   }
   if (app == ATOS_APP_PAGERANK || app == ATOS_APP_COLOR) {

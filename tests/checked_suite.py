@@ -40,6 +40,7 @@ def main():
 
     graphs = dict(small_graphs())
     graphs["rmat14"] = gg.rmat(14, 16, seed=5)
+    graphs["star12000"] = gg.star(12000)  # a row long enough to be split into segment tasks
     for gname, g in graphs.items():
         srcs = bfs_sources(g)
         bfs_ref = np.stack([oracle.bfs(g, s) for s in srcs])
@@ -51,7 +52,7 @@ def main():
             for cname, cfg in shapes.items():
                 base = cfg.flags
                 try:
-                    for flags in (0, atos.FLAG_BFS_EXPAND_ONCE):
+                    for flags in (0, atos.FLAG_BFS_EXPAND_ONCE, atos.FLAG_BFS_EXPAND_ONCE | atos.FLAG_BFS_SPLIT_ROWS):
                         cfg.flags = base | flags
                         d, st = G.bfs(srcs, cfg=cfg)
                         runs += 1

@@ -268,3 +268,66 @@ def test_thread_workers_arguments(atos):
         with pytest.raises(atos.AtosError) as e:
             atos.Server([G], max_slots=4, budget_bytes=1 << 26, cfg=cfg)
         assert e.value.status == atos.abi.ERR_UNSUPPORTED
+
+
+def _hub_chain(k=3, leaves=12000, seed=4):
+    """k hubs of `leaves` leaves each, hub i joined to hub i+1 by a path of i+2 edges and to a
+    shared ring of 50 vertices, so the search reaches the hubs at several depths (and may reach a
+    hub first by a longer route)."""
+    pairs, nxt = [], 0
+    hubs = list(range(k))
+    nxt = k
+    ring = list(range(nxt, nxt + 50))
+    nxt += 50
+    pairs += [(ring[i], ring[(i + 1) % 50]) for i in range(50)]
+    for i, h in enumerate(hubs):
+        pairs += [(h, nxt + j) for j in range(leaves)]
+        nxt += leaves
+        pairs.append((h, ring[(17 * i) % 50]))
+        if i + 1 < k:
+            path = list(range(nxt, nxt + i + 1))
+            nxt += i + 1
+            chain = [h] + path + [hubs[i + 1]]
+            pairs += list(zip(chain[:-1], chain[1:]))
+    return gg.from_edges(nxt, pairs, "hub_chain")
+
+
+def test_bfs_split_rows(atos):
+    """ATOS_FLAG_BFS_SPLIT_ROWS: rows longer than 8192 entries become segment tasks; depths stay
+    bit-exact for every CTA configuration, with and without expansion markers, and more tasks
+    are popped than vertices expanded (the segments).  Warp and thread workers ignore the flag."""
+    for g in (gg.rmat(18, 16, seed=5), gg.star(20000), _hub_chain()):
+        deg = np.diff(g.row_ptr)
+        assert (deg > 8192).any()
+        srcs = bfs_sources(g) + [int(np.argmax(deg))]
+        ref = np.stack([oracle.bfs(g, s) for s in srcs])
+        with atos.Graph.from_csr(g) as G:
+            for cname, cfg in {**configs(atos), **thread_worker_configs(atos)}.items():
+                if cname.startswith("bsp"):
+                    continue
+                base = cfg.flags | atos.FLAG_BFS_SPLIT_ROWS
+                for extra in (0, atos.FLAG_BFS_EXPAND_ONCE):
+                    cfg.flags = base | extra
+                    d, st = G.bfs(srcs, cfg=cfg)
+                    assert st.status == 0, (g.name, cname, extra, st.status)
+                    assert np.array_equal(d.cpu().numpy(), ref), (g.name, cname, extra)
+                    if cfg.worker_size > 32 and extra:
+                        # the hub source's row alone is split into ceil(deg / 4096) segments
+                        assert st.tasks > int((ref != oracle.UNREACHED).sum()), (g.name, cname)
+
+
+def test_bfs_split_rows_many_sources(atos):
+    """Segment tables of 64 sources run in windows of 8 and all at once (RMAT scale 18)."""
+    g = gg.rmat(18, 16, seed=5)
+    srcs = [int(x) for x in gg.sources(g, 64, seed=3)]
+    refs = np.stack([oracle.bfs(g, s) for s in srcs[:8]])
+    with atos.Graph.from_csr(g) as G:
+        for window in (8, 0):
+            cfg = atos.queue_config(worker_size=512, fetch_size=512, window=window,
+                                    flags=atos.FLAG_BFS_SPLIT_ROWS | atos.FLAG_BFS_EXPAND_ONCE)
+            d, st = G.bfs(srcs, cfg=cfg)
+            assert st.status == 0
+            d = d.cpu().numpy()
+            assert np.array_equal(d[:8], refs), window
+            for i in range(8, 64, 8):
+                assert oracle.bfs_certificate(g, srcs[i], d[i]) == (0, -1), (window, srcs[i])
