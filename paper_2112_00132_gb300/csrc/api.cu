@@ -27,6 +27,9 @@ cudaError_t gc_finish(const Instance* h_inst, DevCtl* d_ctl, cudaStream_t s);
 cudaError_t gc_split_build(const int32_t* row_ptr, const int32_t* col, int n, int32_t* mid, int32_t* scol,
                            int32_t* long_rows, int* long_count, cudaStream_t s);
 cudaError_t gc_wait_init(const int32_t* mid, int n, int32_t* wait, cudaStream_t s);
+int64_t gc_bitmap_scratch(int n);
+cudaError_t gc_bitmap_build(const int32_t* mid, int n, int2* fw, int32_t* scratch, uint32_t* total_words,
+                            cudaStream_t s);
 size_t spread_build_scratch_bytes(int32_t n);
 cudaError_t spread_build(const int32_t* rp, const int32_t* col, int32_t n, int32_t* perm, int32_t* new_rp,
                          int32_t* new_col, int32_t* bsums, void* scratch, int32_t* h_hubs, HubMap* h_map,
@@ -130,6 +133,10 @@ struct atos_graph_s {
   // smaller-id neighbours first (gc_col) and how many they are (gc_mid); built on first use
   int32_t* gc_mid[2] = {nullptr, nullptr};
   int32_t* gc_col[2] = {nullptr, nullptr};
+  int2* gc_fw[2] = {nullptr, nullptr};      // pushed colours: each vertex's bitmap (first word, words)
+  uint32_t gc_fwords[2] = {0, 0};           // bitmap words of each layout
+  unsigned* d_gc_forbid = nullptr;          // the bitmaps (gc_forbid_cap words)
+  uint32_t gc_forbid_cap = 0;
   size_t expanded_rows = 0;
   unsigned long long* d_timeline = nullptr;  // throughput timeline (atos_timeline), 2 counters per bucket
   int64_t tl_bucket_ns = 0;
@@ -616,7 +623,8 @@ int atos_graph_destroy(atos_graph_t g) {
   pool_free(g->d_expanded);
   pool_free(g->d_segs);
   pool_free(g->d_gc_wait);
-  for (int k = 0; k < 2; ++k) pool_free(g->gc_mid[k]), pool_free(g->gc_col[k]);
+  for (int k = 0; k < 2; ++k) pool_free(g->gc_mid[k]), pool_free(g->gc_col[k]), pool_free(g->gc_fw[k]);
+  pool_free(g->d_gc_forbid);
   pool_free(g->d_timeline);
   g->s.release();
   delete g;
@@ -920,14 +928,42 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
       }
       g->gc_mid[lay] = mid, g->gc_col[lay] = scol;
     }
+    if (!g->gc_fw[lay]) {  // pushed colours: the bitmaps' places, built once per layout
+      int2* fw = nullptr;
+      int32_t* tmp = nullptr;
+      uint32_t words = 0;
+      int rc2 = from_cuda(dev_alloc(&fw, (size_t)n));
+      if (!rc2) rc2 = from_cuda(dev_alloc(&tmp, (size_t)gc_bitmap_scratch(n)));
+      if (!rc2) rc2 = from_cuda(gc_bitmap_build(g->gc_mid[lay], n, fw, tmp, &words, st));  // synchronises
+      pool_free(tmp);
+      if (rc2) {
+        pool_free(fw);
+        return rc2;
+      }
+      g->gc_fw[lay] = fw, g->gc_fwords[lay] = words;
+    }
+    if (g->gc_forbid_cap < g->gc_fwords[lay]) {
+      cudaDeviceSynchronize();  // a previous call may still use the old bitmaps
+      pool_free(g->d_gc_forbid);
+      g->d_gc_forbid = nullptr;
+      g->gc_forbid_cap = 0;
+      ATOS_TRY(dev_alloc(&g->d_gc_forbid, (size_t)std::max<uint32_t>(g->gc_fwords[lay], 1)));
+      g->gc_forbid_cap = g->gc_fwords[lay];
+    }
     I.gc_wait = g->d_gc_wait;
     I.gc_mid = g->gc_mid[lay];
     I.col = g->gc_col[lay];
+    I.gc_fw = g->gc_fw[lay];
+    I.gc_forbid = g->d_gc_forbid;
+    I.gc_forbid_words = g->gc_fwords[lay];
   }
   g->s.h_insts[0] = I;
   cfg.window = 1;
   ATOS_TRY(cudaEventRecord(g->s.ev0, st));
-  if (dependency) ATOS_TRY(gc_wait_init(I.gc_mid, n, I.gc_wait, st));
+  if (dependency) {
+    ATOS_TRY(gc_wait_init(I.gc_mid, n, I.gc_wait, st));
+    if (I.gc_forbid) ATOS_TRY(cudaMemsetAsync(I.gc_forbid, 0, sizeof(unsigned) * I.gc_forbid_words, st));
+  }
   int64_t iters = 0;
   rc = run_instances(g, 1, n, cfg, gc_persistent_kernel, gc_discrete_kernel, kAppGc, st, &iters);
   if (rc) return rc;

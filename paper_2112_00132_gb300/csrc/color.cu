@@ -1,5 +1,6 @@
 // color.cu -- colouring kernels: persistent / discrete instantiations of the task body in
 // color.cuh and the colour-count reduction.
+#include "bsp.cuh"
 #include "color.cuh"
 #include "engine.cuh"
 #include "launch.cuh"
@@ -111,6 +112,38 @@ cudaError_t gc_split_build(const int32_t* row_ptr, const int32_t* col, int n, in
   gc_split_kernel<<<(int)blocks, 256, 0, s>>>(row_ptr, col, n, mid, scol, long_rows, long_count);
   gc_split_long_kernel<<<256, kSplitBlock, 0, s>>>(row_ptr, col, mid, scol, long_rows, long_count);
   return cudaGetLastError();
+}
+
+// Pushed colours: vertex v's bitmap has (mid[v] + 32) / 32 words (room for colours 0..mid[v],
+// which holds its first-fit colour); fw[v] = (first word, words), the words laid out in id order.
+__global__ void gc_words_kernel(const int32_t* __restrict__ mid, int n, int32_t* __restrict__ words) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    words[v] = (mid[v] + 32) >> 5;
+}
+
+__global__ void gc_fw_kernel(const int32_t* __restrict__ first, int n, int2* __restrict__ fw) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    fw[v] = make_int2(first[v], first[v + 1] - first[v]);
+}
+
+int64_t gc_bitmap_scratch(int n) { return (int64_t)n + 1 + n / 1024 + 2; }
+
+cudaError_t gc_bitmap_build(const int32_t* mid, int n, int2* fw, int32_t* scratch, uint32_t* total_words,
+                            cudaStream_t s) {
+  *total_words = 0;
+  if (n <= 0) return cudaSuccess;
+  int blocks = (n + 255) / 256;
+  blocks = blocks < 1 ? 1 : (blocks > 4096 ? 4096 : blocks);
+  count_launches(2);
+  gc_words_kernel<<<blocks, 256, 0, s>>>(mid, n, scratch);
+  cudaError_t e = bsp::scan_inplace(scratch, n, scratch + n + 1, s);
+  if (e != cudaSuccess) return e;
+  gc_fw_kernel<<<blocks, 256, 0, s>>>(scratch, n, fw);
+  int32_t words = 0;
+  e = cudaMemcpyAsync(&words, scratch + n, sizeof(words), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) *total_words = (uint32_t)words;
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t gc_wait_init(const int32_t* mid, int n, int32_t* wait, cudaStream_t s) {

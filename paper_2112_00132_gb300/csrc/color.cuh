@@ -29,6 +29,17 @@
 // fenced before the decrements that follow it, and the task that reads it was pushed (fenced,
 // published) by the decrement that completed the count, so the colours a ready vertex reads are
 // final.
+//
+// With pushed colours (I.gc_forbid set) a ready vertex reads no neighbour at all: every vertex
+// has a bitmap of (smaller neighbours + 1) colour bits, and a coloured vertex sets its colour's bit
+// in the bitmap of each larger neighbour just before decrementing that neighbour's count.  When
+// the count reaches zero the bitmap holds the colours of all smaller neighbours, and the first
+// zero bit is the first-fit colour (at most `smaller neighbours` bits are set, so one of the first
+// smaller + 1 is clear; a colour beyond the bitmap cannot be the first free one and is not
+// recorded).  This moves the reading of a vertex's smaller neighbours off the dependency chain:
+// the chain's hops are then a bitmap scan and a decrement each, whatever the row lengths.  The bits
+// are fenced before the decrements, and the decrement that completes a count fences before it
+// pushes the vertex, so the bitmap a ready vertex reads is complete.
 #pragma once
 
 #include "engine.cuh"
@@ -42,6 +53,26 @@ struct GcExtra {
   unsigned bits[2 * B];  // per item: forbidden colours [base, base + 64) (assign) or
                          // (own colour, conflict flag) (check)
 };
+
+// Pushed colours: records colour c in the bitmap of the larger neighbour w (when the bitmap has
+// room for it: first fit for w is at most its smaller-neighbour count).
+template <class Ctx>
+__device__ __forceinline__ void gc_push_colour(const Instance& I, int w, int c, Ctx& ctx) {
+  const int2 f = __ldg(I.gc_fw + w);
+  if ((c >> 5) < f.y)
+    atomicOr(I.gc_forbid + ATOS_IX(f.x + (c >> 5), I.gc_forbid_words, ctx, kSiteEntry), 1u << (c & 31));
+}
+
+// Pushed colours: the first-fit colour of a ready vertex, the first clear bit of its bitmap.
+template <class Ctx>
+__device__ __forceinline__ int gc_first_free(const Instance& I, int v, Ctx& ctx) {
+  const int2 f = __ldg(I.gc_fw + v);
+  for (int w = 0; w < f.y; ++w) {
+    const unsigned b = __ldcg(I.gc_forbid + ATOS_IX(f.x + w, I.gc_forbid_words, ctx, kSiteEntry));
+    if (~b) return 32 * w + __ffs(~b) - 1;
+  }
+  return 32 * f.y;  // not reached: at most f.y * 32 - 1 bits are set
+}
 
 // Queues an assign task for u unless one is already queued.
 __device__ __forceinline__ bool gc_claim_assign(const Instance& I, int u) {
@@ -60,8 +91,37 @@ struct GcBody {
   // their larger neighbours (the rest of the row).  A vertex made ready is published as soon as
   // the round that made it ready ends, not at the end of the batch: a hub's row is long, and the
   // next vertex on the longest dependency path is often among the first it releases.
+  //
+  // Local continuation: the vertices the last countdown round made ready (up to FETCH_SIZE of
+  // them) are not published but run by this CTA as its next batch, which takes the queue's
+  // push-pop round trip off a dependency chain's hops; the rest are published.  While a CTA holds
+  // such local work it leaves one task of the batch it popped unreported, so the instance cannot
+  // look finished (completed = pushed) before the local work, and whatever it releases, is done.
   template <int BLOCK, class S>
   __device__ static void cta_batch_dependency(S& sm, int cnt, const Launch& L, unsigned long long* st) {
+    const int keep_max = min(L.fetch, BLOCK);
+    int from_queue = cnt;
+    bool open = false;
+    for (;;) {
+      const int keep = cta_dependency_round<BLOCK>(sm, cnt, keep_max, L, st);
+      int done = from_queue;
+      if (keep && !open) done -= 1, open = true;  // from_queue >= 1 here: the first batch was popped
+      else if (!keep && open) done += 1, open = false;
+      const int item = (int)threadIdx.x < keep ? sm.push[threadIdx.x] : 0;
+      cta_flush<BLOCK>(sm, sm.I, done, L, st, keep);  // publishes the rest
+      if (!keep) return;
+      if ((int)threadIdx.x < keep) sm.items[threadIdx.x] = item;
+      __syncthreads();
+      cnt = keep;
+      from_queue = 0;
+    }
+  }
+
+  // One batch of the dependency-ordered mode; returns how many of the vertices its last
+  // countdown round made ready (the first entries of the push buffer, which the caller
+  // publishes from there on) it keeps for local continuation.
+  template <int BLOCK, class S>
+  __device__ static int cta_dependency_round(S& sm, int cnt, int keep_max, const Launch& L, unsigned long long* st) {
     const Instance& I = sm.I;
     const int t = threadIdx.x;
     int v = 0, lower = 0, upper = 0, s = 0;
@@ -80,9 +140,68 @@ struct GcBody {
     int64_t edges = 0;
     int colour = -1;
     constexpr int R = LbsRun<BLOCK>::R;
-    // First fit is at most the number of smaller neighbours, so a vertex needs lower + 1 colour
-    // bits.  When the batch's bitmaps fit in shared memory (2 words per thread) one pass over the
-    // smaller neighbours decides every colour; otherwise windows of 64 colours are examined in turn.
+    if (I.gc_forbid) {
+      if (ready) colour = gc_first_free(I, v, sm);
+    } else {
+      colour_from_reads<BLOCK>(sm, cnt, ready, lower, colour, edges);
+    }
+    if (ready) {
+      st_relaxed(I.color + v, colour);
+      __threadfence();  // the colour is visible before any decrement below can make a neighbour ready
+    }
+    // count down the larger neighbours of every ready vertex; the decrement that reaches zero
+    // pushes the neighbour
+    if (t < cnt) {
+      sm.start[t] = s + lower;
+      sm.aux[t] = colour;
+    }
+    int total;
+    const int off = block_exclusive_scan<BLOCK>(upper, sm.tmp, total);
+    if (t < cnt) sm.off[t] = off;
+    __syncthreads();
+    __threadfence();  // (the other threads' colour writes of this batch, ordered by the barrier)
+    for (int r = 0; r < total; r += BLOCK * R) {
+      int owner[R], nb[R];
+      lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
+      if (I.gc_forbid && owner[0] >= 0) {
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          if (owner[j] >= 0) gc_push_colour(I, nb[j], sm.aux[owner[j]], sm);
+        __threadfence();  // the colour bits are visible before the decrements
+      }
+      bool made_ready = false;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const bool go = owner[j] >= 0 && atomicSub(I.gc_wait + nb[j], 1) == 1;
+        made_ready |= go;
+        cta_push(sm, go, ~nb[j]);
+      }
+      if (made_ready) __threadfence();  // the count's other decrements (and their writes) come first
+      __syncthreads();
+      // publish a round's ready vertices right away, except the last round's (kept or published
+      // by the caller)
+      if (sm.npush > 0 && r + BLOCK * R < total) cta_flush<BLOCK>(sm, I, 0, L, st);
+    }
+    __syncthreads();
+    if (t == 0) {
+      st[kStatTasks] += cnt;
+      st[kStatEdges] += edges + total;
+    }
+    // a failed launch stops here (the caller publishes, and nothing is kept); one thread decides
+    if (t == 0) sm.keep = ld_relaxed(L.status) != 0 ? 0 : min(sm.npush, keep_max);
+    __syncthreads();
+    return sm.keep;
+  }
+
+  // The colours of the ready vertices of a CTA batch from their smaller neighbours' colours.
+  // First fit is at most the number of smaller neighbours, so a vertex needs lower + 1 colour
+  // bits.  When the batch's bitmaps fit in shared memory (2 words per thread) one pass over the
+  // smaller neighbours decides every colour; otherwise windows of 64 colours are examined in turn.
+  template <int BLOCK, class S>
+  __device__ static void colour_from_reads(S& sm, int cnt, bool ready, int lower, int& colour, int64_t& edges) {
+    const Instance& I = sm.I;
+    const int t = threadIdx.x;
+    constexpr int R = LbsRun<BLOCK>::R;
     int words_total;
     const int woff = block_exclusive_scan<BLOCK>(ready ? (lower + 32) >> 5 : 0, sm.tmp, words_total);
     if (words_total <= 2 * BLOCK) {
@@ -150,38 +269,6 @@ struct GcBody {
         if (!__syncthreads_or(again)) break;
       }
     }
-    if (ready) {
-      st_relaxed(I.color + v, colour);
-      __threadfence();  // the colour is visible before any decrement below can make a neighbour ready
-    }
-    // count down the larger neighbours of every ready vertex; the decrement that reaches zero
-    // pushes the neighbour
-    if (t < cnt) {
-      sm.start[t] = s + lower;
-      sm.aux[t] = v;
-    }
-    int total;
-    const int off = block_exclusive_scan<BLOCK>(upper, sm.tmp, total);
-    if (t < cnt) sm.off[t] = off;
-    __syncthreads();
-    __threadfence();  // (the other threads' colour writes of this batch, ordered by the barrier)
-    for (int r = 0; r < total; r += BLOCK * R) {
-      int owner[R], nb[R];
-      lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const bool go = owner[j] >= 0 && atomicSub(I.gc_wait + nb[j], 1) == 1;
-        cta_push(sm, go, ~nb[j]);
-      }
-      __syncthreads();
-      if (sm.npush > 0) cta_flush<BLOCK>(sm, I, 0, L, st);
-    }
-    __syncthreads();
-    if (t == 0) {
-      st[kStatTasks] += cnt;
-      st[kStatEdges] += edges + total;
-    }
-    cta_flush<BLOCK>(sm, I, cnt, L, st);
   }
 
   template <int BLOCK, class S>
@@ -311,6 +398,18 @@ struct GcBody {
     const int m = s + ldg(I.gc_mid + v);  // [s, m): smaller neighbours, [m, e): larger ones
     int64_t edges = 0;
     int colour = -1;
+    if (I.gc_forbid) {  // pushed colours: the first clear bit of the bitmap, 32 words per step
+      const int2 f = __ldg(I.gc_fw + v);
+      for (int w0 = 0; colour < 0 && w0 < f.y; w0 += 32) {
+        const int w = w0 + lane;
+        const unsigned freeb = w < f.y ? ~__ldcg(I.gc_forbid + ATOS_IX(f.x + w, I.gc_forbid_words, L, kSiteEntry)) : 0u;
+        const unsigned any = __ballot_sync(0xffffffffu, freeb != 0u);
+        if (any) {
+          const int l = __ffs(any) - 1;
+          colour = 32 * (w0 + l) + __ffs(__shfl_sync(0xffffffffu, freeb, l)) - 1;
+        }
+      }
+    }
     for (int base = 0; colour < 0; base += kGcWindow) {
       unsigned lo = 0, hi = 0;
       for (int k = s + lane; k < m; k += 32) {
@@ -335,7 +434,12 @@ struct GcBody {
       bool go = false;
       if (k < e) {
         w = nbr_at(I, k, L);
+        if (I.gc_forbid) {
+          gc_push_colour(I, w, colour, L);
+          __threadfence();  // the colour bit is visible before the decrement
+        }
         go = atomicSub(I.gc_wait + w, 1) == 1;
+        if (go) __threadfence();  // the count's other decrements (and their writes) come first
       }
       warp_push(ws, go, ~w);
       if (ws.npush > 0) warp_flush(ws, I, 0, L, st);  // publish a ready vertex right away
@@ -497,6 +601,7 @@ struct GcBody {
     const int m = ready ? s + ldg(I.gc_mid + v) : s;  // [s, m): smaller neighbours, [m, e): larger
     unsigned long long edges = 0;
     int colour = -1;
+    if (I.gc_forbid && ready) colour = gc_first_free(I, v, L);  // pushed colours
     for (int base = 0; __any_sync(0xffffffffu, ready && colour < 0); base += kGcWindow) {
       const bool active = ready && colour < 0;
       unsigned long long used = 0;
@@ -524,7 +629,12 @@ struct GcBody {
       int w = 0;
       if (k < e) {
         w = nbr_at(I, k, L);
+        if (I.gc_forbid) {
+          gc_push_colour(I, w, colour, L);
+          __threadfence();  // the colour bit is visible before the decrement
+        }
         go = atomicSub(I.gc_wait + w, 1) == 1;
+        if (go) __threadfence();  // the count's other decrements (and their writes) come first
         ++k;
       }
       warp_push(ws, go, ~w);

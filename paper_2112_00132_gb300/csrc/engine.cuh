@@ -105,6 +105,10 @@ struct Instance {
   int32_t* gc_wait;      // colouring in dependency order: 1 + smaller-id neighbours not coloured yet
   const int32_t* gc_mid; // colouring in dependency order: smaller-id neighbours of each vertex, which
                          // `col` lists first in its row (the larger ones follow)
+  const int2* gc_fw;     // colouring in dependency order with pushed colours (optional): per vertex,
+                         // (first word, words) of its bitmap in gc_forbid
+  unsigned* gc_forbid;   // bit c of a vertex's bitmap: a coloured smaller neighbour holds colour c
+  uint32_t gc_forbid_words;  // words of gc_forbid
   double* cert_y;        // PageRank in batches and serving: FP64 scratch (n) of the output certificate
   int32_t* expanded;     // BFS (optional): the smallest depth at which each vertex has been expanded
   int4* segs;            // BFS row splitting (optional): segment tasks (vertex, first entry, depth, -)
@@ -417,6 +421,7 @@ struct CtaSmem {
   int tmp[33];
   int npush;
   int h, n, flag, cnt;
+  int keep;        // a body's block-wide decision (colouring: local continuation)
   unsigned base;
   int inst_id;
   int* status;     // the launch's status and failed-site words (checked builds record here)
@@ -440,12 +445,12 @@ __device__ __forceinline__ void cta_push(S& sm, bool want, int item) {
   if (want) sm.push[ATOS_IX(base + __popc(m & lanemask_lt()), S::kPushCap, sm, kSitePushBuffer)] = item;
 }
 
-// Publishes the CTA push buffer and reports `done` finished tasks (call with the whole block,
-// after a __syncthreads that follows the last cta_push).  Leaves npush = 0.
+// Publishes the CTA push buffer from entry `from` on and reports `done` finished tasks (call with
+// the whole block, after a __syncthreads that follows the last cta_push).  Leaves npush = 0.
 template <int BLOCK, class S>
 __device__ __forceinline__ void cta_flush(S& sm, const Instance& I, int done, const Launch& L,
-                                          unsigned long long* st) {
-  const int m = sm.npush;
+                                          unsigned long long* st, int from = 0) {
+  const int m = sm.npush - from;
   if (threadIdx.x == 0) {
     sm.base = reserve_and_complete(I, m, done, L);
     st[kStatPushes] += m;
@@ -454,7 +459,7 @@ __device__ __forceinline__ void cta_flush(S& sm, const Instance& I, int done, co
   const unsigned base = sm.base;
   if (m && base != 0xffffffffu) {
     if ((int)threadIdx.x < m) __threadfence();  // order the task body's writes before the items
-    for (int k = threadIdx.x; k < m; k += BLOCK) publish(I, base + k, sm.push[k], L);
+    for (int k = threadIdx.x; k < m; k += BLOCK) publish(I, base + k, sm.push[from + k], L);
   }
   __syncthreads();
   if (threadIdx.x == 0) sm.npush = 0;
