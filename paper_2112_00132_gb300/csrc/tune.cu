@@ -67,8 +67,8 @@ std::vector<atos_config> candidates(int app, int nsrc) {
   }
   if (app == ATOS_APP_COLOR) {
     // dependency-ordered colouring: exactly serial first fit in id order, one task per vertex
-    for (int w : {256, 512, 1024})
-      for (int f : {w, 64}) {  // small pops spread the long dependency chains' ready vertices
+    for (int w : {128, 256, 512, 1024})
+      for (int f : {w, w == 128 ? 32 : 64}) {  // small pops spread the long dependency chains' ready vertices
         atos_config c = make(nullptr, w, f, ATOS_FETCH_GREEDY);
         c.flags |= ATOS_FLAG_GC_DEPENDENCY;
         out.push_back(c);
