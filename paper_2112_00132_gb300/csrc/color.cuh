@@ -47,6 +47,7 @@
 namespace atos {
 
 constexpr int kGcWindow = 64;  // colours examined per pass: two 32-bit words per item
+constexpr int kGcHead = 16;    // dependency order: larger neighbours counted down in a batch's first pass
 
 template <int B>
 struct GcExtra {
@@ -153,16 +154,45 @@ struct GcBody {
       __threadfence();  // the colour is visible before any decrement below can make a neighbour ready
     }
     // count down the larger neighbours of every ready vertex; the decrement that reaches zero
-    // pushes the neighbour
-    if (t < cnt) {
-      sm.start[t] = s + lower;
-      sm.aux[t] = colour;
-    }
-    int total;
-    const int off = block_exclusive_scan<BLOCK>(upper, sm.tmp, total);
-    if (t < cnt) sm.off[t] = off;
+    // pushes the neighbour.  Two passes: first the first kGcHead larger neighbours of every vertex
+    // of the batch, then the rest of the rows, so that the next vertex of a dependency chain,
+    // which is nearly always among a vertex's first larger neighbours, is released in the first
+    // round whatever the other rows of the batch hold.
+    if (t < cnt) sm.aux[t] = colour;
     __syncthreads();
     __threadfence();  // (the other threads' colour writes of this batch, ordered by the barrier)
+    const int head = min(upper, kGcHead);
+    const bool more = __syncthreads_or(upper > kGcHead);
+    int total = countdown_pass<BLOCK>(sm, cnt, head, s + lower, !more, L, st);
+    if (more) total += countdown_pass<BLOCK>(sm, cnt, upper - head, s + lower + head, true, L, st);
+    __syncthreads();
+    if (t == 0) {
+      st[kStatTasks] += cnt;
+      st[kStatEdges] += edges + total;
+    }
+    // a failed launch stops here (the caller publishes, and nothing is kept); one thread decides
+    if (t == 0) sm.keep = ld_relaxed(L.status) != 0 ? 0 : min(sm.npush, keep_max);
+    __syncthreads();
+    return sm.keep;
+  }
+
+  // One countdown pass over entries [start, start + count) of each batch item's row (the
+  // neighbours' colour bits, then their counts).  Ready vertices are published after every round
+  // except the last round of the last pass (kept or published by the caller).  Returns the
+  // entries counted down.
+  template <int BLOCK, class S>
+  __device__ static int countdown_pass(S& sm, int cnt, int count, int start, bool last, const Launch& L,
+                                       unsigned long long* st) {
+    const Instance& I = sm.I;
+    const int t = threadIdx.x;
+    constexpr int R = LbsRun<BLOCK>::R;
+    int total;
+    const int off = block_exclusive_scan<BLOCK>(count, sm.tmp, total);  // ends with a barrier
+    if (t < cnt) {
+      sm.off[t] = off;
+      sm.start[t] = start;
+    }
+    __syncthreads();
     for (int r = 0; r < total; r += BLOCK * R) {
       int owner[R], nb[R];
       lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
@@ -181,19 +211,9 @@ struct GcBody {
       }
       if (made_ready) __threadfence();  // the count's other decrements (and their writes) come first
       __syncthreads();
-      // publish a round's ready vertices right away, except the last round's (kept or published
-      // by the caller)
-      if (sm.npush > 0 && r + BLOCK * R < total) cta_flush<BLOCK>(sm, I, 0, L, st);
+      if (sm.npush > 0 && (!last || r + BLOCK * R < total)) cta_flush<BLOCK>(sm, I, 0, L, st);
     }
-    __syncthreads();
-    if (t == 0) {
-      st[kStatTasks] += cnt;
-      st[kStatEdges] += edges + total;
-    }
-    // a failed launch stops here (the caller publishes, and nothing is kept); one thread decides
-    if (t == 0) sm.keep = ld_relaxed(L.status) != 0 ? 0 : min(sm.npush, keep_max);
-    __syncthreads();
-    return sm.keep;
+    return total;
   }
 
   // The colours of the ready vertices of a CTA batch from their smaller neighbours' colours.
