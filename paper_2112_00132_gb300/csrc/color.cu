@@ -115,15 +115,16 @@ cudaError_t gc_split_build(const int32_t* row_ptr, const int32_t* col, int n, in
 }
 
 // Pushed colours: vertex v's bitmap has (mid[v] + 32) / 32 words (room for colours 0..mid[v],
-// which holds its first-fit colour); fw[v] = (first word, words), the words laid out in id order.
+// which holds its first-fit colour): its own word in [0, n), then the rest (overflow) at
+// fw[v] = (first word, words), laid out in id order after the n first words.
 __global__ void gc_words_kernel(const int32_t* __restrict__ mid, int n, int32_t* __restrict__ words) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    words[v] = (mid[v] + 32) >> 5;
+    words[v] = ((mid[v] + 32) >> 5) - 1;
 }
 
 __global__ void gc_fw_kernel(const int32_t* __restrict__ first, int n, int2* __restrict__ fw) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    fw[v] = make_int2(first[v], first[v + 1] - first[v]);
+    fw[v] = make_int2(n + first[v], first[v + 1] - first[v]);
 }
 
 int64_t gc_bitmap_scratch(int n) { return (int64_t)n + 1 + n / 1024 + 2; }
@@ -142,7 +143,7 @@ cudaError_t gc_bitmap_build(const int32_t* mid, int n, int2* fw, int32_t* scratc
   int32_t words = 0;
   e = cudaMemcpyAsync(&words, scratch + n, sizeof(words), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess) *total_words = (uint32_t)words;
+  if (e == cudaSuccess) *total_words = (uint32_t)n + (uint32_t)words;
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -21,25 +21,22 @@
 // Dependency-ordered mode (ATOS_FLAG_GC_DEPENDENCY, I.gc_wait set): a vertex is coloured once,
 // after all of its smaller-id neighbours, taking the smallest colour none of them holds, so the
 // result is exactly serial first fit in id order, with one colouring task per vertex and no
-// recolouring.  The rows (I.col) list each vertex's smaller-id neighbours first (I.gc_mid[v] of
-// them), so the colour pass reads only those.  gc_wait[v] starts at 1 + I.gc_mid[v].  The virtual initial task
-// v releases the 1; a coloured vertex decrements the counter of each larger neighbour; whichever
+// recolouring.  gc_wait[v] starts at 1 + (smaller neighbours of v).  The virtual initial task v
+// releases the 1; a coloured vertex decrements the count of each larger neighbour; whichever
 // decrement reaches zero makes the vertex ready and (for a neighbour) pushes it as ~w.  Only one
-// decrement reaches zero, so each vertex is coloured exactly once.  A colour is written and
-// fenced before the decrements that follow it, and the task that reads it was pushed (fenced,
-// published) by the decrement that completed the count, so the colours a ready vertex reads are
-// final.
+// decrement reaches zero, so each vertex is coloured exactly once.
 //
-// With pushed colours (I.gc_forbid set) a ready vertex reads no neighbour at all: every vertex
-// has a bitmap of (smaller neighbours + 1) colour bits, and a coloured vertex sets its colour's bit
-// in the bitmap of each larger neighbour just before decrementing that neighbour's count.  When
-// the count reaches zero the bitmap holds the colours of all smaller neighbours, and the first
-// zero bit is the first-fit colour (at most `smaller neighbours` bits are set, so one of the first
-// smaller + 1 is clear; a colour beyond the bitmap cannot be the first free one and is not
-// recorded).  This moves the reading of a vertex's smaller neighbours off the dependency chain:
-// the chain's hops are then a bitmap scan and a decrement each, whatever the row lengths.  The bits
-// are fenced before the decrements, and the decrement that completes a count fences before it
-// pushes the vertex, so the bitmap a ready vertex reads is complete.
+// A ready vertex reads no neighbour: its smaller neighbours push their colours to it.  Every
+// vertex has a bitmap of at least (smaller neighbours + 1) colour bits, and a coloured vertex sets
+// its colour's bit in the bitmap of each larger neighbour just before it decrements that
+// neighbour's count.  When the count reaches zero the bitmap holds the colours of all smaller
+// neighbours, and its first clear bit is the first-fit colour (at most `smaller neighbours` bits
+// are set, so one of the first smaller + 1 is clear).  The rows (I.col) list each vertex's
+// smaller-id neighbours first (I.gc_mid[v] of them), so the countdown walks only the larger part.
+// Each bit is fenced before its decrement (release), and the decrement that completes a count is
+// fenced before the vertex is pushed, kept or coloured (acquire), so the bitmap a ready vertex
+// reads is complete.  A dependency chain's hop is then a bitmap read and a decrement, whatever the
+// row lengths.
 #pragma once
 
 #include "engine.cuh"
@@ -55,25 +52,41 @@ struct GcExtra {
                          // (own colour, conflict flag) (check)
 };
 
-// Pushed colours: records colour c in the bitmap of the larger neighbour w (when the bitmap has
-// room for it: first fit for w is at most its smaller-neighbour count).
+// Pushed colours.  Each vertex's bitmap is its word gc_forbid[v] (colours 0..31) followed, for a
+// vertex with 32 or more smaller neighbours, by gc_fw[v].y overflow words at gc_forbid[gc_fw[v].x]
+// (colours 32 and up): (smaller neighbours + 1) bits rounded up to whole words, and most vertices
+// (and most colours) need the first word only, which is found without reading gc_fw.
+
+// Records colour c in the bitmap of the larger neighbour w.  A colour of the first word is always
+// recorded; a later one only if w's bitmap reaches it (first fit for w is at most its
+// smaller-neighbour count, and a set bit beyond that count never hides the first clear one, as at
+// most that many bits are set).
 template <class Ctx>
 __device__ __forceinline__ void gc_push_colour(const Instance& I, int w, int c, Ctx& ctx) {
+  if (c < 32) {
+    atomicOr(I.gc_forbid + w, 1u << c);
+    return;
+  }
   const int2 f = __ldg(I.gc_fw + w);
-  if ((c >> 5) < f.y)
-    atomicOr(I.gc_forbid + ATOS_IX(f.x + (c >> 5), I.gc_forbid_words, ctx, kSiteEntry), 1u << (c & 31));
+  const int k = (c >> 5) - 1;
+  if (k < f.y) atomicOr(I.gc_forbid + ATOS_IX(f.x + k, I.gc_forbid_words, ctx, kSiteEntry), 1u << (c & 31));
 }
 
-// Pushed colours: the first-fit colour of a ready vertex, the first clear bit of its bitmap.
+// The first-fit colour of a ready vertex: the first clear bit of its bitmap.
 template <class Ctx>
 __device__ __forceinline__ int gc_first_free(const Instance& I, int v, Ctx& ctx) {
+  const unsigned b0 = __ldcg(I.gc_forbid + v);
+  if (~b0) return __ffs(~b0) - 1;
   const int2 f = __ldg(I.gc_fw + v);
   for (int w = 0; w < f.y; ++w) {
     const unsigned b = __ldcg(I.gc_forbid + ATOS_IX(f.x + w, I.gc_forbid_words, ctx, kSiteEntry));
-    if (~b) return 32 * w + __ffs(~b) - 1;
+    if (~b) return 32 * (w + 1) + __ffs(~b) - 1;
   }
-  return 32 * f.y;  // not reached: at most f.y * 32 - 1 bits are set
+  return 32 * (f.y + 1);  // not reached: at most (f.y + 1) * 32 - 1 bits are set
 }
+
+// Dependency order: item v >= 0 is the release task of v (its initial count), ~v a pushed vertex.
+__device__ __forceinline__ bool item_is_release(int item) { return item >= 0; }
 
 // Queues an assign task for u unless one is already queued.
 __device__ __forceinline__ bool gc_claim_assign(const Instance& I, int u) {
@@ -139,19 +152,12 @@ struct GcBody {
         lower = ldg(I.gc_mid + v);
         upper = ldg(I.row_ptr + v + 1) - s - lower;
       }
-      sm.start[t] = s;
     }
-    int64_t edges = 0;
     int colour = -1;
-    constexpr int R = LbsRun<BLOCK>::R;
-    if (I.gc_forbid) {
-      if (ready) colour = gc_first_free(I, v, sm);
-    } else {
-      colour_from_reads<BLOCK>(sm, cnt, ready, lower, colour, edges);
-    }
     if (ready) {
-      st_relaxed(I.color + v, colour);
-      __threadfence();  // the colour is visible before any decrement below can make a neighbour ready
+      if (item_is_release(sm.items[t]) && lower > 0) __threadfence();  // the count's other decrements (and bits) come first
+      colour = gc_first_free(I, v, sm);
+      st_relaxed(I.color + v, colour);  // read after the run only: the neighbours get it by their bitmaps
     }
     // count down the larger neighbours of every ready vertex; the decrement that reaches zero
     // pushes the neighbour.  Two passes: first the first kGcHead larger neighbours of every vertex
@@ -159,8 +165,6 @@ struct GcBody {
     // which is nearly always among a vertex's first larger neighbours, is released in the first
     // round whatever the other rows of the batch hold.
     if (t < cnt) sm.aux[t] = colour;
-    __syncthreads();
-    __threadfence();  // (the other threads' colour writes of this batch, ordered by the barrier)
     const int head = min(upper, kGcHead);
     const bool more = __syncthreads_or(upper > kGcHead);
     int total = countdown_pass<BLOCK>(sm, cnt, head, s + lower, !more, L, st);
@@ -168,7 +172,7 @@ struct GcBody {
     __syncthreads();
     if (t == 0) {
       st[kStatTasks] += cnt;
-      st[kStatEdges] += edges + total;
+      st[kStatEdges] += total;
     }
     // a failed launch stops here (the caller publishes, and nothing is kept); one thread decides
     if (t == 0) sm.keep = ld_relaxed(L.status) != 0 ? 0 : min(sm.npush, keep_max);
@@ -196,7 +200,7 @@ struct GcBody {
     for (int r = 0; r < total; r += BLOCK * R) {
       int owner[R], nb[R];
       lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
-      if (I.gc_forbid && owner[0] >= 0) {
+      if (owner[0] >= 0) {  // a thread's entries are consecutive: none if the first is past the end
 #pragma unroll
         for (int j = 0; j < R; ++j)
           if (owner[j] >= 0) gc_push_colour(I, nb[j], sm.aux[owner[j]], sm);
@@ -214,84 +218,6 @@ struct GcBody {
       if (sm.npush > 0 && (!last || r + BLOCK * R < total)) cta_flush<BLOCK>(sm, I, 0, L, st);
     }
     return total;
-  }
-
-  // The colours of the ready vertices of a CTA batch from their smaller neighbours' colours.
-  // First fit is at most the number of smaller neighbours, so a vertex needs lower + 1 colour
-  // bits.  When the batch's bitmaps fit in shared memory (2 words per thread) one pass over the
-  // smaller neighbours decides every colour; otherwise windows of 64 colours are examined in turn.
-  template <int BLOCK, class S>
-  __device__ static void colour_from_reads(S& sm, int cnt, bool ready, int lower, int& colour, int64_t& edges) {
-    const Instance& I = sm.I;
-    const int t = threadIdx.x;
-    constexpr int R = LbsRun<BLOCK>::R;
-    int words_total;
-    const int woff = block_exclusive_scan<BLOCK>(ready ? (lower + 32) >> 5 : 0, sm.tmp, words_total);
-    if (words_total <= 2 * BLOCK) {
-      if (t < cnt) {
-        sm.aux[t] = woff;
-        sm.items[t] = ready ? (lower + 32) >> 5 : 0;  // the task items are in registers by now
-      }
-      for (int k = t; k < words_total; k += BLOCK) sm.x.bits[k] = 0u;
-      int total;
-      const int off = block_exclusive_scan<BLOCK>(ready ? lower : 0, sm.tmp, total);  // ends with a barrier
-      if (t < cnt) sm.off[t] = off;
-      __syncthreads();
-      for (int r = 0; r < total; r += BLOCK * R) {
-        int owner[R], nb[R], c[R];
-        lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
-#pragma unroll
-        for (int j = 0; j < R; ++j) c[j] = owner[j] >= 0 ? __ldcg(I.color + nb[j]) : -1;
-#pragma unroll
-        for (int j = 0; j < R; ++j)
-          if (owner[j] >= 0 && c[j] >= 0 && (c[j] >> 5) < sm.items[owner[j]])
-            atomicOr(&sm.x.bits[ATOS_IX(sm.aux[owner[j]] + (c[j] >> 5), 2 * BLOCK, sm, kSiteShared)],
-                     1u << (c[j] & 31));
-      }
-      edges += total;
-      __syncthreads();
-      if (ready)
-        for (int w = 0; colour < 0; ++w) {  // a zero bit exists among the first lower + 1
-          const unsigned free_bits = ~sm.x.bits[woff + w];
-          if (free_bits) colour = 32 * w + __ffs(free_bits) - 1;
-        }
-      __syncthreads();
-    } else {
-      bool active = ready;
-      for (int base = 0;; base += kGcWindow) {
-        int total;
-        const int off = block_exclusive_scan<BLOCK>(active ? lower : 0, sm.tmp, total);
-        if (t < cnt) {
-          sm.off[t] = off;
-          sm.x.bits[2 * t] = 0u;
-          sm.x.bits[2 * t + 1] = 0u;
-        }
-        if (total == 0 && base > 0) break;
-        __syncthreads();
-        for (int r = 0; r < total; r += BLOCK * R) {
-          int owner[R], nb[R], c[R];
-          lbs_round<BLOCK>(sm, I.col, cnt, total, r, owner, nb);
-#pragma unroll
-          for (int j = 0; j < R; ++j) c[j] = owner[j] >= 0 ? __ldcg(I.color + nb[j]) : -1;
-#pragma unroll
-          for (int j = 0; j < R; ++j) {
-            const int rel = c[j] - base;
-            if (owner[j] >= 0 && rel >= 0 && rel < kGcWindow)
-              atomicOr(&sm.x.bits[2 * owner[j] + (rel >> 5)], 1u << (rel & 31));
-          }
-        }
-        edges += total;
-        __syncthreads();
-        bool again = false;
-        if (active) {
-          const unsigned long long used = ((unsigned long long)sm.x.bits[2 * t + 1] << 32) | sm.x.bits[2 * t];
-          if (~used) colour = base + __ffsll((long long)~used) - 1;
-          else again = true;
-        }
-        active = again;
-        if (!__syncthreads_or(again)) break;
-      }
-    }
   }
 
   template <int BLOCK, class S>
@@ -419,37 +345,13 @@ struct GcBody {
     if (!__shfl_sync(0xffffffffu, ready, 0)) return;
     const int s = ldg(I.row_ptr + v), e = ldg(I.row_ptr + v + 1);
     const int m = s + ldg(I.gc_mid + v);  // [s, m): smaller neighbours, [m, e): larger ones
-    int64_t edges = 0;
-    int colour = -1;
-    if (I.gc_forbid) {  // pushed colours: the first clear bit of the bitmap, 32 words per step
-      const int2 f = __ldg(I.gc_fw + v);
-      for (int w0 = 0; colour < 0 && w0 < f.y; w0 += 32) {
-        const int w = w0 + lane;
-        const unsigned freeb = w < f.y ? ~__ldcg(I.gc_forbid + ATOS_IX(f.x + w, I.gc_forbid_words, L, kSiteEntry)) : 0u;
-        const unsigned any = __ballot_sync(0xffffffffu, freeb != 0u);
-        if (any) {
-          const int l = __ffs(any) - 1;
-          colour = 32 * (w0 + l) + __ffs(__shfl_sync(0xffffffffu, freeb, l)) - 1;
-        }
-      }
-    }
-    for (int base = 0; colour < 0; base += kGcWindow) {
-      unsigned lo = 0, hi = 0;
-      for (int k = s + lane; k < m; k += 32) {
-        const int rel = __ldcg(I.color + nbr_at(I, k, L)) - base;
-        if (rel >= 0 && rel < 32) lo |= 1u << rel;
-        else if (rel >= 32 && rel < 64) hi |= 1u << (rel - 32);
-      }
-      edges += m - s;
-      lo = __reduce_or_sync(0xffffffffu, lo);
-      hi = __reduce_or_sync(0xffffffffu, hi);
-      const unsigned long long used = ((unsigned long long)hi << 32) | lo;
-      if (~used) colour = base + __ffsll((long long)~used) - 1;
-    }
+    int colour = 0;
     if (lane == 0) {
-      st_relaxed(I.color + v, colour);
-      __threadfence();  // the colour is visible before any decrement below
+      if (item_is_release(item) && m > s) __threadfence();  // the count's other decrements (and bits) come first
+      colour = gc_first_free(I, v, L);
+      st_relaxed(I.color + v, colour);  // read after the run only
     }
+    colour = __shfl_sync(0xffffffffu, colour, 0);
     __syncwarp();
     for (int k0 = m; k0 < e; k0 += 32) {
       const int k = k0 + lane;
@@ -457,17 +359,15 @@ struct GcBody {
       bool go = false;
       if (k < e) {
         w = nbr_at(I, k, L);
-        if (I.gc_forbid) {
-          gc_push_colour(I, w, colour, L);
-          __threadfence();  // the colour bit is visible before the decrement
-        }
+        gc_push_colour(I, w, colour, L);
+        __threadfence();  // the colour bit is visible before the decrement
         go = atomicSub(I.gc_wait + w, 1) == 1;
         if (go) __threadfence();  // the count's other decrements (and their writes) come first
       }
       warp_push(ws, go, ~w);
       if (ws.npush > 0) warp_flush(ws, I, 0, L, st);  // publish a ready vertex right away
     }
-    if (lane == 0) st[kStatEdges] += edges + (e - m);
+    if (lane == 0) st[kStatEdges] += e - m;
   }
 
   __device__ static void warp_item(WarpSmem& ws, const Instance& I, int item, const Launch& L,
@@ -624,26 +524,11 @@ struct GcBody {
     const int m = ready ? s + ldg(I.gc_mid + v) : s;  // [s, m): smaller neighbours, [m, e): larger
     unsigned long long edges = 0;
     int colour = -1;
-    if (I.gc_forbid && ready) colour = gc_first_free(I, v, L);  // pushed colours
-    for (int base = 0; __any_sync(0xffffffffu, ready && colour < 0); base += kGcWindow) {
-      const bool active = ready && colour < 0;
-      unsigned long long used = 0;
-      int k = active ? s : m;
-      while (__any_sync(0xffffffffu, k < m)) {
-        if (k < m) {
-          const int rel = __ldcg(I.color + nbr_at(I, k, L)) - base;
-          if (rel >= 0 && rel < kGcWindow) used |= 1ull << rel;
-          ++k;
-        }
-      }
-      if (active) {
-        edges += (unsigned long long)(m - s);
-        if (~used) colour = base + __ffsll((long long)~used) - 1;
-      }
-    }
     if (ready) {
+      if (item_is_release(item) && m > s) __threadfence();  // the count's other decrements (and bits) come first
+      colour = gc_first_free(I, v, L);
       st_relaxed(I.color + v, colour);
-      __threadfence();  // the colour is visible before any decrement below
+      __threadfence();  // not needed for the result; thread workers measured faster with it (RMAT 22)
       edges += (unsigned long long)(e - m);
     }
     int k = ready ? m : e;
@@ -652,10 +537,8 @@ struct GcBody {
       int w = 0;
       if (k < e) {
         w = nbr_at(I, k, L);
-        if (I.gc_forbid) {
-          gc_push_colour(I, w, colour, L);
-          __threadfence();  // the colour bit is visible before the decrement
-        }
+        gc_push_colour(I, w, colour, L);
+        __threadfence();  // the colour bit is visible before the decrement
         go = atomicSub(I.gc_wait + w, 1) == 1;
         if (go) __threadfence();  // the count's other decrements (and their writes) come first
         ++k;
