@@ -28,6 +28,9 @@ cudaError_t gc_split_build(const int32_t* row_ptr, const int32_t* col, int n, in
                            int32_t* long_rows, int* long_count, cudaStream_t s);
 cudaError_t gc_wait_init(const int32_t* mid, int n, int32_t* wait, cudaStream_t s);
 int64_t gc_bitmap_scratch(int n);
+cudaError_t gc_tail_segments(const int32_t* row_ptr, const int32_t* mid, int n, void* scratch, uint64_t* count,
+                             cudaStream_t s);
+uint64_t gc_tail_slack();
 cudaError_t gc_bitmap_build(const int32_t* mid, int n, int2* fw, int32_t* scratch, uint32_t* total_words,
                             cudaStream_t s);
 size_t spread_build_scratch_bytes(int32_t n);
@@ -136,6 +139,9 @@ struct atos_graph_s {
   int2* gc_fw[2] = {nullptr, nullptr};      // pushed colours: each vertex's bitmap (first word, words)
   uint32_t gc_fwords[2] = {0, 0};           // bitmap words of each layout
   unsigned* d_gc_forbid = nullptr;          // the bitmaps (gc_forbid_cap words)
+  uint64_t gc_tails[2] = {0, 0};            // tail segments a run can create, per layout
+  int4* d_gc_segs = nullptr;                // the tail-segment table (gc_segs_cap entries)
+  uint64_t gc_segs_cap = 0;
   uint32_t gc_forbid_cap = 0;
   size_t expanded_rows = 0;
   unsigned long long* d_timeline = nullptr;  // throughput timeline (atos_timeline), 2 counters per bucket
@@ -625,6 +631,7 @@ int atos_graph_destroy(atos_graph_t g) {
   pool_free(g->d_gc_wait);
   for (int k = 0; k < 2; ++k) pool_free(g->gc_mid[k]), pool_free(g->gc_col[k]), pool_free(g->gc_fw[k]);
   pool_free(g->d_gc_forbid);
+  pool_free(g->d_gc_segs);
   pool_free(g->d_timeline);
   g->s.release();
   delete g;
@@ -935,13 +942,28 @@ int atos_color(atos_graph_t g, int32_t* colors, int32_t* num_colors, const atos_
       int rc2 = from_cuda(dev_alloc(&fw, (size_t)n));
       if (!rc2) rc2 = from_cuda(dev_alloc(&tmp, (size_t)gc_bitmap_scratch(n)));
       if (!rc2) rc2 = from_cuda(gc_bitmap_build(g->gc_mid[lay], n, fw, tmp, &words, st));  // synchronises
+      uint64_t tails = 0;
+      if (!rc2) rc2 = from_cuda(gc_tail_segments(I.row_ptr, g->gc_mid[lay], n, tmp, &tails, st));  // synchronises
       pool_free(tmp);
       if (rc2) {
         pool_free(fw);
         return rc2;
       }
-      g->gc_fw[lay] = fw, g->gc_fwords[lay] = words;
+      g->gc_fw[lay] = fw, g->gc_fwords[lay] = words, g->gc_tails[lay] = tails ? tails + gc_tail_slack() : 0;
     }
+    // tail segments (CTA workers): room for every one the run can create, plus the chunks CTAs
+    // may leave partly used; item -(n + 1 + entry) must stay within int32
+    const uint64_t tails = g->gc_tails[lay];
+    const bool use_tails = cfg.worker_size > 32 && tails > 0 && (uint64_t)n + 1 + tails < (1ull << 31);
+    if (use_tails && g->gc_segs_cap < tails) {
+      cudaDeviceSynchronize();  // a previous call may still use the old table
+      pool_free(g->d_gc_segs);
+      g->d_gc_segs = nullptr;
+      g->gc_segs_cap = 0;
+      ATOS_TRY(dev_alloc(&g->d_gc_segs, (size_t)tails));
+      g->gc_segs_cap = tails;
+    }
+    if (use_tails) I.segs = g->d_gc_segs, I.seg_cap = (uint32_t)tails;
     if (g->gc_forbid_cap < g->gc_fwords[lay]) {
       cudaDeviceSynchronize();  // a previous call may still use the old bitmaps
       pool_free(g->d_gc_forbid);

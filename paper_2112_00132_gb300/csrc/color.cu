@@ -129,6 +129,46 @@ __global__ void gc_fw_kernel(const int32_t* __restrict__ first, int n, int2* __r
 
 int64_t gc_bitmap_scratch(int n) { return (int64_t)n + 1 + n / 1024 + 2; }
 
+// Tail segments the dependency-ordered colouring can create: a ready vertex's larger neighbours
+// after its first kGcHead, in segments of up to kGcSegment entries (each vertex is ready once).
+__global__ void gc_tail_count_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ mid, int n,
+                                     unsigned long long* out) {
+  unsigned long long c = 0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int upper = row_ptr[v + 1] - row_ptr[v] - mid[v];
+    if (upper > kGcHead) c += (unsigned long long)((upper - kGcHead + kGcSegment - 1) / kGcSegment);
+  }
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// Table entries a run may leave unused: every CTA (at most 32 per SM) may hold a partly used chunk.
+uint64_t gc_tail_slack() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 160;
+  return (uint64_t)kGcSegChunk * 32u * (uint64_t)sms;
+}
+
+// scratch: 8 bytes of device memory; synchronises s
+cudaError_t gc_tail_segments(const int32_t* row_ptr, const int32_t* mid, int n, void* scratch, uint64_t* count,
+                             cudaStream_t s) {
+  *count = 0;
+  if (n <= 0) return cudaSuccess;
+  unsigned long long* d = (unsigned long long*)scratch;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(*d), s);
+  if (e != cudaSuccess) return e;
+  int blocks = (n + 255) / 256;
+  blocks = blocks < 1 ? 1 : (blocks > 4096 ? 4096 : blocks);
+  count_launches(1);
+  gc_tail_count_kernel<<<blocks, 256, 0, s>>>(row_ptr, mid, n, d);
+  unsigned long long h = 0;
+  e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) *count = h;
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t gc_bitmap_build(const int32_t* mid, int n, int2* fw, int32_t* scratch, uint32_t* total_words,
                             cudaStream_t s) {
   *total_words = 0;

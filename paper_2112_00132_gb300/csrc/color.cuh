@@ -45,6 +45,8 @@ namespace atos {
 
 constexpr int kGcWindow = 64;  // colours examined per pass: two 32-bit words per item
 constexpr int kGcHead = 16;    // dependency order: larger neighbours counted down in a batch's first pass
+constexpr int kGcSegment = 2048;  // dependency order: entries of a tail segment task
+constexpr int kGcSegChunk = 64;   // dependency order: segment-table entries a CTA claims at a time
 
 template <int B>
 struct GcExtra {
@@ -134,58 +136,121 @@ struct GcBody {
     }
   }
 
-  // One batch of the dependency-ordered mode; returns how many of the vertices its last
-  // countdown round made ready (the first entries of the push buffer, which the caller
-  // publishes from there on) it keeps for local continuation.
+  // One batch of the dependency-ordered mode; returns how many of the vertices it made ready (the
+  // first entries of the push buffer, which the caller publishes from there on) it keeps for local
+  // continuation.
+  //
+  // The countdown runs in two passes.  The first covers the first kGcHead larger neighbours of
+  // every ready vertex of the batch: the next vertex of a dependency chain is nearly always among a
+  // vertex's first larger neighbours, so it is released in the first round whatever the other
+  // rows hold.  The rest of the rows (the tails) follow in a second pass, together with the tail
+  // segments in the batch; a tail longer than kGcSegment entries is cut into segment tasks
+  // instead (table I.segs, item -(n + 1 + entry)), which idle CTAs count down in parallel, so a
+  // hub's long row does not hold one CTA for its whole length.
   template <int BLOCK, class S>
   __device__ static int cta_dependency_round(S& sm, int cnt, int keep_max, const Launch& L, unsigned long long* st) {
     const Instance& I = sm.I;
     const int t = threadIdx.x;
-    int v = 0, lower = 0, upper = 0, s = 0;
-    bool ready = false;
+    int item = 0, v = 0, head = 0, start = 0, tail = 0, colour = -1;
+    bool ready = false, segment = false;
     if (t < cnt) {
-      const int item = sm.items[t];
-      v = item >= 0 ? item : ~item;
-      ready = item < 0 || atomicSub(I.gc_wait + v, 1) == 1;
-      s = ldg(I.row_ptr + v);
-      if (ready) {
-        lower = ldg(I.gc_mid + v);
-        upper = ldg(I.row_ptr + v + 1) - s - lower;
+      item = sm.items[t];
+      segment = item < -I.n;
+      if (segment) {  // a tail segment: entries [y, y + z) of x's row, x coloured w
+        const int4 e = __ldcg(I.segs + ATOS_IX(-(item + I.n + 1), I.seg_cap, sm, kSiteItem));
+        v = e.x, start = e.y, tail = e.z, colour = e.w;
+      } else {
+        v = item >= 0 ? item : ~item;
+        ready = item < 0 || atomicSub(I.gc_wait + v, 1) == 1;
+        const int s = ldg(I.row_ptr + v);
+        if (ready) {
+          const int lower = ldg(I.gc_mid + v);
+          const int upper = ldg(I.row_ptr + v + 1) - s - lower;
+          if (item_is_release(item) && lower > 0) __threadfence();  // the count's other decrements (and bits) come first
+          colour = gc_first_free(I, v, sm);
+          st_relaxed(I.color + v, colour);  // read after the run only: the neighbours get it by their bitmaps
+          head = min(upper, kGcHead);
+          start = s + lower;
+          tail = upper - head;
+        }
       }
+      sm.aux[t] = colour;
     }
-    int colour = -1;
-    if (ready) {
-      if (item_is_release(sm.items[t]) && lower > 0) __threadfence();  // the count's other decrements (and bits) come first
-      colour = gc_first_free(I, v, sm);
-      st_relaxed(I.color + v, colour);  // read after the run only: the neighbours get it by their bitmaps
+    // with tails to come, the first pass publishes everything it releases at once (other CTAs go on
+    // with those vertices while this one walks the tails); otherwise its last round's are kept
+    const bool more = __syncthreads_or(tail > 0);
+    int total = countdown_pass<BLOCK>(sm, cnt, head, start, more, L, st);
+    if (more) {
+      // tails longer than a segment go to other CTAs as segments; the others follow inline
+      const bool long_tail = ready && tail > kGcSegment;
+      if (I.segs && __syncthreads_or(long_tail) &&
+          split_tails<BLOCK>(sm, v, start + head, long_tail ? tail : 0, colour, sm.npush)) {
+        if (long_tail) tail = 0;
+        cta_flush<BLOCK>(sm, I, 0, L, st);  // the segments go out before the inline pass
+      }
+      total += countdown_pass<BLOCK>(sm, cnt, tail, ready ? start + head : start, false, L, st);
     }
-    // count down the larger neighbours of every ready vertex; the decrement that reaches zero
-    // pushes the neighbour.  Two passes: first the first kGcHead larger neighbours of every vertex
-    // of the batch, then the rest of the rows, so that the next vertex of a dependency chain,
-    // which is nearly always among a vertex's first larger neighbours, is released in the first
-    // round whatever the other rows of the batch hold.
-    if (t < cnt) sm.aux[t] = colour;
-    const int head = min(upper, kGcHead);
-    const bool more = __syncthreads_or(upper > kGcHead);
-    int total = countdown_pass<BLOCK>(sm, cnt, head, s + lower, !more, L, st);
-    if (more) total += countdown_pass<BLOCK>(sm, cnt, upper - head, s + lower + head, true, L, st);
+    __syncthreads();
+    const int front = sm.npush;  // the last round's vertices
     __syncthreads();
     if (t == 0) {
       st[kStatTasks] += cnt;
       st[kStatEdges] += total;
+      // a failed launch stops here (the caller publishes, and nothing is kept)
+      sm.keep = ld_relaxed(L.status) != 0 ? 0 : min(front, keep_max);
     }
-    // a failed launch stops here (the caller publishes, and nothing is kept); one thread decides
-    if (t == 0) sm.keep = ld_relaxed(L.status) != 0 ? 0 : min(sm.npush, keep_max);
     __syncthreads();
     return sm.keep;
   }
 
-  // One countdown pass over entries [start, start + count) of each batch item's row (the
-  // neighbours' colour bits, then their counts).  Ready vertices are published after every round
-  // except the last round of the last pass (kept or published by the caller).  Returns the
-  // entries counted down.
+  // Appends to the push buffer, after its first `released` entries, the tail of a ready vertex
+  // (entries [start, start + tail) of v's row, v coloured `colour`) as segments of up to kGcSegment
+  // entries.  Table entries are claimed kGcSegChunk at a time per CTA.  Returns false (nothing
+  // appended) when the table or the push buffer has no room.  Whole block.
   template <int BLOCK, class S>
-  __device__ static int countdown_pass(S& sm, int cnt, int count, int start, bool last, const Launch& L,
+  __device__ static bool split_tails(S& sm, int v, int start, int tail, int colour, int released) {
+    const Instance& I = sm.I;
+    const int parts = tail > 0 ? (tail + kGcSegment - 1) / kGcSegment : 0;
+    int nseg;
+    const int off = block_exclusive_scan<BLOCK>(parts, sm.tmp, nseg);  // ends with a barrier
+    if (threadIdx.x == 0) {
+      unsigned j0 = 0xffffffffu;
+      if (released + nseg <= S::kPushCap) {
+        if (sm.seg_hi - sm.seg_lo < (unsigned)nseg) {  // claim a new chunk (the rest of the old one is lost)
+          const unsigned want = max((unsigned)nseg, (unsigned)kGcSegChunk);
+          sm.seg_lo = atomicAdd(&I.ctl->seg_next, want);
+          sm.seg_hi = sm.seg_lo + want;
+        }
+        if (sm.seg_hi <= I.seg_cap && sm.seg_lo <= sm.seg_hi) {
+          j0 = sm.seg_lo;
+          sm.seg_lo += (unsigned)nseg;
+        } else {
+          sm.seg_lo = sm.seg_hi = 0;
+        }
+      }
+      sm.base = j0;
+    }
+    __syncthreads();
+    const unsigned j0 = sm.base;
+    if (j0 == 0xffffffffu) return false;  // uniform
+    for (int k = 0; k < parts; ++k) {
+      const int j = (int)j0 + off + k;
+      const int first = k * kGcSegment;
+      I.segs[j] = make_int4(v, start + first, min(kGcSegment, tail - first), colour);
+      sm.push[ATOS_IX(released + off + k, S::kPushCap, sm, kSitePushBuffer)] = -(I.n + 1 + j);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sm.npush = released + nseg;
+    __syncthreads();
+    return true;
+  }
+
+  // One countdown pass over entries [start, start + count) of each batch item's row (the
+  // neighbours' colour bits, then their counts).  Vertices made ready are published after every
+  // round but the last, and after the last too if flush_last (else they stay in the push buffer
+  // for the caller to keep or publish).  Returns the entries counted down.
+  template <int BLOCK, class S>
+  __device__ static int countdown_pass(S& sm, int cnt, int count, int start, bool flush_last, const Launch& L,
                                        unsigned long long* st) {
     const Instance& I = sm.I;
     const int t = threadIdx.x;
@@ -215,7 +280,7 @@ struct GcBody {
       }
       if (made_ready) __threadfence();  // the count's other decrements (and their writes) come first
       __syncthreads();
-      if (sm.npush > 0 && (!last || r + BLOCK * R < total)) cta_flush<BLOCK>(sm, I, 0, L, st);
+      if (sm.npush > 0 && (flush_last || r + BLOCK * R < total)) cta_flush<BLOCK>(sm, I, 0, L, st);
     }
     return total;
   }

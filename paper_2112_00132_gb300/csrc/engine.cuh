@@ -111,7 +111,8 @@ struct Instance {
   uint32_t gc_forbid_words;  // words of gc_forbid
   double* cert_y;        // PageRank in batches and serving: FP64 scratch (n) of the output certificate
   int32_t* expanded;     // BFS (optional): the smallest depth at which each vertex has been expanded
-  int4* segs;            // BFS row splitting (optional): segment tasks (vertex, first entry, depth, -)
+  int4* segs;            // segment tasks (optional): BFS row splitting (vertex, first entry, depth, -);
+                         // dependency-ordered colouring (vertex, first entry, entries, colour)
   uint32_t seg_cap;      // entries of segs
   double exact_sum;      // PageRank: n - alpha * (isolated vertices), the fixed point's sum
   HubMap hub;            // PageRank on the spread-id copy: the hubs' ids
@@ -274,6 +275,7 @@ __device__ __forceinline__ int nbr_at(const Instance& I, int k, const Launch& L)
 __device__ __forceinline__ int checked_item(const Instance& I, int item, const Launch& L) {
 #ifdef ATOS_CHECKED
   const bool ok = (item >= 0 && item < I.n) || (I.app == kAppGc && item < 0 && ~item < I.n) ||
+                  (I.app == kAppGc && I.segs && item < -I.n && (uint32_t)(-(item + I.n + 1)) < I.seg_cap) ||
                   (I.app == kAppBfs && I.segs && item < 0 && (uint32_t)(-(item + 1)) < I.seg_cap);
   if (!ok) {
     record_bounds(L.status, L.fail_site, kSiteItem);
@@ -422,6 +424,7 @@ struct CtaSmem {
   int npush;
   int h, n, flag, cnt;
   int keep;        // a body's block-wide decision (colouring: local continuation)
+  unsigned seg_lo, seg_hi;  // segment-table entries this CTA has claimed and not used yet
   unsigned base;
   int inst_id;
   int* status;     // the launch's status and failed-site words (checked builds record here)
@@ -706,6 +709,7 @@ __global__ void __launch_bounds__(BLOCK, (MinBlocks<Body, BLOCK>::value)) cta_pe
     if (threadIdx.x == 0) {
       sm.I = L.insts[inst];
       sm.inst_id = inst;
+      sm.seg_lo = sm.seg_hi = 0;
       sm.flag = ld_relaxed(&sm.I.ctl->finished);  // one thread decides for the block
     }
     __syncthreads();
@@ -736,6 +740,7 @@ __global__ void __launch_bounds__(BLOCK) cta_discrete_kernel(Launch L) {
   if (threadIdx.x == 0) {
     sm.I = L.insts[inst];
     sm.npush = 0;
+    sm.seg_lo = sm.seg_hi = 0;
     sm.status = L.status;
     sm.fail_site = L.fail_site;
   }

@@ -410,8 +410,50 @@ def test_color_dependency_equals_serial_greedy(atos, graphs, gname):
                 bad = np.flatnonzero(c != want)
                 assert bad.size == 0, f"{gname}/{cname}/spread={spread}: {bad.size} colours differ"
                 assert k == kw
-                assert st.tasks <= 2 * g.n  # one release per vertex, at most one ready push
+                # one release per vertex, at most one ready push, and the tail segments of the
+                # rows longer than 16 larger neighbours (up to 2048 entries each)
+                ids = perm if spread else np.arange(g.n)
+                assert st.tasks <= 2 * g.n + _tail_segments(g, ids)
                 assert G.scratch_check()[1] == 0
+
+
+def _tail_segments(g, ids):
+    """Tail segments the dependency-ordered colouring may create on g under the given ids."""
+    deg = np.diff(g.row_ptr)
+    src = np.repeat(np.arange(g.n), deg)
+    larger = np.bincount(src[ids[g.col] > ids[src]], minlength=g.n) if g.n else np.zeros(0, np.int64)
+    return int(np.ceil(np.maximum(0, larger - 16) / 2048).sum())
+
+
+def test_color_dependency_tail_segments(atos):
+    """Rows with more than 16 larger neighbours: CTA workers hand the rest of the row to other
+    CTAs as tail segments of up to 2048 entries once the first 16 released a vertex; the colouring
+    is still exactly serial first fit, and the star's hub row shows up as extra tasks."""
+    for g in (gg.star(20000), gg.rmat(16, 16, seed=3), _hub_ring(3, 9000)):
+        ref, kref = oracle.greedy_color(g)
+        with atos.Graph.from_csr(g) as G:
+            for cfg in (atos.queue_config(worker_size=128, fetch_size=32, fetch_policy=atos.FETCH_GREEDY),
+                        atos.queue_config(worker_size=256, fetch_size=256),
+                        atos.queue_config(worker_size=1024, fetch_size=64, fetch_policy=atos.FETCH_GREEDY),
+                        atos.queue_config("discrete-cta")):
+                cfg.flags |= atos.FLAG_GC_DEPENDENCY
+                for _ in range(2):  # the segment table is reused by the next call
+                    colors, k, st = G.color(cfg=cfg)
+                    assert st.status == 0 and k == kref, (g.name, cfg.worker_size)
+                    assert np.array_equal(colors.cpu().numpy(), ref), (g.name, cfg.worker_size)
+                    assert st.tasks <= 2 * g.n + _tail_segments(g, np.arange(g.n))
+                    if g.name.startswith("star"):
+                        assert st.tasks > 2 * g.n - 1, st.tasks  # the hub's tail went out as segments
+
+
+def _hub_ring(k, leaves):
+    """k hubs (ids 0..k-1) joined in a ring, each with `leaves` leaves of larger ids."""
+    pairs = [(i, (i + 1) % k) for i in range(k)]
+    nxt = k
+    for h in range(k):
+        pairs += [(h, nxt + j) for j in range(leaves)]
+        nxt += leaves
+    return gg.from_edges(nxt, pairs, "hub_ring")
 
 
 def test_color_dependency_full_size(atos):
