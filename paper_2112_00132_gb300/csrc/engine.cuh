@@ -212,7 +212,7 @@ struct Waiter {
     if (start == 0) start = now;
     if ((long long)(now - start) > limit) return false;
     if (sleep_ns) __nanosleep(sleep_ns);
-    sleep_ns = sleep_ns ? min(sleep_ns * 2, 2048u) : 32u;
+    sleep_ns = sleep_ns ? min(sleep_ns * 2, 512u) : 32u;
     return true;
   }
   __device__ __forceinline__ void reset() { start = 0, sleep_ns = 0; }
