@@ -41,6 +41,8 @@ struct MixedBody {
   template <int B>
   using Extra = MixedExtra<B>;
   static constexpr int kResidentThreads = 1536;
+  template <int B>
+  static constexpr int kLbsR = LbsRun<B>::R;
 
   template <int BLOCK, class S>
   __device__ static void cta_batch(S& sm, int cnt, const Launch& L, unsigned long long* st) {

@@ -13,13 +13,16 @@ struct BfsBody {
   template <int B>
   using Extra = NoExtra;
   static constexpr int kResidentThreads = 1536;
+  // edges per thread of a load-balancing round (RMAT 22 x64: 2 beats 4 at 256 threads)
+  template <int B>
+  static constexpr int kLbsR = B <= 512 ? 2 : 1;
 
   // Reads the neighbours' depths of one load-balancing round, relaxes them (atomicMin) and
   // pushes the neighbours it improved.
   template <int BLOCK, class S>
-  __device__ static void relax_round(S& sm, int32_t* __restrict__ depth, const int (&item)[LbsRun<BLOCK>::R],
-                                     const int (&nb)[LbsRun<BLOCK>::R]) {
-    constexpr int R = LbsRun<BLOCK>::R;
+  __device__ static void relax_round(S& sm, int32_t* __restrict__ depth, const int (&item)[S::kR],
+                                     const int (&nb)[S::kR]) {
+    constexpr int R = S::kR;
     int cur[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) cur[j] = item[j] >= 0 ? __ldcg(depth + nb[j]) : 0;
@@ -102,7 +105,7 @@ struct BfsBody {
     if ((int)threadIdx.x < cnt) sm.off[threadIdx.x] = off;
     __syncthreads();
     int32_t* __restrict__ depth = I.depth;
-    constexpr int R = LbsRun<BLOCK>::R;
+    constexpr int R = S::kR;
     int rounds = 0;
     if (BLOCK >= 512) {
       // software-pipelined: the next round's col gathers are in flight while this round's

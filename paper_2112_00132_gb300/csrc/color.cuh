@@ -103,6 +103,10 @@ struct GcBody {
   // push state in registers instead of spilling (RMAT 22, 128-thread CTAs: 34 -> 29 ms in
   // dependency order, 13 -> 9 ms for Algorithm 6 on the spread layout)
   static constexpr int kResidentThreads = 768;
+  // edges per thread of a load-balancing round (RMAT 22, dependency order: 2 beats 4 at 128-256
+  // threads)
+  template <int B>
+  static constexpr int kLbsR = B <= 512 ? 2 : 1;
 
   // Dependency-ordered mode: item v >= 0 releases the initial count of v, item ~v is a vertex
   // made ready by its last smaller neighbour.  Ready vertices take the smallest colour their
@@ -254,7 +258,7 @@ struct GcBody {
                                        unsigned long long* st) {
     const Instance& I = sm.I;
     const int t = threadIdx.x;
-    constexpr int R = LbsRun<BLOCK>::R;
+    constexpr int R = S::kR;
     int total;
     const int off = block_exclusive_scan<BLOCK>(count, sm.tmp, total);  // ends with a barrier
     if (t < cnt) {
@@ -328,7 +332,7 @@ struct GcBody {
       if (t < cnt) sm.off[t] = off;
       if (total == 0 && base > 0) break;
       __syncthreads();
-      constexpr int R = LbsRun<BLOCK>::R;
+      constexpr int R = S::kR;
       int rounds = 0;
       for (int r = 0; r < total; r += BLOCK * R) {
         int owner[R], nb[R], c[R];

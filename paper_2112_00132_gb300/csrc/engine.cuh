@@ -405,10 +405,12 @@ struct LbsRun {
   static constexpr int R = BLOCK <= 256 ? 4 : (BLOCK == 512 ? 2 : 1);
 };
 
-// Shared memory of a CTA worker.  `Extra` is the task body's own per-item state.
-template <int BLOCK, class Extra>
+// Shared memory of a CTA worker.  `Extra` is the task body's own per-item state; R_ the edges per
+// thread of its load-balancing rounds (the body's kLbsR).
+template <int BLOCK, class Extra, int R_ = LbsRun<BLOCK>::R>
 struct CtaSmem {
-  static constexpr int kRoundPushes = LbsRun<BLOCK>::R * BLOCK;  // most pushes one round can add
+  static constexpr int kR = R_;
+  static constexpr int kRoundPushes = R_ * BLOCK;  // most pushes one round can add
   // push buffer: room for several rounds, so the load-balancing loops check it (a block barrier)
   // only every kFlushEvery rounds
   static constexpr int kPushCap = 4 * kRoundPushes < 4096 ? 4 * kRoundPushes
@@ -488,8 +490,8 @@ __device__ __forceinline__ bool flush_round(int& rounds) {
 // starting at e0 = base + t * R; for each it returns the owning item and the neighbour id.
 template <int BLOCK, class S>
 __device__ __forceinline__ void lbs_round(const S& sm, const int32_t* __restrict__ col, int cnt, int total,
-                                          int base, int (&item)[LbsRun<BLOCK>::R], int (&nb)[LbsRun<BLOCK>::R]) {
-  constexpr int R = LbsRun<BLOCK>::R;
+                                          int base, int (&item)[S::kR], int (&nb)[S::kR]) {
+  constexpr int R = S::kR;
   const int e0 = base + (int)threadIdx.x * R;
 #pragma unroll
   for (int j = 0; j < R; ++j) item[j] = -1;
@@ -608,7 +610,8 @@ __device__ __forceinline__ void cta_orphan_pending(S& sm, bool pending, const La
 // Returns 1 when the worker paused (serving slice over), 0 when the instance ended for it
 // (terminated, or the launch failed).
 template <class Body, int BLOCK>
-__device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::template Extra<BLOCK>>& sm, const Launch& L,
+__device__ int cta_run_instance(CtaSmem<BLOCK, typename Body::template Extra<BLOCK>, Body::template kLbsR<BLOCK>>& sm,
+                                const Launch& L,
                                 unsigned long long* st, unsigned long long t0) {
   const Instance& I = sm.I;
   Waiter wait;
@@ -700,7 +703,7 @@ struct MinBlocks {
 
 template <class Body, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<Body, BLOCK>::value)) cta_persistent_kernel(Launch L) {
-  __shared__ CtaSmem<BLOCK, typename Body::template Extra<BLOCK>> sm;
+  __shared__ CtaSmem<BLOCK, typename Body::template Extra<BLOCK>, Body::template kLbsR<BLOCK>> sm;
   unsigned long long st[kNumStats] = {};
   const unsigned long long t0 = globaltimer();
   int inst = (int)(blockIdx.x % (unsigned)min(L.window, L.ninst));
@@ -734,7 +737,7 @@ __global__ void __launch_bounds__(BLOCK, (MinBlocks<Body, BLOCK>::value)) cta_pe
 // blockIdx.y selects the instance, blockIdx.x a FETCH-sized slice.  Items are already written.
 template <class Body, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) cta_discrete_kernel(Launch L) {
-  __shared__ CtaSmem<BLOCK, typename Body::template Extra<BLOCK>> sm;
+  __shared__ CtaSmem<BLOCK, typename Body::template Extra<BLOCK>, Body::template kLbsR<BLOCK>> sm;
   unsigned long long st[kNumStats] = {};
   const int inst = blockIdx.y;
   if (threadIdx.x == 0) {

@@ -185,6 +185,9 @@ struct PrBody {
   // 64 registers measured faster on RMAT at 256 and 512 threads but slower on the grid, and the
   // tuned RMAT configuration (1024 threads, one CTA per SM) is the same either way
   static constexpr int kResidentThreads = 1536;
+  // edges per thread of a load-balancing round (RMAT 22: 4 at up to 512 threads, 2 at 1024)
+  template <int B>
+  static constexpr int kLbsR = B <= 512 ? 4 : 2;
 
   // Algorithm 4's Check_Size scan of `nchk` vertex ids (rounded up to whole groups of 4) from
   // the round-robin cursor, which counts groups.  Each thread issues its G group loads, then its
@@ -244,7 +247,7 @@ struct PrBody {
     if ((int)threadIdx.x < cnt) sm.off[threadIdx.x] = off;
     __syncthreads();
     float* __restrict__ res = I.res;
-    constexpr int R = LbsRun<BLOCK>::R;
+    constexpr int R = S::kR;
     if (I.pr_crossing) {
       int rounds = 0;
       for (int base = 0; base < total; base += BLOCK * R) {
