@@ -44,7 +44,7 @@
 namespace atos {
 
 constexpr int kGcWindow = 64;  // colours examined per pass: two 32-bit words per item
-constexpr int kGcHead = 16;    // dependency order: larger neighbours counted down in a batch's first pass
+constexpr int kGcHead = 32;    // dependency order: larger neighbours counted down in a batch's first pass
 constexpr int kGcSegment = 2048;  // dependency order: entries of a tail segment task
 constexpr int kGcSegChunk = 64;   // dependency order: segment-table entries a CTA claims at a time
 

@@ -411,7 +411,7 @@ def test_color_dependency_equals_serial_greedy(atos, graphs, gname):
                 assert bad.size == 0, f"{gname}/{cname}/spread={spread}: {bad.size} colours differ"
                 assert k == kw
                 # one release per vertex, at most one ready push, and the tail segments of the
-                # rows longer than 16 larger neighbours (up to 2048 entries each)
+                # rows with more than 32 larger neighbours (up to 2048 entries each)
                 ids = perm if spread else np.arange(g.n)
                 assert st.tasks <= 2 * g.n + _tail_segments(g, ids)
                 assert G.scratch_check()[1] == 0
@@ -422,13 +422,13 @@ def _tail_segments(g, ids):
     deg = np.diff(g.row_ptr)
     src = np.repeat(np.arange(g.n), deg)
     larger = np.bincount(src[ids[g.col] > ids[src]], minlength=g.n) if g.n else np.zeros(0, np.int64)
-    return int(np.ceil(np.maximum(0, larger - 16) / 2048).sum())
+    return int(np.ceil(np.maximum(0, larger - 32) / 2048).sum())
 
 
 def test_color_dependency_tail_segments(atos):
-    """Rows with more than 16 larger neighbours: CTA workers hand the rest of the row to other
-    CTAs as tail segments of up to 2048 entries once the first 16 released a vertex; the colouring
-    is still exactly serial first fit, and the star's hub row shows up as extra tasks."""
+    """Rows with more than 32 + 2048 larger neighbours: CTA workers hand the rest of the row,
+    after the first 32, to other CTAs as tail segments of up to 2048 entries; the colouring is
+    still exactly serial first fit, and the star's hub row shows up as extra tasks."""
     for g in (gg.star(20000), gg.rmat(16, 16, seed=3), _hub_ring(3, 9000)):
         ref, kref = oracle.greedy_color(g)
         with atos.Graph.from_csr(g) as G:
