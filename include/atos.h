@@ -125,12 +125,19 @@ extern "C" {
                                      vertex once, after all of its smaller-id neighbours (in the ids
                                      the run uses), with the smallest colour none of them holds: a
                                      per-vertex count of uncoloured smaller neighbours makes a vertex
-                                     ready, and the task that colours a vertex counts down its larger
-                                     neighbours.  The result is exactly serial first fit in id order,
-                                     one task per vertex and no recolouring; the run takes as many
-                                     dependent steps as the longest path of increasing ids.  n int32
-                                     of scratch.  The BSP strategy ignores it; batches and servers
-                                     return ATOS_ERR_UNSUPPORTED. */
+                                     ready, and the task that colours a vertex sets its colour in a
+                                     bitmap of each larger neighbour and counts the neighbour down, so
+                                     a ready vertex reads only its own bitmap.  The result is exactly
+                                     serial first fit in id order, one task per vertex and no
+                                     recolouring; the run takes as many dependent steps as the longest
+                                     path of increasing ids.  With a CTA worker, rows with more than
+                                     2080 larger neighbours are counted down partly by other CTAs
+                                     (segment tasks of 2048 entries).  Scratch, per vertex layout and
+                                     built on first use: the rows split at the smaller neighbours
+                                     (n + nnz int32), the bitmaps (n int2 + about n + nnz / 64 words),
+                                     the segment table (16 bytes per possible segment), and n int32
+                                     counts.  The BSP strategy ignores it; batches and servers return
+                                     ATOS_ERR_UNSUPPORTED. */
 
 #define ATOS_FLAG_BFS_SPLIT_ROWS 512u /* atos_bfs with a CTA worker (worker_size >= 64, persistent
                                      and discrete): a popped vertex whose row holds more than 8192
