@@ -436,10 +436,13 @@ def run_atos(args, rank: int, world: int):
         },
         "clocks": clocks.summary(),
     }
-    if not args.no_e2e:
-        result["e2e"] = run_e2e(args, g, srcs, (cfg_bfs, cfg_pr, cfg_gc), bfs_edges + pr_edges + gc_edges, world)
+    # the end-to-end leg builds its own graph objects: release this one (and its autotuning and
+    # comparison state, CUDA graphs of the device-loop BSP forms included) first
     G.close()
     del depths
+    torch.cuda.synchronize()
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(args, g, srcs, (cfg_bfs, cfg_pr, cfg_gc), bfs_edges + pr_edges + gc_edges, world)
     if not args.no_configs and world == 1:
         # the other workloads, each measured on its own after the main step (not part of `value`)
         result["configs"] = {"grid2048": grid_leg(atos, stream, dev, hbm_peak),
