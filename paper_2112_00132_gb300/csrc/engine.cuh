@@ -105,9 +105,10 @@ struct Instance {
   int32_t* gc_wait;      // colouring in dependency order: 1 + smaller-id neighbours not coloured yet
   const int32_t* gc_mid; // colouring in dependency order: smaller-id neighbours of each vertex, which
                          // `col` lists first in its row (the larger ones follow)
-  const int2* gc_fw;     // colouring in dependency order with pushed colours (optional): per vertex,
-                         // (first word, words) of its bitmap in gc_forbid
-  unsigned* gc_forbid;   // bit c of a vertex's bitmap: a coloured smaller neighbour holds colour c
+  const int2* gc_fw;     // colouring in dependency order: per vertex, (first word, words) of the
+                         // overflow part of its bitmap (colours 32 and up) in gc_forbid
+  unsigned* gc_forbid;   // the bitmaps: word v holds vertex v's colours 0..31, the overflow words
+                         // follow; bit c set = a coloured smaller neighbour holds colour c
   uint32_t gc_forbid_words;  // words of gc_forbid
   double* cert_y;        // PageRank in batches and serving: FP64 scratch (n) of the output certificate
   int32_t* expanded;     // BFS (optional): the smallest depth at which each vertex has been expanded
