@@ -109,9 +109,10 @@ struct GcBody {
   static constexpr int kLbsR = B <= 512 ? 2 : 1;
 
   // Dependency-ordered mode: item v >= 0 releases the initial count of v, item ~v is a vertex
-  // made ready by its last smaller neighbour.  Ready vertices take the smallest colour their
-  // smaller neighbours (the first gc_mid[v] entries of the row) do not hold, then count down
-  // their larger neighbours (the rest of the row).  A vertex made ready is published as soon as
+  // made ready by its last smaller neighbour, an item below -n a tail segment.  A ready vertex
+  // takes the first clear bit of its colour bitmap (its smaller neighbours' colours, pushed by
+  // them), then counts down its larger neighbours (the row after its first gc_mid[v] entries):
+  // each gets the colour's bit, then a decrement.  A vertex made ready is published as soon as
   // the round that made it ready ends, not at the end of the batch: a hub's row is long, and the
   // next vertex on the longest dependency path is often among the first it releases.
   //
