@@ -444,6 +444,15 @@ def test_color_dependency_tail_segments(atos):
                     assert st.tasks <= 2 * g.n + _tail_segments(g, np.arange(g.n))
                     if g.name.startswith("star"):
                         assert st.tasks > 2 * g.n - 1, st.tasks  # the hub's tail went out as segments
+            # the spread-id copy: serial first fit in that copy's id order
+            perm, _ = G.spread_layout()
+            ref_sp, kref_sp = oracle.greedy_color(g, order=np.argsort(perm))
+            cfg = atos.queue_config(worker_size=128, fetch_size=32, fetch_policy=atos.FETCH_GREEDY,
+                                    flags=atos.FLAG_GC_DEPENDENCY | atos.FLAG_SPREAD_IDS)
+            colors, k, st = G.color(cfg=cfg)
+            assert st.status == 0 and k == kref_sp, g.name
+            assert np.array_equal(colors.cpu().numpy(), ref_sp), g.name
+            assert st.tasks <= 2 * g.n + _tail_segments(g, perm)
 
 
 def _hub_ring(k, leaves):
